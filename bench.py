@@ -1,0 +1,355 @@
+"""Benchmark of the resampling hot path on one B300 (or N independent replicas).
+
+Workload (one "step"): a 4096x4096x3 FP32 image of 64 random plane waves plus
+N(0, 0.05^2) noise, clipped to [0, 1] (synthetic; seeded), resampled with
+Lanczos-3 and the mirror boundary by scale 1.37 (-> 5612x5612x3) and by scale
+0.3 with antialiasing (-> 1229x1229x3, ~20 taps per axis).  Each step runs the
+whole path on the GPU: the FP64 weight-table kernels of both plans and the two
+resample kernels.  Inputs stay resident in HBM; the input (201 MB) is larger
+than L2 (126 MB), so no explicit flush is needed between steps.
+
+Printed line (rank 0): output Mpixel/s over the K timed steps, the roofline of
+the dominant kernel (the x1.37 resample), an end-to-end figure through the C
+ABI with host buffers (H2D of the input and D2H of both outputs inside the
+timed region), SM clocks sampled during the timed region, and the FP64 CPU
+oracle timed on the host cores on a bounded sample of the same workload.
+
+``--impl reference`` times that oracle alone (the project has no other
+reference implementation: the paper ships no code).  Under torchrun each rank
+runs an independent replica (no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "output Mpixel/s, 4096x4096x3 FP32 Lanczos-3 mirror, x1.37 + x0.3 (antialiased)"
+UNIT = "Mpixel/s"
+SCALES = (1.37, 0.3)
+N_IN = 4096
+C = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample-s", type=float, default=12.0,
+                    help="target seconds of oracle work for the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def out_sizes():
+    return [max(1, int(math.floor(N_IN * s + 0.5))) for s in SCALES]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1110_5450_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "rs.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, only if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") == kernel_source_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "", 1).isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_baseline(img, budget_s: float):
+    """The FP64 oracle on the host cores, on a band of output rows of both
+    scales sized to about ``budget_s`` seconds; returns (Mpixel/s, cores, text)."""
+    import oracle
+
+    o = oracle.default()
+    outs = out_sizes()
+    # calibrate on 8 rows of each scale, then size each band to its share of the budget
+    rates = []
+    for s, n in zip(SCALES, outs):
+        t0 = time.perf_counter()
+        o.resample(img, n, n, "lanczos", "mirror", param=3.0, rows=(0, 8))
+        rates.append(8 / max(time.perf_counter() - t0, 1e-6))  # rows/s
+    total_px = sum(n * n for n in outs)
+    rows = [max(8, min(n, int(budget_s * (n * n) / total_px * r))) for n, r in zip(outs, rates)]
+    full_s, dt = 0.0, 0.0
+    for (n, k) in zip(outs, rows):
+        y0 = (n - k) // 2
+        t0 = time.perf_counter()
+        o.resample(img, n, n, "lanczos", "mirror", param=3.0, rows=(y0, y0 + k))
+        t = time.perf_counter() - t0
+        dt += t
+        full_s += t * (n / k)  # seconds for all n rows at the sampled rate
+    value = total_px / full_s / 1e6
+    sample = "central bands of %s output rows of the x1.37 and x0.3 outputs (%.1f s)" % (
+        "+".join(str(k) for k in rows), dt)
+    return value, o.default_threads(), sample
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import synth
+
+    img = synth.sinusoids(N_IN, N_IN, C, seed=synth.SEED_C2)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(img, min(per_step, 2.0))
+    vals, cores, sample = [], 0, ""
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, sample = cpu_baseline(img, per_step)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    outs = out_sizes()
+    mpx_step = sum(n * n for n in outs) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mpx_step / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "C2 4096x4096x3 x1.37+x0.3 Lanczos-3 mirror"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample + "; per step, %d steps in %.1f s" % (args.steps, wall)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import paper_1110_5450_b300 as rs
+    import synth
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    outs = out_sizes()
+
+    img = synth.sinusoids(N_IN, N_IN, C, seed=synth.SEED_C2 + rank)
+    x = torch.from_numpy(img).to(dev)
+    with torch.cuda.stream(stream):
+        plans = [rs.Plan(N_IN, N_IN, C, scale=s, kernel="lanczos", param=3.0, boundary="mirror",
+                         dtype=torch.float32, stream=stream) for s in SCALES]
+        ys = [torch.empty(p.out_shape, dtype=torch.float32, device=dev) for p in plans]
+    torch.cuda.synchronize()
+    # our kernels per step and plan: weight tables (+ band tables on the fused
+    # path) and the resample (one fused kernel, or the H and V kernels)
+    launches_per_step = sum(3 for p in plans)
+
+    def step(ev=None):
+        for k, (p, y) in enumerate(zip(plans, ys)):
+            p.recompute(stream)
+            if ev is not None and k == 0:
+                ev[0].record(stream)
+            p(x, out=y, stream=stream)
+            if ev is not None and k == 0:
+                ev[1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev.index or 0)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(kev[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end)
+    kms = [a.elapsed_time(b) for a, b in kev]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+
+    mpx_step = sum(n * n for n in outs) / 1e6
+    value = world * args.steps * mpx_step / (ms / 1e3)
+
+    # roofline of the dominant kernel: the x1.37 resample
+    in_bytes = N_IN * N_IN * C * 4
+    out_bytes = outs[0] * outs[0] * C * 4
+    alg = in_bytes + out_bytes
+    k_avg_s = statistics.mean(kms) / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = alg / k_avg_s / 1e9
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(img).pin_memory()
+        h_outs = [torch.empty(p.out_shape, dtype=torch.float32).pin_memory() for p in plans]
+        d_in = torch.empty_like(x)
+
+        def e2e_step():
+            d_in.copy_(h_in, non_blocking=True)
+            for p, y, h in zip(plans, ys, h_outs):
+                p.recompute(stream)
+                rs.rs_resample(p.handle, d_in.data_ptr(), y.data_ptr(), stream.cuda_stream)
+                h.copy_(y, non_blocking=True)
+
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                e2e_step()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            n_e2e = max(3, min(args.steps, 10))
+            a.record(stream)
+            for _ in range(n_e2e):
+                e2e_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / n_e2e
+        e2e = {"value": mpx_step / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+               "d2h_bytes_per_step": sum(n * n * C * 4 for n in outs), "ms_per_step": e_ms}
+
+    for p in plans:
+        p.check()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline(img, args.cpu_sample_s)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        info = plans[0].info
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "C2 4096x4096x3 FP32 sinusoids+noise, Lanczos-3 mirror, x1.37 and x0.3",
+                       "outputs": ["%dx%dx%d" % (n, n, C) for n in outs],
+                       "step": "weight-table kernels + resample, both scales",
+                       "l2": "input 201 MB > 126 MB L2, no flush",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "path_x1.37": rs.PATHS[info.path], "tile": [info.tile_h, info.tile_w],
+                       "band": [info.group_h, info.span_h], "path_x0.3": rs.PATHS[plans[1].info.path]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(),
+                         "kernel": "fused resample x1.37", "algorithmic_bytes": alg,
+                         "avg_kernel_ms": k_avg_s * 1e3, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * rs.h -- C ABI of the B300 (sm_103a) reconstruction-filter resampler.
+ *
+ * What the library computes.  For an image of in_h x in_w pixels with
+ * `channels` interleaved samples per pixel (HWC), each output sample is a
+ * normalised weighted sum of input samples under a separable reconstruction
+ * kernel:
+ *
+ *     out[y][x][c] = sum_j sum_i  wy(y, j) wx(x, i) in[B_h(j)][B_w(i)][c]
+ *
+ * with, per axis (n_in input samples, n_out output samples):
+ *   - half-pixel centres: output i sits at c_i = (i + 1/2) n_in / n_out;
+ *   - antialiasing: the kernel is widened by sc = max(1, n_in / n_out), so
+ *     its argument is x = ((2j+1) n_out - (2i+1) n_in) / D with the exact
+ *     integer denominator D = 2 max(n_in, n_out) (D = 2 n_out with
+ *     RS_NO_ANTIALIAS);
+ *   - taps: the integers j with |x| < R (R the kernel's support radius); the
+ *     first tap is j_lo = floor(((2i+1) n_in - R D - n_out) / (2 n_out)) + 1,
+ *     computed in 64-bit integers, so tap indices are exact;
+ *   - weights: w = K(x) evaluated in FP64, divided by their FP64 sum, then
+ *     rounded to the working precision; the rounding residual 1 - sum(w) is
+ *     added to the largest-magnitude weight and that weight re-rounded;
+ *   - kernels (standard published definitions):
+ *       RS_K_LINEAR    tent 1 - |x|, R = 1
+ *       RS_K_CUBIC     Keys cubic convolution with parameter a = `param`
+ *                      (R. Keys, IEEE Trans. ASSP 29(6), 1981), R = 2
+ *       RS_K_LANCZOS   sinc(x) sinc(x / R), R = `param` (integer 1..16)
+ *                      (C. Duchon, J. Appl. Meteor. 18, 1979)
+ *       RS_K_BSPLINE3  cubic B-spline (M. Unser, IEEE SP Mag. 16(6), 1999),
+ *                      used directly as an approximating kernel, R = 2
+ *   - boundary maps B for an axis of n samples:
+ *       RS_B_CLAMP       min(max(j, 0), n - 1)
+ *       RS_B_MIRROR      half-sample symmetric (edge sample repeated),
+ *                        period 2n, folds any number of times
+ *       RS_B_REFLECT101  whole-sample symmetric, period 2n - 2
+ *       RS_B_TRUNCATE    out-of-range taps dropped, the rest renormalised
+ *   - no clamping of the result (cubic and Lanczos overshoot is kept).
+ *
+ * The paper this library accompanies (arXiv:1110.5450) states no resampling
+ * formula of its own; every definition above is the standard one cited beside
+ * it.
+ *
+ * Conventions for every entry point.
+ *   - Pointers named d_* are CUDA device pointers on the current device;
+ *     pointers named h_* are host pointers.  `stream` is a cudaStream_t cast
+ *     to void* (NULL = the legacy default stream).
+ *   - The caller owns every image buffer.  A plan owns its weight tables and
+ *     any intermediate buffer; rs_destroy frees them (NULL is accepted).
+ *   - Work is enqueued asynchronously on the stream; argument errors are
+ *     returned synchronously before anything is enqueued.  Errors raised on
+ *     the device (RS_CHECK bounds words, bounded waits that ran out) are
+ *     reported by rs_plan_check / rs_batch_poll after the stream has drained.
+ *   - No C++ exception crosses this interface.  rs_last_error() returns a
+ *     thread-local message describing the most recent failure on the calling
+ *     thread.
+ *   - A plan may be used from one host thread at a time.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RS_API __attribute__((visibility("default")))
+#else
+#define RS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RS_OK = 0,
+    RS_ERR_INVALID_ARG = 1, /* malformed descriptor, NULL pointer, bad size   */
+    RS_ERR_UNSUPPORTED = 2, /* valid request this build does not implement    */
+    RS_ERR_OOM = 3,         /* a device allocation failed                     */
+    RS_ERR_BUDGET = 4,      /* a server's memory budget cannot hold a request */
+    RS_ERR_CUDA = 5,        /* a CUDA runtime call failed                     */
+    RS_ERR_TIMEOUT = 6,     /* a bounded device or host wait ran out          */
+    RS_ERR_BUSY = 7,        /* queue full or work still in flight             */
+    RS_ERR_DEVICE = 8       /* a device-side check (RS_CHECK) failed          */
+} rs_status;
+
+typedef enum { RS_F64 = 0, RS_F32 = 1, RS_F16 = 2, RS_BF16 = 3 } rs_dtype;
+
+typedef enum {
+    RS_K_LINEAR = 0,
+    RS_K_CUBIC = 1,   /* param = a, e.g. -0.5 */
+    RS_K_LANCZOS = 2, /* param = R, e.g. 3    */
+    RS_K_BSPLINE3 = 3
+} rs_kernel;
+
+typedef enum {
+    RS_B_CLAMP = 0,
+    RS_B_MIRROR = 1,
+    RS_B_REFLECT101 = 2,
+    RS_B_TRUNCATE = 3
+} rs_boundary;
+
+/* Plan flags. */
+#define RS_NO_ANTIALIAS 0x01u /* do not widen the kernel when downscaling        */
+#define RS_FORCE_SIMT 0x02u   /* never pick the tensor-core (tcgen05) path        */
+#define RS_FORCE_TC 0x04u     /* pick the tcgen05 banded-GEMM path (F16/BF16)     */
+#define RS_TWO_PASS 0x08u     /* separate H-then-V kernels through an HBM buffer  */
+#define RS_CHECK 0x10u        /* device bounds checks that set an error word      */
+
+/* Plan descriptor.  Sizes are in samples/elements, not bytes. */
+typedef struct {
+    int32_t in_h, in_w, channels; /* source grid, HWC interleaved, 1 <= channels <= 64 */
+    int32_t out_h, out_w;         /* target grid; 0 => derive from scale_h / scale_w   */
+    double scale_h, scale_w;      /* used iff out_* == 0: out = max(1, floor(n s + 1/2)) */
+    int32_t kernel;               /* rs_kernel                                          */
+    double param;                 /* a for RS_K_CUBIC, R for RS_K_LANCZOS, else ignored */
+    int32_t boundary;             /* rs_boundary                                        */
+    int32_t in_dtype, out_dtype;  /* rs_dtype; must be equal.  Accumulation is FP64 for
+                                     RS_F64 and FP32 otherwise                          */
+    uint32_t flags;               /* RS_* flags above                                   */
+    int64_t in_row_stride;        /* elements between input rows; 0 => in_w * channels  */
+    int64_t out_row_stride;       /* elements between output rows; 0 => out_w*channels  */
+} rs_plan_desc;
+
+typedef struct rs_plan rs_plan;
+
+/* Create a plan: validates the descriptor, derives the output size, allocates
+ * the weight tables on the current device and enqueues the FP64 weight-table
+ * kernel on `stream`, then synchronises that stream once to read back the
+ * tap-span statistics that choose the pass kernel.  On success *out receives
+ * the plan; on failure *out is set to NULL and nothing stays allocated.
+ * Limits: sides 1 .. 2^22, taps per output (before boundary folding) <= 256. */
+RS_API rs_status rs_plan_create(const rs_plan_desc *desc, void *stream, rs_plan **out);
+
+/* Resample one image: d_in holds in_h rows of in_row_stride elements of
+ * in_dtype, d_out receives out_h rows of out_row_stride elements of
+ * out_dtype.  Buffers must not overlap.  Asynchronous on `stream`. */
+RS_API rs_status rs_resample(rs_plan *plan, const void *d_in, void *d_out, void *stream);
+
+/* Re-run the weight-table kernels of a plan on `stream` into the plan's
+ * existing tables (no allocation, no synchronisation).  The tables are a
+ * deterministic function of the descriptor, so this reproduces them bit for
+ * bit; it exists so that a timed step can include the table computation. */
+RS_API rs_status rs_plan_recompute(rs_plan *plan, void *stream);
+
+/* Free a plan after waiting for its work to finish.  NULL is accepted. */
+RS_API rs_status rs_destroy(rs_plan *plan);
+
+/* Facts about a created plan. */
+typedef struct {
+    int32_t out_h, out_w;     /* derived output size                              */
+    int32_t taps_h, taps_w;   /* raw taps per output (max over outputs), per axis */
+    int32_t table_h, table_w; /* stored (boundary-folded) taps per output         */
+    int32_t path;             /* 0 = fused SIMT, 1 = two-pass SIMT, 2 = tcgen05    */
+    int32_t tile_h, tile_w;   /* output tile of the chosen pass kernel            */
+    int32_t group_h, group_w; /* outputs per thread group along each axis         */
+    int32_t span_h, span_w;   /* register band width (inputs per group)           */
+    int64_t scratch_bytes;    /* device bytes owned by the plan                   */
+} rs_plan_info;
+
+RS_API rs_status rs_plan_get_info(const rs_plan *plan, rs_plan_info *info);
+
+/* Copy one axis' tables to the host (synchronises the device).  axis 0 = rows
+ * (height), 1 = columns (width).  Each h_* may be NULL to skip it; arrays are
+ * sized for n_out entries (h_w64: n_out * table entries, row-major).
+ *   h_jlo    first raw tap j_lo (may be negative or >= n_in)
+ *   h_count  number of raw taps with |x| < R
+ *   h_start  first input index of the stored, boundary-folded window
+ *   h_w64    folded, normalised FP64 weights (window position k <-> index
+ *            h_start + k)
+ *   h_wwork  weights rounded to the working precision and residual-corrected,
+ *            widened to double for the copy */
+RS_API rs_status rs_plan_get_tables(const rs_plan *plan, int axis, int32_t *h_jlo, int32_t *h_count,
+                             int32_t *h_start, double *h_w64, double *h_wwork);
+
+/* Synchronise the device and report any device-side error word the plan's
+ * kernels set (RS_CHECK builds and bounded waits); clears the word. */
+RS_API rs_status rs_plan_check(rs_plan *plan);
+
+RS_API const char *rs_status_string(rs_status status);
+RS_API const char *rs_last_error(void);
+
+/* Library version, for the Python binding's sanity check. */
+RS_API int32_t rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_H */

@@ -1,0 +1,260 @@
+"""Python binding of the B300 reconstruction-filter resampler (include/rs.h).
+
+Argument marshalling only: every step of the resampling path (tap indices,
+FP64 weight tables, pass kernels) runs in the CUDA kernels of
+``librs_b300.so``.  PyTorch is used for device memory and streams.  There is
+no CPU fallback: importing this package without the compiled library raises.
+
+The functions keep the C names (``rs_plan_create``, ``rs_resample``,
+``rs_plan_recompute``, ``rs_destroy``, ...); ``Plan`` is a small convenience
+wrapper that owns one plan and accepts torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librs_b300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "librs_b300.so is not built; run `python paper_1110_5450_b300/build.py` "
+        "(the resampler has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------- enums
+RS_OK, RS_ERR_INVALID_ARG, RS_ERR_UNSUPPORTED, RS_ERR_OOM, RS_ERR_BUDGET = 0, 1, 2, 3, 4
+RS_ERR_CUDA, RS_ERR_TIMEOUT, RS_ERR_BUSY, RS_ERR_DEVICE = 5, 6, 7, 8
+RS_F64, RS_F32, RS_F16, RS_BF16 = 0, 1, 2, 3
+RS_K_LINEAR, RS_K_CUBIC, RS_K_LANCZOS, RS_K_BSPLINE3 = 0, 1, 2, 3
+RS_B_CLAMP, RS_B_MIRROR, RS_B_REFLECT101, RS_B_TRUNCATE = 0, 1, 2, 3
+RS_NO_ANTIALIAS, RS_FORCE_SIMT, RS_FORCE_TC, RS_TWO_PASS, RS_CHECK = 0x1, 0x2, 0x4, 0x8, 0x10
+
+KERNELS = {"linear": RS_K_LINEAR, "cubic": RS_K_CUBIC, "lanczos": RS_K_LANCZOS,
+           "bspline3": RS_K_BSPLINE3}
+BOUNDARIES = {"clamp": RS_B_CLAMP, "mirror": RS_B_MIRROR, "reflect101": RS_B_REFLECT101,
+              "truncate": RS_B_TRUNCATE}
+DEFAULT_PARAM = {"linear": 0.0, "cubic": -0.5, "lanczos": 3.0, "bspline3": 0.0}
+PATHS = {0: "fused", 1: "two_pass", 2: "tcgen05"}
+
+
+class rs_plan_desc(ctypes.Structure):
+    _fields_ = [("in_h", ctypes.c_int32), ("in_w", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("out_h", ctypes.c_int32), ("out_w", ctypes.c_int32),
+                ("scale_h", ctypes.c_double), ("scale_w", ctypes.c_double),
+                ("kernel", ctypes.c_int32), ("param", ctypes.c_double),
+                ("boundary", ctypes.c_int32),
+                ("in_dtype", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
+                ("flags", ctypes.c_uint32),
+                ("in_row_stride", ctypes.c_int64), ("out_row_stride", ctypes.c_int64)]
+
+
+class rs_plan_info(ctypes.Structure):
+    _fields_ = [("out_h", ctypes.c_int32), ("out_w", ctypes.c_int32),
+                ("taps_h", ctypes.c_int32), ("taps_w", ctypes.c_int32),
+                ("table_h", ctypes.c_int32), ("table_w", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
+                ("group_h", ctypes.c_int32), ("group_w", ctypes.c_int32),
+                ("span_h", ctypes.c_int32), ("span_w", ctypes.c_int32),
+                ("scratch_bytes", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_lib.rs_plan_create.restype = ctypes.c_int
+_lib.rs_plan_create.argtypes = [ctypes.POINTER(rs_plan_desc), _vp, ctypes.POINTER(_vp)]
+_lib.rs_resample.restype = ctypes.c_int
+_lib.rs_resample.argtypes = [_vp, _vp, _vp, _vp]
+_lib.rs_plan_recompute.restype = ctypes.c_int
+_lib.rs_plan_recompute.argtypes = [_vp, _vp]
+_lib.rs_destroy.restype = ctypes.c_int
+_lib.rs_destroy.argtypes = [_vp]
+_lib.rs_plan_get_info.restype = ctypes.c_int
+_lib.rs_plan_get_info.argtypes = [_vp, ctypes.POINTER(rs_plan_info)]
+_lib.rs_plan_get_tables.restype = ctypes.c_int
+_lib.rs_plan_get_tables.argtypes = [_vp, ctypes.c_int, _i32p, _i32p, _i32p, _dp, _dp]
+_lib.rs_plan_check.restype = ctypes.c_int
+_lib.rs_plan_check.argtypes = [_vp]
+_lib.rs_status_string.restype = ctypes.c_char_p
+_lib.rs_status_string.argtypes = [ctypes.c_int]
+_lib.rs_last_error.restype = ctypes.c_char_p
+_lib.rs_last_error.argtypes = []
+_lib.rs_version.restype = ctypes.c_int32
+_lib.rs_version.argtypes = []
+
+# Every symbol include/rs.h declares (checked by the CPU test suite).
+EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
+           "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version"]
+
+
+class RSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = "%s: %s (%s)" % (where, rs_status_string(status), rs_last_error())
+        super().__init__(msg)
+
+
+def _check(status: int, where: str):
+    if status != RS_OK:
+        raise RSError(status, where)
+
+
+def rs_status_string(status: int) -> str:
+    return _lib.rs_status_string(int(status)).decode()
+
+
+def rs_last_error() -> str:
+    return _lib.rs_last_error().decode()
+
+
+def rs_version() -> int:
+    return int(_lib.rs_version())
+
+
+def rs_plan_create(desc: rs_plan_desc, stream: int = 0) -> int:
+    """Returns the plan handle (an integer); raises RSError on failure."""
+    h = _vp()
+    _check(_lib.rs_plan_create(ctypes.byref(desc), _vp(stream), ctypes.byref(h)), "rs_plan_create")
+    return h.value
+
+
+def rs_resample(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(_lib.rs_resample(_vp(plan), _vp(d_in), _vp(d_out), _vp(stream)), "rs_resample")
+
+
+def rs_plan_recompute(plan: int, stream: int = 0) -> None:
+    _check(_lib.rs_plan_recompute(_vp(plan), _vp(stream)), "rs_plan_recompute")
+
+
+def rs_destroy(plan: int) -> None:
+    _check(_lib.rs_destroy(_vp(plan)), "rs_destroy")
+
+
+def rs_plan_get_info(plan: int) -> rs_plan_info:
+    info = rs_plan_info()
+    _check(_lib.rs_plan_get_info(_vp(plan), ctypes.byref(info)), "rs_plan_get_info")
+    return info
+
+
+def rs_plan_get_tables(plan: int, axis: int):
+    """(jlo, count, start, w64, wwork) numpy arrays of one axis (0 rows, 1 columns)."""
+    import numpy as np
+
+    info = rs_plan_get_info(plan)
+    n = info.out_h if axis == 0 else info.out_w
+    t = info.table_h if axis == 0 else info.table_w
+    jlo = np.empty(n, np.int32)
+    cnt = np.empty(n, np.int32)
+    start = np.empty(n, np.int32)
+    w64 = np.empty((n, t), np.float64)
+    ww = np.empty((n, t), np.float64)
+    _check(_lib.rs_plan_get_tables(_vp(plan), axis, jlo.ctypes.data_as(_i32p), cnt.ctypes.data_as(_i32p),
+                                   start.ctypes.data_as(_i32p), w64.ctypes.data_as(_dp),
+                                   ww.ctypes.data_as(_dp)), "rs_plan_get_tables")
+    return jlo, cnt, start, w64, ww
+
+
+def rs_plan_check(plan: int) -> None:
+    _check(_lib.rs_plan_check(_vp(plan)), "rs_plan_check")
+
+
+def out_size(n: int, scale: float) -> int:
+    """Output length the library derives from a scale: max(1, floor(n s + 1/2))."""
+    return max(1, int(math.floor(n * scale + 0.5)))
+
+
+# ------------------------------------------------------------ torch helper
+def _torch_dtype_code(dt):
+    import torch
+
+    table = {torch.float64: RS_F64, torch.float32: RS_F32, torch.float16: RS_F16,
+             torch.bfloat16: RS_BF16}
+    if dt not in table:
+        raise TypeError("unsupported dtype %s" % dt)
+    return table[dt]
+
+
+def make_desc(in_h, in_w, channels, out_h=0, out_w=0, scale_h=0.0, scale_w=0.0, kernel="lanczos",
+              param=None, boundary="mirror", dtype=RS_F32, flags=0, in_row_stride=0,
+              out_row_stride=0) -> rs_plan_desc:
+    if param is None:
+        param = DEFAULT_PARAM[kernel]
+    if not isinstance(dtype, int):
+        dtype = _torch_dtype_code(dtype)
+    return rs_plan_desc(int(in_h), int(in_w), int(channels), int(out_h), int(out_w), float(scale_h),
+                        float(scale_w), KERNELS[kernel], float(param), BOUNDARIES[boundary],
+                        int(dtype), int(dtype), int(flags), int(in_row_stride), int(out_row_stride))
+
+
+class Plan:
+    """One resampling plan on the current CUDA device.
+
+    >>> p = Plan(4096, 4096, 3, scale=1.37, kernel="lanczos", boundary="mirror")
+    >>> y = p(x)          # x: (4096, 4096, 3) float32 CUDA tensor
+    """
+
+    def __init__(self, in_h, in_w, channels=1, out_h=0, out_w=0, scale=None, scale_h=None,
+                 scale_w=None, kernel="lanczos", param=None, boundary="mirror", dtype=None,
+                 flags=0, stream=None):
+        import torch
+
+        if dtype is None:
+            dtype = torch.float32
+        self.torch_dtype = dtype
+        sh = scale_h if scale_h is not None else (scale if scale is not None else 0.0)
+        sw = scale_w if scale_w is not None else (scale if scale is not None else 0.0)
+        self.desc = make_desc(in_h, in_w, channels, out_h, out_w, sh, sw, kernel, param, boundary,
+                              _torch_dtype_code(dtype), flags)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = rs_plan_create(self.desc, s.cuda_stream)
+        self.info = rs_plan_get_info(self.handle)
+        self.in_shape = (int(in_h), int(in_w), int(channels))
+        self.out_shape = (self.info.out_h, self.info.out_w, int(channels))
+
+    @property
+    def path(self) -> str:
+        return PATHS.get(self.info.path, str(self.info.path))
+
+    def __call__(self, x, out=None, stream=None):
+        import torch
+
+        if not (x.is_cuda and x.dtype == self.torch_dtype and x.is_contiguous()):
+            raise ValueError("input must be a contiguous CUDA tensor of dtype %s" % self.torch_dtype)
+        if x.numel() != self.in_shape[0] * self.in_shape[1] * self.in_shape[2]:
+            raise ValueError("input has %d elements, plan expects %s" % (x.numel(), self.in_shape))
+        if out is None:
+            out = torch.empty(self.out_shape, dtype=self.torch_dtype, device=x.device)
+        elif not (out.is_cuda and out.dtype == self.torch_dtype and out.is_contiguous()
+                  and out.numel() == self.out_shape[0] * self.out_shape[1] * self.out_shape[2]):
+            raise ValueError("bad output tensor")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rs_resample(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def recompute(self, stream=None):
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rs_plan_recompute(self.handle, s.cuda_stream)
+
+    def tables(self, axis: int):
+        return rs_plan_get_tables(self.handle, axis)
+
+    def check(self):
+        rs_plan_check(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

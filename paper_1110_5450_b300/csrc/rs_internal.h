@@ -1,0 +1,120 @@
+// rs_internal.h -- internal declarations of the B300 resampler library.
+// Not installed; the public interface is include/rs.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "rs.h"
+
+namespace rs {
+
+// Largest raw tap count per output the plan accepts (before boundary folding).
+constexpr int kMaxTaps = 256;
+// Largest side length: keeps every integer of the tap formula far below 2^63.
+constexpr int64_t kMaxSide = int64_t(1) << 22;
+
+// Geometry of one axis.  The kernel argument of raw tap j for output i is
+// x = ((2j+1) n_out - (2i+1) n_in) / D, and tap j belongs to output i iff the
+// numerator's magnitude is below R*D.
+struct AxisGeom {
+    int64_t n_in = 0, n_out = 0;
+    int64_t D = 0;     // 2 max(n_in, n_out), or 2 n_out without antialiasing
+    int64_t R = 0;     // kernel support radius
+    int32_t t_raw = 0; // bound on raw taps per output: ceil(R D / n_out)
+    int32_t t_eff = 0; // stored window width after boundary folding: min(t_raw, n_in)
+    int32_t kernel = 0;
+    int32_t boundary = 0;
+    double param = 0.0;
+};
+
+// Device tables of one axis.
+struct AxisTables {
+    int32_t *jlo = nullptr;   // [n_out] first raw tap
+    int32_t *cnt = nullptr;   // [n_out] raw tap count
+    int32_t *start = nullptr; // [n_out] first index of the folded window
+    double *w64 = nullptr;    // [n_out][t_eff] folded normalised FP64 weights
+    void *wwork = nullptr;    // [n_out][t_eff] working precision (float or double)
+    // Register band for the fused kernel: outputs are grouped G at a time;
+    // group g reads inputs [base[g], base[g] + J) with weights [g][r][j].
+    int32_t *band_base = nullptr; // [groups]
+    void *band_w = nullptr;       // [groups][G][J] working precision
+    int32_t G = 0, J = 0, groups = 0;
+};
+
+// Parameters of the weight-table kernel for one axis (passed by value).
+struct WeightArgs {
+    AxisGeom g;
+    AxisTables t;
+    int work_is_double; // working precision: 1 = FP64, 0 = FP32
+    int *err;           // device error word
+};
+
+// Weight-table kernel for both axes in one launch.
+cudaError_t launch_weights(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s);
+// Band tables for the fused kernel (both axes, one launch).
+cudaError_t launch_band(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s);
+
+// Element type code shared by the pass launchers.
+enum class Dt : int { F64 = RS_F64, F32 = RS_F32, F16 = RS_F16, BF16 = RS_BF16 };
+
+inline size_t dt_size(int d)
+{
+    return d == RS_F64 ? 8 : d == RS_F32 ? 4 : 2;
+}
+
+// Two-pass (H then V) path through an HBM intermediate of the accumulation type.
+struct TwoPassArgs {
+    const void *in;
+    void *out;
+    void *tmp; // [in_h][out_w * C] accumulation type
+    int64_t in_h, in_w, out_h, out_w, C;
+    int64_t in_stride, out_stride; // elements
+    int32_t *start_x, *start_y;
+    const void *w_x, *w_y; // working precision [n_out][t]
+    int32_t t_x, t_y;
+    int dtype; // rs_dtype (in == out)
+};
+cudaError_t launch_two_pass(const TwoPassArgs &a, cudaStream_t s);
+
+// Fused single-pass kernel (V then H inside one CTA, register bands).
+struct FusedArgs {
+    const void *in;
+    void *out;
+    int64_t in_h, in_w, out_h, out_w, C;
+    int64_t in_stride, out_stride; // elements
+    const int32_t *base_y, *base_x; // band bases
+    const void *band_y, *band_x;    // band weights [groups][G][J]
+    int32_t gy, jy, gx, jx;         // band shapes
+    int32_t tile_h, tile_w;         // output tile (multiples of gy, gx)
+    int32_t box_h, box_w;           // staged input tile (rows, samples) upper bounds
+    int32_t tiles_y, tiles_x;
+    int dtype;
+    int use_tma;
+    void *tmap; // device-resident or by-value CUtensorMap (128 B), when use_tma
+    int *err;
+};
+
+struct FusedChoice {
+    int gy = 0, jy = 0, gx = 0, jx = 0; // band shapes (instantiated set)
+    int tile_h = 0, tile_w = 0;
+    int threads = 0;
+    size_t smem = 0;
+    int ctas_per_sm = 0;
+};
+
+// Returns false when no instantiated variant fits (dtype, C, G, J).
+bool fused_supported(int dtype, int C, int g, int j);
+// Instantiated band widths for a group size (ascending); used to round up J.
+int fused_round_j(int g, int j);
+cudaError_t launch_fused(const FusedArgs &a, const FusedChoice &c, cudaStream_t s, int num_sms);
+size_t fused_smem_bytes(const FusedArgs &a, const FusedChoice &c);
+
+// Thread-local last-error string.
+void set_error(const std::string &msg);
+
+} // namespace rs

@@ -13,3 +13,15 @@ for p in (_ROOT, _TESTS):
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def load_build_module():
+    """The library's build script, loaded by path (importing the package
+    itself requires the built library)."""
+    import importlib.util
+
+    path = os.path.join(_ROOT, "paper_1110_5450_b300", "build.py")
+    spec = importlib.util.spec_from_file_location("rs_build_script", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
