@@ -172,6 +172,30 @@ RS_API rs_status rs_plan_get_info(const rs_plan *plan, rs_plan_info *info);
 RS_API rs_status rs_plan_get_tables(const rs_plan *plan, int axis, int32_t *h_jlo, int32_t *h_count,
                              int32_t *h_start, double *h_w64, double *h_wwork);
 
+/* Allocation-free resample.  For callers that cannot call cudaMalloc -- a
+ * plug-in inside an application whose own allocator owns the device memory, or
+ * a real-time loop that may not pay for cudaMalloc/cudaFree (cudaFree
+ * synchronises the whole device).  The paper has no counterpart of this entry
+ * point; it is a deployment convenience.
+ *
+ * Same descriptor and buffers as rs_plan_create + rs_resample, but no plan:
+ * each call computes the weight tables and runs the separate H-then-V pass
+ * kernels with the tables and the intermediate placed in one library-owned
+ * static device array of RS_STATIC_SCRATCH_BYTES (32 MiB), which every GPU
+ * that loads the library holds until the process exits.  No cudaMalloc,
+ * cudaFree or other allocating call is made.  A request whose tables plus
+ * intermediate (in_h * out_w * channels * 4 bytes, 8 for RS_F64) exceed the
+ * array returns RS_ERR_BUDGET with the sizes in rs_last_error().
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array and it keeps the previous call's
+ * contents; calls whose GPU work overlaps (different streams or host threads)
+ * race on it, so issue them on one stream.  Asynchronous on `stream`; device
+ * errors of the table kernel are not reported by this entry point. */
+#define RS_STATIC_SCRATCH_BYTES (32u << 20)
+RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in, void *d_out, void *stream);
+
 /* Synchronise the device and report any device-side error word the plan's
  * kernels set (RS_CHECK builds and bounded waits); clears the word. */
 RS_API rs_status rs_plan_check(rs_plan *plan);

@@ -86,10 +86,14 @@ _lib.rs_last_error.restype = ctypes.c_char_p
 _lib.rs_last_error.argtypes = []
 _lib.rs_version.restype = ctypes.c_int32
 _lib.rs_version.argtypes = []
+_lib.rs_resample_noalloc.restype = ctypes.c_int
+_lib.rs_resample_noalloc.argtypes = [ctypes.POINTER(rs_plan_desc), _vp, _vp, _vp]
+RS_STATIC_SCRATCH_BYTES = 32 << 20
 
 # Every symbol include/rs.h declares (checked by the CPU test suite).
 EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
-           "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version"]
+           "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version",
+           "rs_resample_noalloc"]
 
 
 class RSError(RuntimeError):
@@ -125,6 +129,13 @@ def rs_plan_create(desc: rs_plan_desc, stream: int = 0) -> int:
 
 def rs_resample(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
     _check(_lib.rs_resample(_vp(plan), _vp(d_in), _vp(d_out), _vp(stream)), "rs_resample")
+
+
+def rs_resample_noalloc(desc: rs_plan_desc, d_in: int, d_out: int, stream: int = 0) -> None:
+    """Allocation-free resample through the library's static device scratch
+    (for callers that cannot allocate device memory; see include/rs.h)."""
+    _check(_lib.rs_resample_noalloc(ctypes.byref(desc), _vp(d_in), _vp(d_out), _vp(stream)),
+           "rs_resample_noalloc")
 
 
 def rs_plan_recompute(plan: int, stream: int = 0) -> None:
