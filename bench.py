@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "output Mpixel/s, 4096x4096x3 FP32 Lanczos-3 mirror, x1.37 + x0.3 (antialiased)"
 UNIT = "Mpixel/s"
-SCALES = (1.37, 0.3)
+SCALES = [1.37, 0.3]
 N_IN = 4096
 C = 3
 
@@ -51,7 +51,16 @@ def parse():
                     help="target seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-tune", action="store_true", help="keep the model-chosen kernel configuration")
+    ap.add_argument("--size", type=int, default=4096,
+                    help="input side (profiling runs only; the benchmark workload is 4096)")
+    ap.add_argument("--scales", type=str, default="1.37,0.3",
+                    help="comma-separated scales (profiling runs only)")
+    a = ap.parse_args()
+    global N_IN, SCALES
+    N_IN = a.size
+    SCALES = [float(v) for v in a.scales.split(",")]
+    return a
 
 
 def dist_info():
@@ -151,22 +160,28 @@ def cpu_baseline(img, budget_s: float):
     scales sized to about ``budget_s`` seconds; returns (Mpixel/s, cores, text)."""
     import oracle
 
+    import numpy as np
+
     o = oracle.default()
     outs = out_sizes()
-    # calibrate on 8 rows of each scale, then size each band to its share of the budget
-    rates = []
-    for s, n in zip(SCALES, outs):
-        t0 = time.perf_counter()
-        o.resample(img, n, n, "lanczos", "mirror", param=3.0, rows=(0, 8))
-        rates.append(8 / max(time.perf_counter() - t0, 1e-6))  # rows/s
+    img = np.ascontiguousarray(img, dtype=np.float64)  # exact upcast, once, outside the timing
+    # grow a central band of output rows per scale until it has taken its
+    # share of the budget (per-call set-up makes tiny samples unrepresentative)
     total_px = sum(n * n for n in outs)
-    rows = [max(8, min(n, int(budget_s * (n * n) / total_px * r))) for n, r in zip(outs, rates)]
-    full_s, dt = 0.0, 0.0
-    for (n, k) in zip(outs, rows):
-        y0 = (n - k) // 2
-        t0 = time.perf_counter()
-        o.resample(img, n, n, "lanczos", "mirror", param=3.0, rows=(y0, y0 + k))
-        t = time.perf_counter() - t0
+    full_s, dt, rows = 0.0, 0.0, []
+    for n in outs:
+        share = budget_s * (n * n) / total_px
+        k = 16
+        while True:
+            k = min(k, n)
+            y0 = (n - k) // 2
+            t0 = time.perf_counter()
+            o.resample(img, n, n, "lanczos", "mirror", param=3.0, rows=(y0, y0 + k))
+            t = time.perf_counter() - t0
+            if t >= 0.5 * share or k == n:
+                break
+            k = int(k * min(8.0, max(2.0, share / max(t, 1e-3))))
+        rows.append(k)
         dt += t
         full_s += t * (n / k)  # seconds for all n rows at the sampled rate
     value = total_px / full_s / 1e6
@@ -232,6 +247,13 @@ def main():
                          dtype=torch.float32, stream=stream) for s in SCALES]
         ys = [torch.empty(p.out_shape, dtype=torch.float32, device=dev) for p in plans]
     torch.cuda.synchronize()
+    # measured autotuning of each plan on its own buffers (outside the timed region)
+    t_tune = time.perf_counter()
+    if not args.no_tune:
+        for p, y in zip(plans, ys):
+            p.autotune(x, out=y, stream=stream)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t_tune
     # our kernels per step and plan: weight tables (+ band tables on the fused
     # path) and the resample (one fused kernel, or the H and V kernels)
     launches_per_step = sum(3 for p in plans)
@@ -323,7 +345,6 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        info = plans[0].info
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -331,10 +352,14 @@ def main():
             "config": {"workload": "C2 4096x4096x3 FP32 sinusoids+noise, Lanczos-3 mirror, x1.37 and x0.3",
                        "outputs": ["%dx%dx%d" % (n, n, C) for n in outs],
                        "step": "weight-table kernels + resample, both scales",
+                       "autotune_s": round(t_tune, 3),
                        "l2": "input 201 MB > 126 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "path_x1.37": rs.PATHS[info.path], "tile": [info.tile_h, info.tile_w],
-                       "band": [info.group_h, info.span_h], "path_x0.3": rs.PATHS[plans[1].info.path]},
+                       "plans": {str(sc): {"path": rs.PATHS[pl.info.path], "tile": [pl.info.tile_h, pl.info.tile_w],
+                                           "group": pl.info.group_h, "band": pl.info.span_h,
+                                           "warps_pass1": pl.info.warps_pass1, "stages": pl.info.stages,
+                                           "smem": pl.info.smem_bytes, "ctas_per_sm": pl.info.ctas_per_sm}
+                                 for sc, pl in zip(SCALES, plans)}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(),
                          "kernel": "fused resample x1.37", "algorithmic_bytes": alg,

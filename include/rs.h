@@ -142,6 +142,18 @@ RS_API rs_status rs_resample(rs_plan *plan, const void *d_in, void *d_out, void 
  * bit; it exists so that a timed step can include the table computation. */
 RS_API rs_status rs_plan_recompute(rs_plan *plan, void *stream);
 
+/* Measured autotuning of the fused path (the kernel tile shape, outputs per
+ * thread group, staged-buffer count and the split of warps between the two
+ * pipelined passes): times candidate configurations on the caller's buffers
+ * (d_in / d_out as for rs_resample; d_out is overwritten) and keeps the
+ * fastest for this plan.  Synchronises `stream`; allocates and frees band
+ * tables while it runs.  cache_path (may be NULL) names a JSON-lines file of
+ * earlier results keyed by device, dtype, channels, kernel, boundary and
+ * geometry; a hit applies the cached choice without timing, a miss appends
+ * the new result.  Plans on the two-pass path return RS_OK unchanged. */
+RS_API rs_status rs_plan_autotune(rs_plan *plan, const void *d_in, void *d_out, void *stream,
+                                  const char *cache_path);
+
 /* Free a plan after waiting for its work to finish.  NULL is accepted. */
 RS_API rs_status rs_destroy(rs_plan *plan);
 
@@ -153,7 +165,11 @@ typedef struct {
     int32_t path;             /* 0 = fused SIMT, 1 = two-pass SIMT, 2 = tcgen05    */
     int32_t tile_h, tile_w;   /* output tile of the chosen pass kernel            */
     int32_t group_h, group_w; /* outputs per thread group along each axis         */
-    int32_t span_h, span_w;   /* register band width (inputs per group)           */
+    int32_t span_h, span_w;   /* band width (inputs per group)                    */
+    int32_t warps_pass1;      /* fused path: warps on staging + vertical pass      */
+    int32_t stages;           /* fused path: staged input buffers (TMA)           */
+    int32_t smem_bytes;       /* fused path: dynamic shared memory per CTA        */
+    int32_t ctas_per_sm;      /* fused path: resident CTAs per SM                 */
     int64_t scratch_bytes;    /* device bytes owned by the plan                   */
 } rs_plan_info;
 

@@ -59,6 +59,8 @@ class rs_plan_info(ctypes.Structure):
                 ("path", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("group_h", ctypes.c_int32), ("group_w", ctypes.c_int32),
                 ("span_h", ctypes.c_int32), ("span_w", ctypes.c_int32),
+                ("warps_pass1", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64)]
 
 
@@ -86,6 +88,8 @@ _lib.rs_last_error.restype = ctypes.c_char_p
 _lib.rs_last_error.argtypes = []
 _lib.rs_version.restype = ctypes.c_int32
 _lib.rs_version.argtypes = []
+_lib.rs_plan_autotune.restype = ctypes.c_int
+_lib.rs_plan_autotune.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_char_p]
 _lib.rs_resample_noalloc.restype = ctypes.c_int
 _lib.rs_resample_noalloc.argtypes = [ctypes.POINTER(rs_plan_desc), _vp, _vp, _vp]
 RS_STATIC_SCRATCH_BYTES = 32 << 20
@@ -93,7 +97,7 @@ RS_STATIC_SCRATCH_BYTES = 32 << 20
 # Every symbol include/rs.h declares (checked by the CPU test suite).
 EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
            "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version",
-           "rs_resample_noalloc"]
+           "rs_resample_noalloc", "rs_plan_autotune"]
 
 
 class RSError(RuntimeError):
@@ -136,6 +140,12 @@ def rs_resample_noalloc(desc: rs_plan_desc, d_in: int, d_out: int, stream: int =
     (for callers that cannot allocate device memory; see include/rs.h)."""
     _check(_lib.rs_resample_noalloc(ctypes.byref(desc), _vp(d_in), _vp(d_out), _vp(stream)),
            "rs_resample_noalloc")
+
+
+def rs_plan_autotune(plan: int, d_in: int, d_out: int, stream: int = 0, cache_path=None) -> None:
+    """Measured autotuning of the fused path on the caller's buffers."""
+    cp = None if cache_path is None else os.fsencode(cache_path)
+    _check(_lib.rs_plan_autotune(_vp(plan), _vp(d_in), _vp(d_out), _vp(stream), cp), "rs_plan_autotune")
 
 
 def rs_plan_recompute(plan: int, stream: int = 0) -> None:
@@ -245,6 +255,17 @@ class Plan:
             raise ValueError("bad output tensor")
         s = stream if stream is not None else torch.cuda.current_stream()
         rs_resample(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def autotune(self, x, out=None, stream=None, cache_path=None):
+        """Time candidate kernel configurations on (x, out) and keep the fastest."""
+        import torch
+
+        if out is None:
+            out = torch.empty(self.out_shape, dtype=self.torch_dtype, device=x.device)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rs_plan_autotune(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream, cache_path)
+        self.info = rs_plan_get_info(self.handle)
         return out
 
     def recompute(self, stream=None):

@@ -30,7 +30,7 @@ const Variant *variants_bf16(int *n);
 
 namespace {
 
-const fused::Variant *find_variant(int dtype, int C, int G, int J)
+const fused::Variant *find_variant(int dtype, int C, int G)
 {
     int n = 0;
     const fused::Variant *v = nullptr;
@@ -42,26 +42,8 @@ const fused::Variant *find_variant(int dtype, int C, int G, int J)
     default: return nullptr;
     }
     for (int i = 0; i < n; ++i)
-        if (v[i].C == C && v[i].G == G && v[i].J == J) return &v[i];
+        if (v[i].C == C && v[i].G == G) return &v[i];
     return nullptr;
-}
-
-// Smallest instantiated band width >= j for (dtype, C, G); 0 if none.
-int round_band(int dtype, int C, int G, int j)
-{
-    int n = 0;
-    const fused::Variant *v = nullptr;
-    switch (dtype) {
-    case RS_F64: v = fused::variants_f64(&n); break;
-    case RS_F32: v = fused::variants_f32(&n); break;
-    case RS_F16: v = fused::variants_f16(&n); break;
-    case RS_BF16: v = fused::variants_bf16(&n); break;
-    default: return 0;
-    }
-    int best = 0;
-    for (int i = 0; i < n; ++i)
-        if (v[i].C == C && v[i].G == G && v[i].J >= j && (best == 0 || v[i].J < best)) best = v[i].J;
-    return best;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -116,6 +98,12 @@ struct Carver {
     }
 };
 
+struct Candidate {
+    int G = 0, J = 0, tile_h = 0, tile_w = 0, stages = 1, box_h = 0, box_w = 0, n_sub = 1, sub_h = 0, n1 = 4;
+    size_t smem = 0;
+    double cost = 0.0; // modelled SM cycles per output pixel
+};
+
 } // namespace
 } // namespace rs
 
@@ -137,10 +125,13 @@ struct rs_plan {
     int G = 0, J = 0;
     size_t smem = 0;
     int grid = 0;
+    int ctas_per_sm = 0;
     int tma_ok = 0;
     CUtensorMap tmap;
     const void *tmap_ptr = nullptr;
     int64_t scratch_bytes = 0;
+    std::vector<int32_t> host_start_y, host_start_x; // for re-planning and tuning
+    Candidate chosen;                                // fused configuration in use
 };
 
 namespace {
@@ -237,6 +228,21 @@ int tile_extent(const std::vector<int32_t> &base, int groups_per_tile, int J, in
     return need;
 }
 
+// Group bases as the band kernel computes them (used here only to size
+// candidate tiles; the kernel's own bases are read back and re-checked).
+std::vector<int32_t> group_bases(const std::vector<int32_t> &start, int G, int J, int64_t n_in, int t_eff)
+{
+    const int n = int(start.size());
+    std::vector<int32_t> b((n + G - 1) / G);
+    for (int g = 0; g < int(b.size()); ++g) {
+        int64_t b0 = n_in;
+        for (int r = 0; r < G && g * G + r < n; ++r) b0 = std::min<int64_t>(b0, start[g * G + r]);
+        b[g] = int32_t(n_in >= J ? std::min<int64_t>(b0, n_in - J) : 0);
+    }
+    (void)t_eff;
+    return b;
+}
+
 // Rows per TMA box when a tile's staged rows need n_sub boxes (<= 256 rows
 // each).  With several boxes the height is a multiple of 8 rows so that each
 // box's shared-memory destination stays 128-byte aligned (a row is a multiple
@@ -248,49 +254,71 @@ int sub_height(int rows, int n_sub)
     return (h + 7) / 8 * 8;
 }
 
-rs_status choose_fused(rs_plan *p, cudaStream_t stream)
+
+// Cost model of one candidate (SM cycles per output pixel, lower is better).
+// Per tile: instruction estimates of the two passes (FMA + shared loads per
+// tap, plus a fixed tail per warp task).  The pipelined CTA runs pass 1 on n1
+// warps and pass 2 on the rest, so its tile time is the slower group's
+// critical path; k resident CTAs overlap their tiles, but the SM cannot issue
+// more than 4 instructions per cycle nor fill shared memory from L2 faster
+// than ~64 B per cycle.  Also picks the warp split n1.
+double model_cost(Candidate &c, int C, size_t esz, size_t asz, int V)
+{
+    const int ngy = c.tile_h / c.G, ngx = c.tile_w / c.G;
+    const int w1 = (c.box_w + 32 * V - 1) / (32 * V) * (32 * V);
+    const int nchunk = w1 / (32 * V);
+    const int rb = std::min(32, c.tile_h);
+    const int t1 = ngy * nchunk;
+    const int t2 = ((c.tile_h + rb - 1) / rb) * ((ngx + 32 / rb - 1) / (32 / rb));
+    const int W = fused::kWarps;
+    const double task1 = c.J * (double(c.G * V) + 1.0 + V + 2.0) + 24.0 + c.G * V;
+    const double task2 = c.J * (double(c.G * C) + 1.0 + C + 2.0) + 24.0 + C * c.G;
+    const double issue = (t1 * task1 + t2 * task2 + 200.0) / 4.0 * 1.25;
+    const double fill = (double(c.box_h) * c.box_w * esz + double(ngy + ngx) * band_stride(c.G, c.J) * asz) / 64.0;
+    const int ctas = int(std::min<size_t>(8, (227 * 1024) / std::max<size_t>(c.smem, 1)));
+    double best = 1e300;
+    for (int n1 = 1; n1 < W; ++n1) {
+        const double crit = std::max(std::ceil(double(t1) / n1) * task1, std::ceil(double(t2) / (W - n1)) * task2);
+        const double per_tile = std::max(std::max(issue, fill), crit * 2.0 / std::max(1, ctas));
+        if (per_tile < best) {
+            best = per_tile;
+            c.n1 = n1;
+        }
+    }
+    return best / (double(c.tile_h) * c.tile_w);
+}
+
+// Builds the band tables for a chosen candidate and fills the kernel
+// parameters (shared by the model-based choice and the autotuner).
+rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool tma_layout)
 {
     const rs_plan_desc &d = p->desc;
     const int C = d.channels;
     const int dt = d.in_dtype;
-    // start tables back to the host (plan creation synchronises once)
-    std::vector<int32_t> sy(p->gy.n_out), sx(p->gx.n_out);
-    cudaError_t e = cudaMemcpyAsync(sy.data(), p->ty.start, sy.size() * 4, cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sx.data(), p->tx.start, sx.size() * 4, cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return cuda_fail(e, "reading weight tables");
-
-    int G = 0, J = 0;
-    const int limit[3][2] = {{4, 32}, {2, 48}, {1, 64}};
-    for (auto &gl : limit) {
-        const int g = gl[0];
-        const int need = std::max(band_needed(sy, g, p->gy.t_eff), band_needed(sx, g, p->gx.t_eff));
-        if (need > gl[1]) continue;
-        const int j = round_band(dt, C, g, need);
-        if (j == 0) continue;
-        G = g;
-        J = j;
-        break;
-    }
-    if (G == 0) return RS_ERR_UNSUPPORTED;
-    p->variant = find_variant(dt, C, G, J);
+    const size_t esz = dt_size(dt);
+    const size_t asz = p->work_double ? 8 : 4;
+    const int vec = int(16 / esz);
+    p->variant = find_variant(dt, C, c.G);
     if (!p->variant) return RS_ERR_UNSUPPORTED;
-    p->G = G;
-    p->J = J;
-
-    // band tables
-    const size_t wsz = p->work_double ? 8 : 4;
-    p->ty.G = p->tx.G = G;
-    p->ty.J = p->tx.J = J;
-    p->ty.groups = int32_t((p->gy.n_out + G - 1) / G);
-    p->tx.groups = int32_t((p->gx.n_out + G - 1) / G);
+    // the tensor map encodes the box size: a new configuration needs a new map
+    p->tmap_ptr = nullptr;
+    p->G = c.G;
+    p->J = c.J;
+    const int js = band_stride(c.G, c.J);
+    p->ty.G = p->tx.G = c.G;
+    p->ty.J = p->tx.J = c.J;
+    p->ty.groups = int32_t((p->gy.n_out + c.G - 1) / c.G);
+    p->tx.groups = int32_t((p->gx.n_out + c.G - 1) / c.G);
     Carver cv;
     const size_t o_by = cv.take(size_t(p->ty.groups) * 4);
     const size_t o_bx = cv.take(size_t(p->tx.groups) * 4);
-    const size_t o_wy = cv.take(size_t(p->ty.groups) * G * J * wsz);
-    const size_t o_wx = cv.take(size_t(p->tx.groups) * G * J * wsz);
-    e = cudaMalloc(&p->bands.p, cv.off);
+    const size_t o_wy = cv.take(size_t(p->ty.groups) * js * asz);
+    const size_t o_wx = cv.take(size_t(p->tx.groups) * js * asz);
+    if (p->bands.p) {
+        cudaFree(p->bands.p);
+        p->bands.p = nullptr;
+    }
+    cudaError_t e = cudaMalloc(&p->bands.p, cv.off);
     if (e != cudaSuccess) return cuda_fail(e, "allocating band tables");
     p->bands.n = cv.off;
     char *base = static_cast<char *>(p->bands.p);
@@ -307,39 +335,10 @@ rs_status choose_fused(rs_plan *p, cudaStream_t stream)
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "reading band tables");
 
-    // tiles
-    const size_t esz = dt_size(dt);
-    const size_t asz = p->work_double ? 8 : 4;
-    const int vec = int(16 / esz);
-    const int tile_h = int(std::min<int64_t>(32, ((p->gy.n_out + G - 1) / G) * G));
-    const int tile_h_g = std::max(G, tile_h - tile_h % G);
-    const int rows = tile_extent(by, tile_h_g / G, J, 1, 1);
-    const bool tma_layout = ((d.in_row_stride * int64_t(esz)) % 16) == 0 && encode_fn() != nullptr;
-    const size_t smem_cap = 227 * 1024;
-    int best_tw = 0, best_stages = 1, best_bw = 0;
-    // widest tile whose staged row fits a 256-element TMA box; prefer two stages
-    for (int stages = 2; stages >= 1 && best_tw == 0; --stages) {
-        for (int ngx = 32; ngx >= 1; --ngx) {
-            const int tw = ngx * G;
-            if (tw > std::max<int64_t>(G, ((p->gx.n_out + G - 1) / G) * G) && ngx > 1) continue;
-            const int bw_need = tile_extent(bx, ngx, J, C, vec);
-            const int bw = (bw_need + vec - 1) / vec * vec;
-            if (bw > 256) continue;
-            const int pt = bw | 1;
-            const int n_sub = (rows + 255) / 256;
-            const int sub_h = sub_height(rows, n_sub);
-            const size_t sm = fused::smem_bytes(esz, asz, n_sub * sub_h, bw, tile_h_g, pt, stages);
-            const size_t per_sm_target = stages == 2 ? smem_cap / 2 : smem_cap;
-            if (sm > per_sm_target) continue;
-            if (tw > 64 * (C == 1 ? 2 : 1)) continue;
-            best_tw = tw;
-            best_stages = stages;
-            best_bw = bw;
-            break;
-        }
-    }
-    if (best_tw == 0) return RS_ERR_UNSUPPORTED;
-
+    // exact staged extents from the kernel's own bases
+    const int ngy = c.tile_h / c.G, ngx = c.tile_w / c.G;
+    const int rows = tile_extent(by, ngy, c.J, 1, 1);
+    const int bw = (tile_extent(bx, ngx, c.J, C, vec) + vec - 1) / vec * vec;
     fused::Params &fp = p->fp;
     std::memset(&fp, 0, sizeof fp);
     fp.in_h = p->gy.n_in;
@@ -352,22 +351,33 @@ rs_status choose_fused(rs_plan *p, cudaStream_t stream)
     fp.base_x = p->tx.band_base;
     fp.band_y = p->ty.band_w;
     fp.band_x = p->tx.band_w;
-    fp.tile_h = tile_h_g;
-    fp.tile_w = best_tw;
+    fp.J = c.J;
+    fp.js = js;
+    fp.tile_h = c.tile_h;
+    fp.tile_w = c.tile_w;
     fp.n_sub = (rows + 255) / 256;
     fp.sub_h = sub_height(rows, fp.n_sub);
     fp.box_h = fp.n_sub * fp.sub_h;
-    fp.box_w = best_bw;
-    fp.pitch_t = best_bw | 1;
+    fp.box_w = bw;
+    const int V = p->variant->V;
+    fp.w1 = (bw + 32 * V - 1) / (32 * V) * (32 * V);
+    fp.pitch_t = fp.w1 | 1;
     fp.groups_y = p->ty.groups;
     fp.groups_x = p->tx.groups;
-    fp.tiles_y = int32_t((p->gy.n_out + tile_h_g - 1) / tile_h_g);
-    fp.tiles_x = int32_t((p->gx.n_out + best_tw - 1) / best_tw);
-    fp.stages = best_stages;
+    fp.tiles_y = int32_t((p->gy.n_out + c.tile_h - 1) / c.tile_h);
+    fp.tiles_x = int32_t((p->gx.n_out + c.tile_w - 1) / c.tile_w);
+    fp.stages = c.stages;
+    fp.n1 = c.n1;
     fp.err = p->d_err;
-    p->tma_ok = tma_layout ? 1 : 0;
-    p->smem = fused::smem_bytes(esz, asz, fp.box_h, fp.box_w, fp.tile_h, fp.pitch_t, p->tma_ok ? best_stages : 1);
-    e = cudaFuncSetAttribute(p->variant->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(p->smem));
+    p->tma_ok = (tma_layout && bw <= 256) ? 1 : 0;
+    p->smem = fused::layout(esz, asz, fp.box_h, fp.box_w, ngy, ngx, js, fp.tile_h, fp.pitch_t,
+                            p->tma_ok ? fp.stages : 1)
+                  .total;
+    if (p->smem > 227 * 1024) return RS_ERR_UNSUPPORTED;
+    // The limit is a property of the kernel function, shared by every plan that
+    // uses this variant, so opt in to the whole per-block maximum once rather
+    // than to this plan's size (occupancy follows the size passed at launch).
+    e = cudaFuncSetAttribute(p->variant->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "setting shared memory size");
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p->variant->fn, fused::kThreads, p->smem);
@@ -375,7 +385,94 @@ rs_status choose_fused(rs_plan *p, cudaStream_t stream)
     if (occ < 1) return RS_ERR_UNSUPPORTED;
     const int64_t tiles = int64_t(fp.tiles_y) * fp.tiles_x;
     p->grid = int(std::min<int64_t>(tiles, int64_t(occ) * p->num_sms));
+    p->ctas_per_sm = occ;
+    p->chosen = c;
     return RS_OK;
+}
+
+// Every feasible fused configuration of a plan (host start tables needed).
+std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout)
+{
+    const rs_plan_desc &d = p->desc;
+    const int C = d.channels;
+    const int dt = d.in_dtype;
+    const size_t esz = dt_size(dt);
+    const size_t asz = p->work_double ? 8 : 4;
+    const int vec = int(16 / esz);
+    const size_t smem_cap = 227 * 1024;
+    const std::vector<int32_t> &sy = p->host_start_y, &sx = p->host_start_x;
+    std::vector<Candidate> out;
+    for (int G : {4, 2, 1}) {
+        const fused::Variant *var = find_variant(dt, C, G);
+        if (!var) continue;
+        const int V = var->V;
+        const int J = std::max(band_needed(sy, G, p->gy.t_eff), band_needed(sx, G, p->gx.t_eff));
+        if (J > 256) continue;
+        const std::vector<int32_t> by = group_bases(sy, G, J, p->gy.n_in, p->gy.t_eff);
+        const std::vector<int32_t> bx = group_bases(sx, G, J, p->gx.n_in, p->gx.t_eff);
+        const int max_h = int(std::min<int64_t>(64, (p->gy.n_out + G - 1) / G * G));
+        for (int tile_h : {8, 16, 32, 64}) {
+            if (tile_h % G || tile_h / G > 32) continue;
+            if (tile_h > std::max(8, max_h) * 2 && tile_h > 8) continue;
+            const int rows = tile_extent(by, tile_h / G, J, 1, 1);
+            const int n_sub = (rows + 255) / 256;
+            const int sub_h = sub_height(rows, n_sub);
+            for (int ngx = 1; ngx <= 32; ++ngx) {
+                const int tile_w = ngx * G;
+                if (tile_w > ((p->gx.n_out + G - 1) / G) * G && ngx > 1) break;
+                const int bw = (tile_extent(bx, ngx, J, C, vec) + vec - 1) / vec * vec;
+                if (tma_layout && bw > 256) break;
+                if (bw > 4096) break;
+                for (int stages : {2, 1}) {
+                    if (stages == 2 && !tma_layout) continue;
+                    Candidate c;
+                    c.G = G;
+                    c.J = J;
+                    c.tile_h = tile_h;
+                    c.tile_w = tile_w;
+                    c.stages = stages;
+                    c.box_h = n_sub * sub_h;
+                    c.box_w = bw;
+                    c.n_sub = n_sub;
+                    c.sub_h = sub_h;
+                    const int w1 = (bw + 32 * V - 1) / (32 * V) * (32 * V);
+                    c.smem = fused::layout(esz, asz, c.box_h, bw, tile_h / G, ngx, band_stride(G, J), tile_h,
+                                           w1 | 1, stages)
+                                 .total;
+                    if (c.smem > smem_cap) continue;
+                    c.cost = model_cost(c, C, esz, asz, V);
+                    out.push_back(c);
+                }
+            }
+        }
+    }
+    return out;
+}
+
+bool tma_layout_ok(const rs_plan *p)
+{
+    return ((p->desc.in_row_stride * int64_t(dt_size(p->desc.in_dtype))) % 16) == 0 && encode_fn() != nullptr;
+}
+
+rs_status choose_fused(rs_plan *p, cudaStream_t stream)
+{
+    // start tables back to the host (plan creation synchronises once)
+    p->host_start_y.resize(p->gy.n_out);
+    p->host_start_x.resize(p->gx.n_out);
+    cudaError_t e = cudaMemcpyAsync(p->host_start_y.data(), p->ty.start, p->host_start_y.size() * 4,
+                                    cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->host_start_x.data(), p->tx.start, p->host_start_x.size() * 4,
+                            cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading weight tables");
+    const bool tma = tma_layout_ok(p);
+    const std::vector<Candidate> cands = enumerate_candidates(p, tma);
+    if (cands.empty()) return RS_ERR_UNSUPPORTED;
+    const Candidate *best = &cands[0];
+    for (const Candidate &c : cands)
+        if (c.cost < best->cost) best = &c;
+    return apply_fused(p, stream, *best, tma);
 }
 
 rs_status encode_map(rs_plan *p, const void *d_in)
@@ -405,6 +502,57 @@ rs_status encode_map(rs_plan *p, const void *d_in)
     p->tmap_ptr = d_in;
     return RS_OK;
 }
+
+// ---------------------------------------------------------------- autotuner
+
+std::string tune_key(const rs_plan *p)
+{
+    cudaDeviceProp prop;
+    std::string dev = "unknown";
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) dev = prop.name;
+    for (char &ch : dev)
+        if (ch == '"' || ch == '|') ch = '_';
+    const rs_plan_desc &d = p->desc;
+    char buf[320];
+    std::snprintf(buf, sizeof buf, "%s|v1|dt%d|c%d|k%d|p%.17g|b%d|f%u|%dx%d->%dx%d|is%lld", dev.c_str(), d.in_dtype,
+                  d.channels, d.kernel, d.param, d.boundary, d.flags & RS_NO_ANTIALIAS, d.in_h, d.in_w, d.out_h,
+                  d.out_w, (long long)d.in_row_stride);
+    return buf;
+}
+
+bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int *tw, int *st, int *n1)
+{
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    const std::string needle = "\"key\": \"" + key + "\"";
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        if (!std::strstr(line, needle.c_str())) continue;
+        const char *q = std::strstr(line, "\"G\":");
+        if (q && std::sscanf(q, "\"G\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, \"n1\": %d", G, th, tw,
+                             st, n1) == 5)
+            found = true; // the last matching line wins
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const Candidate &c, double us)
+{
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"G\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, \"n1\": %d, "
+                 "\"band\": %d, \"us\": %.3f}\n",
+                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us);
+    std::fclose(f);
+}
+
+// Mean launch time (µs) of the plan's current configuration.
+rs_status time_plan(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s, double *us);
 
 } // namespace
 
@@ -601,6 +749,76 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
     return RS_OK;
 }
 
+rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stream_v, const char *cache_path)
+{
+    if (!p || !d_in || !d_out) return fail(RS_ERR_INVALID_ARG, "NULL plan or buffer");
+    if (p->path != 0) return RS_OK; // only the fused path has choices to tune
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const bool tma = tma_layout_ok(p);
+    std::vector<Candidate> cands = enumerate_candidates(p, tma);
+    if (cands.empty()) return RS_OK;
+    const std::string key = tune_key(p);
+    int G, th, tw, st, n1;
+    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1)) {
+        for (const Candidate &c : cands)
+            if (c.G == G && c.tile_h == th && c.tile_w == tw && c.stages == st) {
+                Candidate k = c;
+                k.n1 = n1;
+                return apply_fused(p, stream, k, tma);
+            }
+    }
+    const Candidate before = p->chosen;
+    // Stage 1: per (G, tile_h, stages) the widest feasible tile and two
+    // narrower ones, warp split from the model.
+    std::vector<Candidate> trial;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        const Candidate &c = cands[i];
+        int widest = 0;
+        for (const Candidate &o : cands)
+            if (o.G == c.G && o.tile_h == c.tile_h && o.stages == c.stages) widest = std::max(widest, o.tile_w);
+        const int ng = widest / c.G;
+        const int a = std::max(1, (2 * ng + 2) / 3), b = std::max(1, (ng + 2) / 3);
+        const int g = c.tile_w / c.G;
+        if (g == ng || g == a || g == b) trial.push_back(c);
+    }
+    Candidate best = before;
+    double best_us = 1e300;
+    std::vector<std::pair<double, Candidate>> scored;
+    for (const Candidate &c : trial) {
+        rs_status s = apply_fused(p, stream, c, tma);
+        if (s != RS_OK) continue;
+        double us = 0;
+        s = time_plan(p, d_in, d_out, stream, &us);
+        if (s != RS_OK) return s;
+        scored.push_back({us, c});
+        if (us < best_us) {
+            best_us = us;
+            best = c;
+        }
+    }
+    // Stage 2: every warp split for the four fastest.
+    std::sort(scored.begin(), scored.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+    for (size_t r = 0; r < scored.size() && r < 4; ++r) {
+        for (int k1 = 1; k1 < fused::kWarps; ++k1) {
+            Candidate c = scored[r].second;
+            if (c.n1 == k1) continue;
+            c.n1 = k1;
+            if (apply_fused(p, stream, c, tma) != RS_OK) continue;
+            double us = 0;
+            rs_status s = time_plan(p, d_in, d_out, stream, &us);
+            if (s != RS_OK) return s;
+            if (us < best_us) {
+                best_us = us;
+                best = c;
+            }
+        }
+    }
+    rs_status s = apply_fused(p, stream, best, tma);
+    if (s != RS_OK) return s;
+    if (best_us < 1e299) cache_store(cache_path, key, best, best_us);
+    return RS_OK;
+}
+
 rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
 {
     if (!p) return fail(RS_ERR_INVALID_ARG, "NULL plan");
@@ -636,6 +854,10 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
         info->tile_w = p->fp.tile_w;
         info->group_h = info->group_w = p->G;
         info->span_h = info->span_w = p->J;
+        info->warps_pass1 = p->fp.n1;
+        info->stages = p->tma_ok ? p->fp.stages : 1;
+        info->smem_bytes = int32_t(p->smem);
+        info->ctas_per_sm = p->ctas_per_sm;
     }
     info->scratch_bytes = p->scratch_bytes;
     return RS_OK;
@@ -683,3 +905,44 @@ rs_status rs_plan_check(rs_plan *p)
 }
 
 } // extern "C"
+
+namespace {
+rs_status time_plan(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s, double *us)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cuda_fail(cudaGetLastError(), "event");
+    }
+    rs_status st = rs_resample(p, d_in, d_out, s); // warm-up
+    int reps = 3;
+    float ms = 0.f;
+    cudaError_t e = cudaSuccess;
+    for (int round = 0; st == RS_OK && round < 4; ++round) {
+        e = cudaEventRecord(a, s);
+        for (int r = 0; r < reps && st == RS_OK; ++r) st = rs_resample(p, d_in, d_out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) break;
+        if (ms > 0.3f) break; // long enough to trust
+        reps *= 4;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != RS_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "timing");
+    // a device-side error during tuning (bounds or a timed-out wait) disqualifies the run
+    int herr = 0;
+    e = cudaMemcpy(&herr, p->d_err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the error word");
+    if (herr) {
+        char buf[64];
+        std::snprintf(buf, sizeof buf, "device error word %d while tuning", herr);
+        return fail(RS_ERR_DEVICE, buf);
+    }
+    *us = 1000.0 * ms / reps;
+    return RS_OK;
+}
+} // namespace

@@ -1,27 +1,37 @@
 // rs_fused.cuh -- fused separable resampling kernel (one launch per image).
 //
 // A persistent CTA walks output tiles of tile_h x tile_w pixels.  For each
-// tile it stages the input rectangle the tile's taps touch in shared memory
-// (TMA 2-D tile copy, double-buffered behind an mbarrier, or plain coalesced
-// loads when the image's row pitch is not 16-byte aligned), then
+// tile it stages in shared memory
+//   * the input rectangle the tile's taps touch (TMA 2-D tile copy), and
+//   * the tile's weight bands of both axes (TMA 1-D bulk copies),
+// double-buffered behind one mbarrier per stage (or plain coalesced loads
+// when the image's row pitch rules TMA out), then computes
 //
-//   pass 1 (vertical):   tt[yo][s]  = sum_j Wy[yo][j] tin[by(yo) + j][s]
+//   pass 1 (vertical):   tt[yo][s]     = sum_j Wy[yo][j] tin[by(yo) + j][s]
 //   pass 2 (horizontal): out[yo][x][c] = sum_j Wx[x][j] tt[yo][(bx(x) + j) C + c]
 //
-// Weights come from "register bands": outputs are grouped G at a time along an
-// axis; a group reads the J consecutive inputs [base, base + J) and holds its
-// G x J weights (zeros outside each output's own taps) in registers, so one
-// shared-memory load feeds G fused multiply-adds.
+// The warps are specialised and pipelined: warps [0, n1) stage tiles and run
+// pass 1 of tile i into intermediate buffer i % 2, while warps [n1, 8) run
+// pass 2 of tile i - 1 from the other buffer.  The hand-off goes through
+// mbarriers (tt full / tt empty per buffer, bounded waits), so no CTA-wide
+// barrier separates the two passes.
 //
-// Shared-memory layout choices (bank conflicts):
-//   pass 1: lanes take consecutive samples of a row -> conflict-free for any
-//           pitch, so the TMA's dense box layout is read as it lands;
-//   pass 2: lanes take consecutive output ROWS of one group, so that every
-//           lane uses the same weights; the intermediate's pitch is odd (in
-//           words of the accumulation type) so the 32 rows hit 32 banks.
+// Weight bands: outputs are grouped G at a time along an axis; group g reads
+// the J consecutive inputs [base[g], base[g] + J) and stores its weights
+// j-major ([j][member]), zero outside each member's own taps, so one
+// shared-memory vector load gives the G weights of input j and one data load
+// feeds G fused multiply-adds (times V columns per thread in pass 1).
+//
+// Bank conflicts:
+//   pass 1: lanes take consecutive samples of a staged row -> conflict-free
+//           for any pitch, so the TMA's dense box layout is read as it lands;
+//   pass 2: lanes take consecutive output ROWS (weights warp-uniform); the
+//           intermediate's pitch is odd in accumulation words, so rows hit
+//           distinct banks.
 #pragma once
 
 #include <cuda.h>
+
 #include <climits>
 
 #include "rs_internal.h"
@@ -31,8 +41,8 @@ namespace fused {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kErrBounds = 201;   // a band would read outside the staged tile
-constexpr int kErrTimeout = 202;  // an mbarrier wait ran out
+constexpr int kErrBounds = 201;  // a band would read outside the staged tile
+constexpr int kErrTimeout = 202; // an mbarrier wait ran out
 
 template <typename A, typename T> __device__ __forceinline__ A to_acc(T v);
 template <> __device__ __forceinline__ float to_acc<float, float>(float v) { return v; }
@@ -114,6 +124,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void flag(int *err, int code)
 {
     if (err) atomicCAS(err, 0, code);
@@ -125,79 +145,139 @@ struct Params {
     int64_t in_h, in_w, out_h, out_w;
     int64_t in_stride, out_stride;
     const int32_t *base_y, *base_x;
-    const void *band_y, *band_x;
-    int32_t tile_h, tile_w;   // output tile
-    int32_t box_h, box_w;     // staged rows, staged samples (pitch of tin)
-    int32_t sub_h, n_sub;     // TMA box height and copies per tile
-    int32_t pitch_t;          // pitch of the intermediate (odd, accumulation words)
+    const void *band_y, *band_x; // [groups][js] accumulation type
+    int32_t J, js;               // band width (inputs per group) and group stride (elements)
+    int32_t tile_h, tile_w;      // output tile (multiples of G)
+    int32_t box_h, box_w;        // staged rows, staged samples (pitch of tin)
+    int32_t sub_h, n_sub;        // TMA box height and copies per tile
+    int32_t pitch_t;             // pitch of the intermediate (odd, >= the pass-1 width)
+    int32_t w1;                  // pass-1 width: box_w rounded up to 32*V columns
     int32_t tiles_y, tiles_x;
     int32_t groups_y, groups_x;
-    int use_tma;              // 1: TMA tile copies; 0: plain coalesced loads
-    int stages;               // staged input buffers (2 = prefetch next tile; TMA only)
+    int use_tma;                 // 1: TMA copies; 0: plain coalesced loads
+    int stages;                  // staged buffers (2 = prefetch the next tile; TMA only)
+    int n1;                      // warps running staging + pass 1 (the rest run pass 2)
     int *err;
 };
 
 struct TileInfo {
-    int32_t ry0;  // first staged input row
-    int32_t xs;   // first staged input sample (aligned)
-    int32_t rows; // rows actually needed
-    int32_t cols; // samples actually needed (from xs)
+    int32_t ry0;    // first staged input row
+    int32_t xs;     // first staged input sample (aligned down to 16 bytes)
+    int32_t nvy;    // valid y-groups in the tile
+    int32_t nvx;    // valid x-groups in the tile
+    int32_t rb[32]; // per y-group: first staged row of its band (base - ry0)
+    int32_t cb[32]; // per x-group: first staged sample of its band (base * C - xs)
 };
 
-// Compute the staged rectangle of tile t (called by one full warp).
-template <int C, int GY, int JY, int GX, int JX>
-__device__ __forceinline__ TileInfo tile_rect(const Params &p, int t, int vec)
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Loads G consecutive weights (16-byte aligned for G = 4 floats).
+template <typename A, int G> __device__ __forceinline__ void load_w(A (&w)[G], const A *p)
 {
-    const int ty = t / p.tiles_x, tx = t % p.tiles_x;
-    const int lane = threadIdx.x & 31;
-    const int gy0 = ty * (p.tile_h / GY), ngy = p.tile_h / GY;
-    const int gx0 = tx * (p.tile_w / GX), ngx = p.tile_w / GX;
-    int ylo = INT_MAX, yhi = INT_MIN, xlo = INT_MAX, xhi = INT_MIN;
-    if (lane < ngy && gy0 + lane < p.groups_y) {
-        const int b = __ldg(p.base_y + gy0 + lane);
-        ylo = b;
-        yhi = b;
-    }
-    if (lane < ngx && gx0 + lane < p.groups_x) {
-        const int b = __ldg(p.base_x + gx0 + lane);
-        xlo = b;
-        xhi = b;
-    }
+    if constexpr (G == 4 && sizeof(A) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+    } else if constexpr (G == 2 && sizeof(A) == 4) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        w[0] = v.x;
+        w[1] = v.y;
+    } else {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ylo = min(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
-        yhi = max(yhi, __shfl_xor_sync(0xffffffffu, yhi, o));
-        xlo = min(xlo, __shfl_xor_sync(0xffffffffu, xlo, o));
-        xhi = max(xhi, __shfl_xor_sync(0xffffffffu, xhi, o));
+        for (int g = 0; g < G; ++g) w[g] = p[g];
     }
-    TileInfo ti;
-    ti.ry0 = ylo;
-    ti.rows = yhi + JY - ylo;
-    const int s0 = xlo * C;
-    ti.xs = s0 - (s0 % vec);
-    ti.cols = (xhi + JX) * C - ti.xs;
-    return ti;
 }
 
-template <typename T, int C, int GY, int JY, int GX, int JX>
-__global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+// Pass-2 record of one intermediate buffer (written by the pass-1 warps).
+struct Rec2 {
+    int32_t ty, tx, nvx, pad;
+    int32_t cb[32];
+};
+
+__host__ __device__ inline size_t rec2_bytes(int ngx, int js, size_t acc)
+{
+    return align_up(sizeof(Rec2) + size_t(ngx) * js * acc, 128);
+}
+
+// Shared-memory layout: stages x (tin, wy, wx) | 2 x tt | 2 x (Rec2 + wx copy)
+// | 2 x TileInfo | 6 mbarriers | abort flag | read slack.
+struct Layout {
+    size_t tin, wy, wx, stage, tt, rec2, total;
+};
+
+__host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int box_w, int ngy, int ngx, int js,
+                                         int tile_h, int pitch_t, int nstage)
+{
+    Layout L;
+    L.tin = align_up(size_t(box_h) * box_w * elem, 128);
+    L.wy = align_up(size_t(ngy) * js * acc, 128);
+    L.wx = align_up(size_t(ngx) * js * acc, 128);
+    L.stage = L.tin + L.wy + L.wx;
+    L.tt = align_up(size_t(tile_h) * pitch_t * acc, 128);
+    L.rec2 = rec2_bytes(ngx, js, acc);
+    // + slack because the vertical pass reads whole 32*V-column chunks past
+    // the last staged row
+    L.total = 128 + size_t(nstage) * L.stage + 2 * L.tt + 2 * L.rec2 + align_up(2 * sizeof(TileInfo), 128) + 64 +
+              1024;
+    return L;
+}
+
+// Bounded wait that also honours the CTA abort flag; false on timeout/abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > 2000000000ull) {
+                flag(err, kErrTimeout);
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+    flag(err, kErrTimeout);
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+template <typename T, int C, int G, int V>
+__global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
 {
     using A = typename AccOf<T>::type;
     constexpr int kVec = 16 / int(sizeof(T)); // elements per 16 bytes
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    const size_t tin_bytes = (size_t(p.box_h) * p.box_w * sizeof(T) + 127) & ~size_t(127);
+    const int ngy = p.tile_h / G, ngx = p.tile_w / G;
     const int nstage = (p.use_tma && p.stages == 2) ? 2 : 1;
-    T *tin0 = reinterpret_cast<T *>(smem);
-    T *tin1 = reinterpret_cast<T *>(smem + (nstage - 1) * tin_bytes);
-    A *tt = reinterpret_cast<A *>(smem + nstage * tin_bytes);
-    const size_t tt_bytes = (size_t(p.tile_h) * p.pitch_t * sizeof(A) + 127) & ~size_t(127);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + nstage * tin_bytes + tt_bytes);
-    TileInfo *info = reinterpret_cast<TileInfo *>(bars + 2);
-    int *abort_flag = reinterpret_cast<int *>(info + 2);
+    const Layout L = layout(sizeof(T), sizeof(A), p.box_h, p.box_w, ngy, ngx, p.js, p.tile_h, p.pitch_t, nstage);
+    unsigned char *after_stages = smem + nstage * L.stage;
+    A *tt0 = reinterpret_cast<A *>(after_stages);
+    unsigned char *rec_base = after_stages + 2 * L.tt;
+    TileInfo *info = reinterpret_cast<TileInfo *>(rec_base + 2 * L.rec2);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(info) +
+                                                  align_up(2 * sizeof(TileInfo), 128));
+    uint64_t *full = bars, *ttfull = bars + 2, *ttempty = bars + 4;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 6);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n1 = p.n1;                 // pass-1 (and staging) warps
+    const int n2 = kWarps - n1;          // pass-2 warps
     const int total = p.tiles_y * p.tiles_x;
     const T *in = static_cast<const T *>(p.in);
     T *out = static_cast<T *>(p.out);
@@ -205,173 +285,243 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
     const A *band_x = static_cast<const A *>(p.band_x);
 
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&ttfull[0], 32 * n1);
+        mbar_init(&ttfull[1], 32 * n1);
+        mbar_init(&ttempty[0], 32 * n2);
+        mbar_init(&ttempty[1], 32 * n2);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    const uint32_t copy_bytes = uint32_t(p.n_sub) * p.sub_h * p.box_w * sizeof(T);
+    auto stage_tin = [&](int s) { return reinterpret_cast<T *>(smem + s * L.stage); };
+    auto stage_wy = [&](int s) { return reinterpret_cast<A *>(smem + s * L.stage + L.tin); };
+    auto stage_wx = [&](int s) { return reinterpret_cast<A *>(smem + s * L.stage + L.tin + L.wy); };
+    auto tt_buf = [&](int b) { return reinterpret_cast<A *>(reinterpret_cast<unsigned char *>(tt0) + b * L.tt); };
+    auto rec2 = [&](int b) { return reinterpret_cast<Rec2 *>(rec_base + b * L.rec2); };
+    auto rec2_w = [&](int b) { return reinterpret_cast<A *>(rec_base + b * L.rec2 + sizeof(Rec2)); };
 
-    // Producer step: warp 0 computes the rectangle and (TMA) lane 0 issues the copies.
-    auto produce = [&](int t, int stage) {
-        TileInfo ti = tile_rect<C, GY, JY, GX, JX>(p, t, kVec);
+    // Staged rectangle, valid groups and per-group band offsets of tile t
+    // (one full warp; lane 0 writes the scalars).
+    auto rect = [&](int t, TileInfo *rec) {
+        const int ty = t / p.tiles_x, tx = t % p.tiles_x;
+        const int gy0 = ty * ngy, gx0 = tx * ngx;
+        const bool vy = lane < ngy && gy0 + lane < p.groups_y;
+        const bool vx = lane < ngx && gx0 + lane < p.groups_x;
+        const int by = vy ? __ldg(p.base_y + gy0 + lane) : INT_MAX;
+        const int bx = vx ? __ldg(p.base_x + gx0 + lane) : INT_MAX;
+        int ylo = by, xlo = bx;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ylo = min(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
+            xlo = min(xlo, __shfl_xor_sync(0xffffffffu, xlo, o));
+        }
+        const int s0 = xlo * C;
+        const int xs = s0 - (s0 % kVec);
+        if (vy) rec->rb[lane] = by - ylo;
+        if (vx) rec->cb[lane] = bx * C - xs;
         if (lane == 0) {
-            info[stage] = ti;
-            if (p.use_tma) {
-                T *dst = stage ? tin1 : tin0;
-                mbar_arrive_expect_tx(&bars[stage], copy_bytes);
-                for (int k = 0; k < p.n_sub; ++k)
-                    tma_load_2d(dst + size_t(k) * p.sub_h * p.box_w, &tmap, &bars[stage], ti.xs,
-                                ti.ry0 + k * p.sub_h);
-            }
+            rec->ry0 = ylo;
+            rec->xs = xs;
+            rec->nvy = min(ngy, p.groups_y - gy0);
+            rec->nvx = min(ngx, p.groups_x - gx0);
+        }
+        __syncwarp();
+    };
+
+    // TMA producer (warp 0): rectangle, then lane 0 issues the copies of stage s.
+    auto produce = [&](int t, int s) {
+        rect(t, &info[s]);
+        if (lane == 0) {
+            const TileInfo &ti = info[s];
+            const int ty = t / p.tiles_x, tx = t % p.tiles_x;
+            const uint32_t by = uint32_t(ti.nvy) * p.js * sizeof(A);
+            const uint32_t bx = uint32_t(ti.nvx) * p.js * sizeof(A);
+            const uint32_t bt = uint32_t(p.n_sub) * p.sub_h * p.box_w * sizeof(T);
+            mbar_arrive_expect_tx(&full[s], bt + by + bx);
+            T *dst = stage_tin(s);
+            for (int k = 0; k < p.n_sub; ++k)
+                tma_load_2d(dst + size_t(k) * p.sub_h * p.box_w, &tmap, &full[s], ti.xs, ti.ry0 + k * p.sub_h);
+            bulk_load(stage_wy(s), band_y + size_t(ty) * ngy * p.js, by, &full[s]);
+            bulk_load(stage_wx(s), band_x + size_t(tx) * ngx * p.js, bx, &full[s]);
         }
     };
 
-    int it = 0;
-    if (p.use_tma && nstage == 2 && warp == 0 && int(blockIdx.x) < total) produce(blockIdx.x, 0);
+    const int J = p.J;
+    const int my_tiles = int(blockIdx.x) < total ? (total - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
 
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
-        const int stage = nstage == 2 ? (it & 1) : 0;
-        // use count of this stage's barrier so far -> phase parity to wait for
-        const uint32_t parity = nstage == 2 ? uint32_t((it >> 1) & 1) : uint32_t(it & 1);
-        T *tin = stage ? tin1 : tin0;
-        if (p.use_tma) {
-            const int tn = t + gridDim.x;
-            if (warp == 0) {
-                if (nstage == 2) {
-                    if (tn < total) produce(tn, stage ^ 1);
-                } else {
-                    produce(t, 0);
-                }
-            }
-            if (!mbar_wait_bounded(&bars[stage], parity)) {
-                flag(p.err, kErrTimeout);
-                atomicExch(abort_flag, 1);
-            }
-            __syncthreads();
-            if (*abort_flag) {
-                // Let any copy still in flight land before the CTA exits.
-                mbar_wait_bounded(&bars[0], 0u);
-                mbar_wait_bounded(&bars[1], 0u);
-                return;
-            }
-        } else {
-            if (warp == 0) produce(t, 0);
-            __syncthreads();
-            const TileInfo ti = info[0];
-            // Plain staging: coalesced loads, zero outside the image.
-            const int64_t row_len = p.in_w * C;
-            for (int r = warp; r < p.box_h; r += kWarps) {
-                const int64_t gy = int64_t(ti.ry0) + r;
-                T *dst = tin + size_t(r) * p.box_w;
-                for (int s = lane; s < p.box_w; s += 32) {
-                    const int64_t gx = int64_t(ti.xs) + s;
-                    T v = from_acc<T, A>(A(0));
-                    if (gy < p.in_h && gx < row_len) v = in[gy * p.in_stride + gx];
-                    dst[s] = v;
-                }
-            }
-            __syncthreads();
+    if (warp < n1) {
+        // ======================= staging + pass 1 =======================
+        const int t1n = 32 * n1;
+        if (p.use_tma && warp == 0) {
+            for (int k = 0; k < nstage && k < my_tiles; ++k) produce(blockIdx.x + k * gridDim.x, k);
         }
-        const TileInfo ti = info[stage];
-        const int ty = t / p.tiles_x, tx = t % p.tiles_x;
-
-        // ---------------- pass 1: vertical, lanes along samples ----------------
-        {
-            const int ngy = p.tile_h / GY;
-            const int nchunk = (ti.cols + 31) >> 5;
-            const int ntask = ngy * nchunk;
-            const int per = (ntask + kWarps - 1) / kWarps;
-            const int t0 = warp * per, t1 = min(ntask, t0 + per);
-            int cur_q = -1;
-            A w[GY][JY];
-            int rb = 0;
-            bool ok = true;
-            for (int task = t0; task < t1; ++task) {
-                const int q = task / nchunk, k = task % nchunk;
-                const int gy = ty * ngy + q;
-                if (gy >= p.groups_y) continue;
-                if (q != cur_q) {
-                    cur_q = q;
-                    const A *src = band_y + size_t(gy) * GY * JY;
-#pragma unroll
-                    for (int r = 0; r < GY; ++r)
-#pragma unroll
-                        for (int j = 0; j < JY; ++j) w[r][j] = __ldg(src + r * JY + j);
-                    rb = __ldg(p.base_y + gy) - ti.ry0;
-                    ok = rb >= 0 && rb + JY <= p.box_h;
-                    if (!ok && lane == 0) flag(p.err, kErrBounds);
+        for (int i = 0; i < my_tiles; ++i) {
+            const int t = blockIdx.x + i * gridDim.x;
+            const int ty = t / p.tiles_x, tx = t % p.tiles_x;
+            const int s = nstage == 2 ? (i & 1) : 0;
+            const int b = i & 1;
+            if (p.use_tma) {
+                const uint32_t par = nstage == 2 ? uint32_t((i >> 1) & 1) : uint32_t(i & 1);
+                if (!wait_or_abort(&full[s], par, abort_flag, p.err)) break;
+            } else {
+                if (warp == 0) rect(t, &info[0]);
+                named_sync(1, t1n);
+                const TileInfo &ti = info[0];
+                const int64_t row_len = p.in_w * C;
+                T *tin = stage_tin(0);
+                for (int r = warp; r < p.box_h; r += n1) {
+                    const int64_t gy = int64_t(ti.ry0) + r;
+                    T *dst = tin + size_t(r) * p.box_w;
+                    for (int c = lane; c < p.box_w; c += 32) {
+                        const int64_t gx = int64_t(ti.xs) + c;
+                        T v = from_acc<T, A>(A(0));
+                        if (gy < p.in_h && gx < row_len) v = in[gy * p.in_stride + gx];
+                        dst[c] = v;
+                    }
                 }
-                if (!ok) continue;
-                const int s = k * 32 + lane;
-                if (s >= p.box_w) continue;
-                A acc[GY];
-#pragma unroll
-                for (int r = 0; r < GY; ++r) acc[r] = A(0);
-                const T *col = tin + size_t(rb) * p.box_w + s;
-#pragma unroll
-                for (int j = 0; j < JY; ++j) {
-                    const A v = to_acc<A, T>(col[size_t(j) * p.box_w]);
-#pragma unroll
-                    for (int r = 0; r < GY; ++r) acc[r] = fma(w[r][j], v, acc[r]);
-                }
-                A *dst = tt + size_t(q * GY) * p.pitch_t + s;
-#pragma unroll
-                for (int r = 0; r < GY; ++r) dst[size_t(r) * p.pitch_t] = acc[r];
+                A *wy = stage_wy(0), *wx = stage_wx(0);
+                const A *sy = band_y + size_t(ty) * ngy * p.js, *sx = band_x + size_t(tx) * ngx * p.js;
+                for (int e = threadIdx.x; e < ti.nvy * p.js; e += t1n) wy[e] = __ldg(sy + e);
+                for (int e = threadIdx.x; e < ti.nvx * p.js; e += t1n) wx[e] = __ldg(sx + e);
+                named_sync(1, t1n);
             }
-        }
-        __syncthreads();
+            // the pass-2 warps must be done with buffer b (tile i - 2)
+            if (i >= 2 && !wait_or_abort(&ttempty[b], uint32_t(((i >> 1) - 1) & 1), abort_flag, p.err)) break;
+            const TileInfo &ti = info[s];
+            const T *tin = stage_tin(s);
+            const A *wys = stage_wy(s);
+            A *tt = tt_buf(b);
 
-        // ---------------- pass 2: horizontal, lanes along output rows ----------------
-        {
-            const int ngx = p.tile_w / GX;
-            const int yo = ty * p.tile_h + lane;
-            const bool row_ok = lane < p.tile_h && yo < p.out_h;
-            for (int q = warp; q < ngx; q += kWarps) {
-                const int gx = tx * ngx + q;
-                if (gx >= p.groups_x) break;
-                A w[GX][JX];
-                const A *src = band_x + size_t(gx) * GX * JX;
-#pragma unroll
-                for (int g = 0; g < GX; ++g)
-#pragma unroll
-                    for (int j = 0; j < JX; ++j) w[g][j] = __ldg(src + g * JX + j);
-                const int cb = __ldg(p.base_x + gx) * C - ti.xs;
-                if (cb < 0 || cb + JX * C > p.box_w) {
+            // pass 1: lanes along samples; V columns 32 apart per lane.  Chunks
+            // past box_w read harmless staged data and land in the padding of
+            // the intermediate (pitch_t >= w1): no predicate in the inner loop.
+            const int nchunk = p.w1 / (32 * V);
+            const int ntask = ti.nvy * nchunk;
+            const int per = (ntask + n1 - 1) / n1;
+            const int k0 = warp * per, k1 = min(ntask, k0 + per);
+            for (int task = k0; task < k1; ++task) {
+                const int q = task / nchunk, k = task - q * nchunk;
+                const int rb = ti.rb[q];
+                if (rb < 0 || rb + J > p.box_h) {
                     if (lane == 0) flag(p.err, kErrBounds);
                     continue;
                 }
-                if (!row_ok) continue;
-                A acc[GX][C];
+                const int c0 = k * 32 * V + lane;
+                A acc[G][V];
 #pragma unroll
-                for (int g = 0; g < GX; ++g)
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[g][v] = A(0);
+                const T *col = tin + rb * p.box_w + c0;
+                const A *wq = wys + q * p.js;
+#pragma unroll 4
+                for (int j = 0; j < J; ++j) {
+                    A w[G];
+                    load_w<A, G>(w, wq);
+                    wq += G;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const A d = to_acc<A, T>(col[32 * v]);
+#pragma unroll
+                        for (int g = 0; g < G; ++g) acc[g][v] = fma(w[g], d, acc[g][v]);
+                    }
+                    col += p.box_w;
+                }
+                A *dst = tt + q * G * p.pitch_t + c0;
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) dst[g * p.pitch_t + 32 * v] = acc[g][v];
+            }
+            // hand the pass-2 record (offsets and x weights) over with buffer b
+            Rec2 *r2 = rec2(b);
+            if (threadIdx.x < 32) {
+                if (lane < ngx) r2->cb[lane] = ti.cb[lane];
+                if (lane == 0) {
+                    r2->ty = ty;
+                    r2->tx = tx;
+                    r2->nvx = ti.nvx;
+                }
+            }
+            {
+                const A *src = stage_wx(s);
+                A *dst = rec2_w(b);
+                for (int e = threadIdx.x; e < ti.nvx * p.js; e += t1n) dst[e] = src[e];
+            }
+            mbar_arrive(&ttfull[b]);
+            // every pass-1 warp is done with stage s before it is refilled
+            named_sync(1, t1n);
+            if (p.use_tma && warp == 0) {
+                const int in_ = i + nstage;
+                if (in_ < my_tiles) produce(blockIdx.x + in_ * gridDim.x, s);
+            }
+        }
+    } else {
+        // =========================== pass 2 ============================
+        const int w2 = warp - n1;
+        const int RB = p.tile_h < 32 ? p.tile_h : 32; // rows per warp task
+        const int GPW = 32 / RB;                      // groups per warp task
+        const int rsub = lane % RB, gsub = lane / RB;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int b = i & 1;
+            if (!wait_or_abort(&ttfull[b], uint32_t((i >> 1) & 1), abort_flag, p.err)) break;
+            const Rec2 *r2 = rec2(b);
+            const A *tt = tt_buf(b);
+            const A *wxs = rec2_w(b);
+            const int ty = r2->ty, tx = r2->tx, nvx = r2->nvx;
+            const int nrb = (p.tile_h + RB - 1) / RB;
+            const int npg = (nvx + GPW - 1) / GPW;
+            const int ntask = nrb * npg;
+            const int per = (ntask + n2 - 1) / n2;
+            const int k0 = w2 * per, k1 = min(ntask, k0 + per);
+            for (int task = k0; task < k1; ++task) {
+                const int rbk = task / npg, pg = task - rbk * npg;
+                const int q = pg * GPW + gsub;
+                const int row = rbk * RB + rsub;
+                const int64_t yo = int64_t(ty) * p.tile_h + row;
+                const int gx = tx * ngx + q;
+                if (q >= nvx || row >= p.tile_h || yo >= p.out_h) continue;
+                const int cb = r2->cb[q];
+                if (cb < 0 || cb + J * C > p.box_w) {
+                    flag(p.err, kErrBounds);
+                    continue;
+                }
+                A acc[G][C];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
 #pragma unroll
                     for (int c = 0; c < C; ++c) acc[g][c] = A(0);
-                const A *row = tt + size_t(lane) * p.pitch_t + cb;
-#pragma unroll
-                for (int j = 0; j < JX; ++j) {
+                const A *rowp = tt + row * p.pitch_t + cb;
+                const A *wq = wxs + q * p.js;
+#pragma unroll 4
+                for (int j = 0; j < J; ++j) {
+                    A w[G];
+                    load_w<A, G>(w, wq);
+                    wq += G;
 #pragma unroll
                     for (int c = 0; c < C; ++c) {
-                        const A v = row[j * C + c];
+                        const A d = rowp[c];
 #pragma unroll
-                        for (int g = 0; g < GX; ++g) acc[g][c] = fma(w[g][j], v, acc[g][c]);
+                        for (int g = 0; g < G; ++g) acc[g][c] = fma(w[g], d, acc[g][c]);
                     }
+                    rowp += C;
                 }
-                // Store GX*C contiguous samples of this row (clipped at the right edge).
-                const int64_t x0 = int64_t(gx) * GX;
-                T *o = out + int64_t(yo) * p.out_stride + x0 * C;
-                const int nvalid = p.out_w - x0 < GX ? int(p.out_w - x0) : GX;
-                constexpr int kRun = GX * C;
+                // Store G*C contiguous samples of this row (clipped at the right edge).
+                const int64_t x0 = int64_t(gx) * G;
+                T *o = out + yo * p.out_stride + x0 * C;
+                const int nvalid = p.out_w - x0 < G ? int(p.out_w - x0) : G;
+                constexpr int kRun = G * C;
                 constexpr int kRunBytes = kRun * int(sizeof(T));
-                if (nvalid == GX && (kRunBytes % 16) == 0 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+                if (nvalid == G && (kRunBytes % 16) == 0 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
                     union {
                         T e[kRun];
                         uint4 v[kRunBytes / 16 > 0 ? kRunBytes / 16 : 1];
                     } u;
 #pragma unroll
-                    for (int g = 0; g < GX; ++g)
+                    for (int g = 0; g < G; ++g)
 #pragma unroll
                         for (int c = 0; c < C; ++c) u.e[g * C + c] = from_acc<T, A>(acc[g][c]);
                     uint4 *ov = reinterpret_cast<uint4 *>(o);
@@ -379,33 +529,31 @@ __global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__
                     for (int v = 0; v < kRunBytes / 16; ++v) ov[v] = u.v[v];
                 } else {
 #pragma unroll
-                    for (int g = 0; g < GX; ++g)
+                    for (int g = 0; g < G; ++g)
                         if (g < nvalid)
 #pragma unroll
                             for (int c = 0; c < C; ++c) o[g * C + c] = from_acc<T, A>(acc[g][c]);
                 }
             }
+            mbar_arrive(&ttempty[b]);
         }
-        __syncthreads();
     }
-}
-
-// Dynamic shared memory the kernel needs for a parameter set.
-inline size_t smem_bytes(size_t elem, size_t acc, int box_h, int box_w, int tile_h, int pitch_t, int nstage)
-{
-    const size_t tin = (size_t(box_h) * box_w * elem + 127) & ~size_t(127);
-    const size_t tt = (size_t(tile_h) * pitch_t * acc + 127) & ~size_t(127);
-    return 128 + size_t(nstage) * tin + tt + 2 * sizeof(uint64_t) + 2 * sizeof(TileInfo) + 16;
+    // On an abort some TMA copies may still be in flight; let them land
+    // (bounded) before the CTA's shared memory is released.
+    if (*abort_flag && p.use_tma && warp == 0) {
+        mbar_wait_bounded(&full[0], 0u);
+        mbar_wait_bounded(&full[1], 0u);
+    }
 }
 
 // One instantiated kernel variant.
 struct Variant {
-    int dtype, C, G, J;
+    int dtype, C, G, V;
     const void *fn;
 };
 
-#define RS_FUSED_VARIANT(T, DT, C, G, J) \
-    { DT, C, G, J, reinterpret_cast<const void *>(&fused_kernel<T, C, G, J, G, J>) }
+#define RS_FUSED_VARIANT(T, DT, C, G, V) \
+    { DT, C, G, V, reinterpret_cast<const void *>(&fused_kernel<T, C, G, V>) }
 
 } // namespace fused
 } // namespace rs

@@ -1,38 +1,19 @@
 // rs_fused_f32.cu -- instantiations of the fused kernel for float storage.
 // The kernel template itself is in rs_fused.cuh; this file only lists the
-// (channels, group, band width) combinations compiled for this storage type.
+// (channels, group size, columns per thread) combinations compiled for this
+// storage type.  The band width J is a run-time parameter.
 #include "rs_fused.cuh"
 
 namespace rs {
 namespace fused {
 
 static const Variant kVariants[] = {
-    RS_FUSED_VARIANT(float, RS_F32, 1, 4, 8),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 4, 9),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 4, 12),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 4, 16),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 4, 24),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 4, 32),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 2, 16),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 2, 24),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 2, 32),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 2, 48),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 1, 32),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 1, 48),
-    RS_FUSED_VARIANT(float, RS_F32, 1, 1, 64),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 4, 8),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 4, 9),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 4, 12),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 4, 16),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 4, 24),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 4, 32),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 2, 16),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 2, 24),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 2, 32),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 2, 48),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 1, 32),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 1, 48),
-    RS_FUSED_VARIANT(float, RS_F32, 3, 1, 64),
+    RS_FUSED_VARIANT(float, RS_F32, 1, 4, 4),
+    RS_FUSED_VARIANT(float, RS_F32, 1, 2, 4),
+    RS_FUSED_VARIANT(float, RS_F32, 1, 1, 4),
+    RS_FUSED_VARIANT(float, RS_F32, 3, 4, 4),
+    RS_FUSED_VARIANT(float, RS_F32, 3, 2, 4),
+    RS_FUSED_VARIANT(float, RS_F32, 3, 1, 4),
 };
 
 const Variant *variants_f32(int *n)

@@ -39,12 +39,17 @@ struct AxisTables {
     int32_t *start = nullptr; // [n_out] first index of the folded window
     double *w64 = nullptr;    // [n_out][t_eff] folded normalised FP64 weights
     void *wwork = nullptr;    // [n_out][t_eff] working precision (float or double)
-    // Register band for the fused kernel: outputs are grouped G at a time;
-    // group g reads inputs [base[g], base[g] + J) with weights [g][r][j].
+    // Weight band for the fused kernel: outputs are grouped G at a time;
+    // group g reads inputs [base[g], base[g] + J) with weight
+    // band_w[g * band_stride(G, J) + j * G + r] for member r and input j.
     int32_t *band_base = nullptr; // [groups]
-    void *band_w = nullptr;       // [groups][G][J] working precision
+    void *band_w = nullptr;       // [groups][band_stride(G, J)] working precision
     int32_t G = 0, J = 0, groups = 0;
 };
+
+// Floats per band group: J * G rounded up to a multiple of 4, so that every
+// group starts on a 16-byte boundary (TMA bulk copies need that).
+__host__ __device__ inline int band_stride(int G, int J) { return (J * G + 3) / 4 * 4; }
 
 // Parameters of the weight-table kernel for one axis (passed by value).
 struct WeightArgs {
@@ -80,39 +85,6 @@ struct TwoPassArgs {
     int dtype; // rs_dtype (in == out)
 };
 cudaError_t launch_two_pass(const TwoPassArgs &a, cudaStream_t s);
-
-// Fused single-pass kernel (V then H inside one CTA, register bands).
-struct FusedArgs {
-    const void *in;
-    void *out;
-    int64_t in_h, in_w, out_h, out_w, C;
-    int64_t in_stride, out_stride; // elements
-    const int32_t *base_y, *base_x; // band bases
-    const void *band_y, *band_x;    // band weights [groups][G][J]
-    int32_t gy, jy, gx, jx;         // band shapes
-    int32_t tile_h, tile_w;         // output tile (multiples of gy, gx)
-    int32_t box_h, box_w;           // staged input tile (rows, samples) upper bounds
-    int32_t tiles_y, tiles_x;
-    int dtype;
-    int use_tma;
-    void *tmap; // device-resident or by-value CUtensorMap (128 B), when use_tma
-    int *err;
-};
-
-struct FusedChoice {
-    int gy = 0, jy = 0, gx = 0, jx = 0; // band shapes (instantiated set)
-    int tile_h = 0, tile_w = 0;
-    int threads = 0;
-    size_t smem = 0;
-    int ctas_per_sm = 0;
-};
-
-// Returns false when no instantiated variant fits (dtype, C, G, J).
-bool fused_supported(int dtype, int C, int g, int j);
-// Instantiated band widths for a group size (ascending); used to round up J.
-int fused_round_j(int g, int j);
-cudaError_t launch_fused(const FusedArgs &a, const FusedChoice &c, cudaStream_t s, int num_sms);
-size_t fused_smem_bytes(const FusedArgs &a, const FusedChoice &c);
 
 // Thread-local last-error string.
 void set_error(const std::string &msg);

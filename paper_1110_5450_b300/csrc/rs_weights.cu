@@ -1,6 +1,6 @@
 // rs_weights.cu -- FP64 weight-table kernel and register-band builder.
 //
-// One thread per output sample of an axis.  Tap indices come from a closed
+// Blocks of consecutive output samples of an axis.  Tap indices come from a closed
 // form in 64-bit integers (exact), weights from the kernel evaluated in FP64
 // at x = ((2j+1) n_out - (2i+1) n_in) / D (one correctly rounded division of
 // exact integers), normalised by their FP64 sum, folded through the boundary
@@ -50,7 +50,7 @@ __device__ double kernel_eval(int kernel, double a, int64_t R, double x)
         if (t >= double(R)) return 0.0;
         if (x == 0.0) return 1.0;
         const double xr = x / double(R);
-        return (sinpi(x) / (kPi * x)) * (sinpi(xr) / (kPi * xr));
+        return (sinpi(x) * sinpi(xr)) / ((kPi * x) * (kPi * xr));
     }
     case RS_K_BSPLINE3:
         if (t < 1.0) return (0.5 * t - 1.0) * t * t + 2.0 / 3.0;
@@ -88,94 +88,161 @@ __device__ __forceinline__ int64_t map_index(int64_t j, int64_t n, int boundary)
     }
 }
 
-__device__ void axis_weights(const WeightArgs &A, int64_t i)
+// Shared-memory budget of one block: per output its tap range, per raw tap
+// its mapped index and kernel value.
+constexpr int kThreadsW = 256;
+constexpr int kFlat = 2048; // raw taps staged per block
+
+// One block computes the tables of outputs [o0, o0 + nb) of one axis in
+// phases: (A) a thread per output finds its taps with the exact integer
+// formula, (B) a thread per (output, tap) evaluates the kernel in FP64 and the
+// boundary map, (C1) a thread per output sums its taps in index order,
+// (C2) a thread per (output, window slot) normalises and folds mapped
+// duplicates into the stored window and rounds to the working precision,
+// (C3) a thread per output puts the rounding residual back.
+__device__ void axis_block(const WeightArgs &A, int64_t o0, int nb, int64_t *jlo_s, int *cnt_s, int64_t *slot_s,
+                           double *val_s, double *sum_s, int64_t *start_s)
 {
     const AxisGeom &g = A.g;
     const AxisTables &T = A.t;
-    const int64_t N0 = (2 * i + 1) * g.n_in;
+    const int tr = g.t_raw, te = g.t_eff;
     const int64_t two_out = 2 * g.n_out;
     const int64_t RD = g.R * g.D;
-    // first raw tap: smallest j with (2j+1) n_out > N0 - R D
-    const int64_t jlo = floor_div(N0 - RD - g.n_out, two_out) + 1;
-    // last raw tap: largest j with (2j+1) n_out < N0 + R D
-    const int64_t jhi = ceil_div(N0 + RD - g.n_out, two_out) - 1;
-    const int64_t cnt = jhi - jlo + 1;
-    T.jlo[i] = int32_t(jlo);
-    T.cnt[i] = int32_t(cnt);
-    const int te = g.t_eff;
-    double *w = T.w64 + i * te;
-    if (cnt < 1 || cnt > g.t_raw) {
-        flag_error(A.err, kErrTaps);
-        T.start[i] = 0;
-        for (int k = 0; k < te; ++k) w[k] = 0.0;
-        return;
-    }
-    const double D = double(g.D);
-    double sum = 0.0;
-    int64_t mlo = g.n_in, mhi = -1;
-    for (int64_t k = 0; k < cnt; ++k) {
-        const int64_t j = jlo + k;
-        const int64_t m = map_index(j, g.n_in, g.boundary);
-        if (m < 0) continue;
-        const double x = double((2 * j + 1) * g.n_out - N0) / D;
-        sum += kernel_eval(g.kernel, g.param, g.R, x);
-        mlo = m < mlo ? m : mlo;
-        mhi = m > mhi ? m : mhi;
-    }
-    int64_t start = mlo < g.n_in - te ? mlo : g.n_in - te;
-    if (start < 0) start = 0;
-    T.start[i] = int32_t(start);
-    for (int k = 0; k < te; ++k) w[k] = 0.0;
-    if (!(sum != 0.0) || mhi < 0 || mhi - start >= te) {
-        flag_error(A.err, kErrSum);
-        return;
-    }
-    for (int64_t k = 0; k < cnt; ++k) {
-        const int64_t j = jlo + k;
-        const int64_t m = map_index(j, g.n_in, g.boundary);
-        if (m < 0) continue;
-        const double x = double((2 * j + 1) * g.n_out - N0) / D;
-        w[m - start] += kernel_eval(g.kernel, g.param, g.R, x) / sum;
-    }
-    if (A.work_is_double) {
-        double *ww = static_cast<double *>(T.wwork) + i * te;
-        for (int k = 0; k < te; ++k) ww[k] = w[k];
-        return;
-    }
-    // Round to FP32, then put the rounding residual back on the largest tap.
-    float *ww = static_cast<float *>(T.wwork) + i * te;
-    double s = 0.0, big = -1.0;
-    int kbig = 0;
-    for (int k = 0; k < te; ++k) {
-        const float f = __double2float_rn(w[k]);
-        ww[k] = f;
-        s += double(f);
-        if (fabs(w[k]) > big) {
-            big = fabs(w[k]);
-            kbig = k;
+    // (A) tap ranges
+    for (int o = threadIdx.x; o < nb; o += blockDim.x) {
+        const int64_t i = o0 + o;
+        const int64_t N0 = (2 * i + 1) * g.n_in;
+        // first raw tap: smallest j with (2j+1) n_out > N0 - R D
+        const int64_t jlo = floor_div(N0 - RD - g.n_out, two_out) + 1;
+        // last raw tap: largest j with (2j+1) n_out < N0 + R D
+        const int64_t jhi = ceil_div(N0 + RD - g.n_out, two_out) - 1;
+        int64_t cnt = jhi - jlo + 1;
+        T.jlo[i] = int32_t(jlo);
+        T.cnt[i] = int32_t(cnt);
+        if (cnt < 1 || cnt > tr) {
+            flag_error(A.err, kErrTaps);
+            cnt = 0;
         }
+        jlo_s[o] = jlo;
+        cnt_s[o] = int(cnt);
     }
-    ww[kbig] = __double2float_rn(double(ww[kbig]) + (1.0 - s));
-}
-
-__global__ void weights_kernel(WeightArgs a0, WeightArgs a1)
-{
-    const int64_t n0 = a0.g.n_out, n1 = a1.g.n_out;
-    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n0 + n1;
-         t += int64_t(gridDim.x) * blockDim.x) {
-        if (t < n0)
-            axis_weights(a0, t);
+    __syncthreads();
+    // (B) kernel values and mapped indices, all lanes busy
+    const double D = double(g.D);
+    for (int e = threadIdx.x; e < nb * tr; e += blockDim.x) {
+        const int o = e / tr, k = e - o * tr;
+        int64_t m = -1;
+        double v = 0.0;
+        if (k < cnt_s[o]) {
+            const int64_t i = o0 + o;
+            const int64_t j = jlo_s[o] + k;
+            m = map_index(j, g.n_in, g.boundary);
+            if (m >= 0) {
+                const double x = double((2 * j + 1) * g.n_out - (2 * i + 1) * g.n_in) / D;
+                v = kernel_eval(g.kernel, g.param, g.R, x);
+            }
+        }
+        slot_s[e] = m;
+        val_s[e] = v;
+    }
+    __syncthreads();
+    // (C1) a thread per output: tap sum in index order, mapped range, window start
+    for (int o = threadIdx.x; o < nb; o += blockDim.x) {
+        const int64_t i = o0 + o;
+        const int cnt = cnt_s[o];
+        const int64_t *sl = slot_s + o * tr;
+        const double *vl = val_s + o * tr;
+        double sum = 0.0;
+        int64_t mlo = g.n_in, mhi = -1;
+        for (int k = 0; k < cnt; ++k) {
+            sum += vl[k];
+            if (sl[k] >= 0) {
+                mlo = sl[k] < mlo ? sl[k] : mlo;
+                mhi = sl[k] > mhi ? sl[k] : mhi;
+            }
+        }
+        int64_t start = mlo < g.n_in - te ? mlo : g.n_in - te;
+        if (start < 0) start = 0;
+        T.start[i] = int32_t(start);
+        const bool ok = cnt != 0 && sum != 0.0 && mhi >= 0 && mhi - start < te;
+        if (cnt != 0 && !ok) flag_error(A.err, kErrSum);
+        sum_s[o] = ok ? sum : 0.0;
+        start_s[o] = start;
+    }
+    __syncthreads();
+    // (C2) a thread per (output, window slot): normalise and fold, all lanes busy
+    for (int e = threadIdx.x; e < nb * te; e += blockDim.x) {
+        const int o = e / te, q = e - o * te;
+        const int64_t i = o0 + o;
+        const double sum = sum_s[o];
+        double acc = 0.0;
+        if (sum != 0.0) {
+            const int cnt = cnt_s[o];
+            const int64_t *sl = slot_s + o * tr;
+            const double *vl = val_s + o * tr;
+            const int64_t jlo = jlo_s[o], start = start_s[o];
+            if (jlo >= 0 && jlo + cnt <= g.n_in) { // every tap maps to itself
+                const int64_t k = start + q - jlo;
+                if (k >= 0 && k < cnt) acc = vl[k] / sum;
+            } else {
+                for (int k = 0; k < cnt; ++k)
+                    if (sl[k] == start + q) acc += vl[k] / sum;
+            }
+        }
+        T.w64[i * te + q] = acc;
+        if (A.work_is_double)
+            static_cast<double *>(T.wwork)[i * te + q] = acc;
         else
-            axis_weights(a1, t - n0);
+            static_cast<float *>(T.wwork)[i * te + q] = __double2float_rn(acc);
+    }
+    if (A.work_is_double) return;
+    __syncthreads();
+    // (C3) a thread per output: put the FP32 rounding residual back on the
+    // largest tap (first index on ties) and re-round it
+    for (int o = threadIdx.x; o < nb; o += blockDim.x) {
+        const int64_t i = o0 + o;
+        const double *w = T.w64 + i * te;
+        float *ww = static_cast<float *>(T.wwork) + i * te;
+        double s32 = 0.0, big = -1.0;
+        int kbig = 0;
+        for (int q = 0; q < te; ++q) {
+            s32 += double(ww[q]);
+            if (fabs(w[q]) > big) {
+                big = fabs(w[q]);
+                kbig = q;
+            }
+        }
+        ww[kbig] = __double2float_rn(double(ww[kbig]) + (1.0 - s32));
     }
 }
 
+__global__ void __launch_bounds__(kThreadsW) weights_kernel(WeightArgs a0, WeightArgs a1, int nb0, int nb1,
+                                                            int blocks0)
+{
+    __shared__ int64_t jlo_s[kThreadsW];
+    __shared__ int cnt_s[kThreadsW];
+    __shared__ int64_t slot_s[kFlat];
+    __shared__ double val_s[kFlat];
+    __shared__ double sum_s[kThreadsW];
+    __shared__ int64_t start_s[kThreadsW];
+    const bool first = int(blockIdx.x) < blocks0;
+    const WeightArgs &A = first ? a0 : a1;
+    const int nb_full = first ? nb0 : nb1;
+    const int64_t o0 = int64_t(first ? blockIdx.x : blockIdx.x - blocks0) * nb_full;
+    const int64_t rem = A.g.n_out - o0;
+    const int nb = int(rem < nb_full ? rem : nb_full);
+    if (nb > 0) axis_block(A, o0, nb, jlo_s, cnt_s, slot_s, val_s, sum_s, start_s);
+}
+
+// Band element (group grp, tap j, member r) of one axis.  Layout:
+// band_w[grp * JS + j * G + r], JS = band_stride(G, J) (a multiple of 4).
 template <typename W>
-__device__ void axis_band(const WeightArgs &A, int64_t grp)
+__device__ void band_element(const WeightArgs &A, int64_t grp, int e)
 {
     const AxisGeom &g = A.g;
     const AxisTables &T = A.t;
     const int G = T.G, J = T.J, te = g.t_eff;
+    const int JS = band_stride(G, J);
     int64_t b0 = g.n_in, hi = 0;
     for (int r = 0; r < G; ++r) {
         const int64_t i = grp * G + r;
@@ -184,56 +251,71 @@ __device__ void axis_band(const WeightArgs &A, int64_t grp)
         b0 = s < b0 ? s : b0;
         hi = s + te > hi ? s + te : hi;
     }
-    int64_t b = g.n_in >= J ? (b0 < g.n_in - J ? b0 : g.n_in - J) : 0;
-    if (hi - b > J) flag_error(A.err, kErrBand);
-    T.band_base[grp] = int32_t(b);
-    const W *ww = static_cast<const W *>(T.wwork);
-    W *out = static_cast<W *>(T.band_w) + grp * G * J;
-    for (int r = 0; r < G; ++r) {
-        const int64_t i = grp * G + r;
-        const int64_t off = i < g.n_out ? T.start[i] - b : 0;
-        for (int j = 0; j < J; ++j) {
-            W v = W(0);
-            if (i < g.n_out && j >= off && j < off + te && (hi - b) <= J) v = ww[i * te + (j - off)];
-            out[r * J + j] = v;
-        }
+    const int64_t b = g.n_in >= J ? (b0 < g.n_in - J ? b0 : g.n_in - J) : 0;
+    const bool fits = (hi - b) <= J;
+    if (e == 0) {
+        T.band_base[grp] = int32_t(b);
+        if (!fits) flag_error(A.err, kErrBand);
     }
+    W v = W(0);
+    const int j = e / G, r = e % G;
+    const int64_t i = grp * G + r;
+    if (j < J && i < g.n_out && fits) {
+        const int64_t off = T.start[i] - b;
+        if (j >= off && j < off + te) v = static_cast<const W *>(T.wwork)[i * te + (j - off)];
+    }
+    static_cast<W *>(T.band_w)[grp * JS + e] = v;
 }
 
 __global__ void band_kernel(WeightArgs a0, WeightArgs a1)
 {
-    const int64_t n0 = a0.t.groups, n1 = a1.t.groups;
+    const int64_t js0 = band_stride(a0.t.G, a0.t.J), js1 = band_stride(a1.t.G, a1.t.J);
+    const int64_t n0 = int64_t(a0.t.groups) * js0, n1 = int64_t(a1.t.groups) * js1;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n0 + n1;
          t += int64_t(gridDim.x) * blockDim.x) {
-        const WeightArgs &A = t < n0 ? a0 : a1;
-        const int64_t grp = t < n0 ? t : t - n0;
+        const bool first = t < n0;
+        const WeightArgs &A = first ? a0 : a1;
+        const int64_t u = first ? t : t - n0;
+        const int64_t js = first ? js0 : js1;
         if (A.work_is_double)
-            axis_band<double>(A, grp);
+            band_element<double>(A, u / js, int(u % js));
         else
-            axis_band<float>(A, grp);
+            band_element<float>(A, u / js, int(u % js));
     }
 }
 
 } // namespace
 
+// Outputs per block: enough blocks to cover the GPU twice, at most kThreadsW
+// outputs and kFlat staged taps.
+static int outputs_per_block(const AxisGeom &g, int64_t total_outputs)
+{
+    int64_t nb = (total_outputs + 295) / 296;
+    nb = nb < 1 ? 1 : nb;
+    nb = nb > kThreadsW ? kThreadsW : nb;
+    const int64_t cap = kFlat / (g.t_raw > 0 ? g.t_raw : 1);
+    nb = nb > cap ? cap : nb;
+    return int(nb < 1 ? 1 : nb);
+}
+
 cudaError_t launch_weights(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s)
 {
-    const int64_t n = a0.g.n_out + a1.g.n_out;
-    const int threads = 128;
-    int blocks = int((n + threads - 1) / threads);
-    if (blocks > 4096) blocks = 4096;
-    weights_kernel<<<blocks, threads, 0, s>>>(a0, a1);
+    const int64_t total = a0.g.n_out + a1.g.n_out;
+    const int nb0 = outputs_per_block(a0.g, total), nb1 = outputs_per_block(a1.g, total);
+    const int64_t b0 = (a0.g.n_out + nb0 - 1) / nb0, b1 = (a1.g.n_out + nb1 - 1) / nb1;
+    weights_kernel<<<int(b0 + b1), kThreadsW, 0, s>>>(a0, a1, nb0, nb1, int(b0));
     return cudaGetLastError();
 }
 
 cudaError_t launch_band(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s)
 {
-    const int64_t n = int64_t(a0.t.groups) + a1.t.groups;
-    const int threads = 128;
-    int blocks = int((n + threads - 1) / threads);
-    if (blocks > 4096) blocks = 4096;
+    const int64_t n = int64_t(a0.t.groups) * band_stride(a0.t.G, a0.t.J) +
+                      int64_t(a1.t.groups) * band_stride(a1.t.G, a1.t.J);
+    const int threads = 256;
+    int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 148 * 16) blocks = 148 * 16;
     if (blocks < 1) blocks = 1;
-    band_kernel<<<blocks, threads, 0, s>>>(a0, a1);
+    band_kernel<<<int(blocks), threads, 0, s>>>(a0, a1);
     return cudaGetLastError();
 }
 

@@ -271,3 +271,49 @@ def test_full_size_sampled_rows(rs, c2_image, scale, dt):
         err = max(err, float(np.abs(got[r] - want[0]).max()))
     assert err <= TOL[dt], (scale, dt, err, info.path)
     assert np.isfinite(got).all()
+
+
+def test_two_plans_sharing_a_kernel_variant(rs):
+    """Plans of different shared-memory size on the same kernel variant,
+    created one after the other and then used in either order."""
+    import torch
+
+    img = synth.sinusoids(512, 512, 3, seed=2)
+    x = torch.from_numpy(img).cuda()
+    a = rs.Plan(512, 512, 3, scale=1.37, kernel="lanczos", boundary="mirror")
+    b = rs.Plan(512, 512, 3, scale=0.3, kernel="lanczos", boundary="mirror")
+    ya, yb = a(x), b(x)
+    torch.cuda.synchronize()
+    for p, y in ((a, ya), (b, yb)):
+        p.check()
+        want = oracle.resample(img.astype(np.float64), p.info.out_h, p.info.out_w, "lanczos", "mirror",
+                               param=3.0)
+        assert np.abs(y.double().cpu().numpy() - want).max() <= TOL["f32"]
+        p.close()
+
+
+def test_autotune_keeps_parity_and_uses_cache(rs, tmp_path):
+    import torch
+
+    img = synth.sinusoids(700, 900, 3, seed=4)
+    x = torch.from_numpy(img).cuda()
+    cache = str(tmp_path / "tune.jsonl")
+    p = rs.Plan(700, 900, 3, scale=0.61, kernel="lanczos", boundary="mirror")
+    y = p.autotune(x, cache_path=cache)
+    y = p(x, out=y)
+    torch.cuda.synchronize()
+    p.check()
+    want = oracle.resample(img.astype(np.float64), p.info.out_h, p.info.out_w, "lanczos", "mirror", param=3.0)
+    assert np.abs(y.double().cpu().numpy() - want).max() <= TOL["f32"]
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and '"G":' in lines[0]
+    q = rs.Plan(700, 900, 3, scale=0.61, kernel="lanczos", boundary="mirror")
+    q.autotune(x, cache_path=cache)
+    assert (q.info.tile_h, q.info.tile_w, q.info.group_h, q.info.warps_pass1) == \
+        (p.info.tile_h, p.info.tile_w, p.info.group_h, p.info.warps_pass1)
+    assert len(open(cache).read().splitlines()) == 1  # a hit appends nothing
+    z = q(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y, z)
+    p.close()
+    q.close()
