@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the model-chosen kernel configuration")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON-lines autotuner cache (a hit skips the tuning launches)")
     ap.add_argument("--size", type=int, default=4096,
                     help="input side (profiling runs only; the benchmark workload is 4096)")
     ap.add_argument("--scales", type=str, default="1.37,0.3",
@@ -251,7 +253,7 @@ def main():
     t_tune = time.perf_counter()
     if not args.no_tune:
         for p, y in zip(plans, ys):
-            p.autotune(x, out=y, stream=stream)
+            p.autotune(x, out=y, stream=stream, cache_path=args.tune_cache)
     torch.cuda.synchronize()
     t_tune = time.perf_counter() - t_tune
     # our kernels per step and plan: weight tables (+ band tables on the fused

@@ -304,7 +304,10 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     p->tmap_ptr = nullptr;
     p->G = c.G;
     p->J = c.J;
-    const int js = band_stride(c.G, c.J);
+    // the vertical band of the FP32 path stores every weight twice (packed pairs)
+    p->ty.dup = p->work_double ? 1 : 2;
+    p->tx.dup = 1;
+    const int js_y = band_stride(c.G * p->ty.dup, c.J), js_x = band_stride(c.G, c.J);
     p->ty.G = p->tx.G = c.G;
     p->ty.J = p->tx.J = c.J;
     p->ty.groups = int32_t((p->gy.n_out + c.G - 1) / c.G);
@@ -312,8 +315,8 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     Carver cv;
     const size_t o_by = cv.take(size_t(p->ty.groups) * 4);
     const size_t o_bx = cv.take(size_t(p->tx.groups) * 4);
-    const size_t o_wy = cv.take(size_t(p->ty.groups) * js * asz);
-    const size_t o_wx = cv.take(size_t(p->tx.groups) * js * asz);
+    const size_t o_wy = cv.take(size_t(p->ty.groups) * js_y * asz);
+    const size_t o_wx = cv.take(size_t(p->tx.groups) * js_x * asz);
     if (p->bands.p) {
         cudaFree(p->bands.p);
         p->bands.p = nullptr;
@@ -352,7 +355,8 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     fp.band_y = p->ty.band_w;
     fp.band_x = p->tx.band_w;
     fp.J = c.J;
-    fp.js = js;
+    fp.js_y = js_y;
+    fp.js_x = js_x;
     fp.tile_h = c.tile_h;
     fp.tile_w = c.tile_w;
     fp.n_sub = (rows + 255) / 256;
@@ -370,7 +374,7 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     fp.n1 = c.n1;
     fp.err = p->d_err;
     p->tma_ok = (tma_layout && bw <= 256) ? 1 : 0;
-    p->smem = fused::layout(esz, asz, fp.box_h, fp.box_w, ngy, ngx, js, fp.tile_h, fp.pitch_t,
+    p->smem = fused::layout(esz, asz, fp.box_h, fp.box_w, ngy, ngx, js_y, js_x, fp.tile_h, fp.pitch_t,
                             p->tma_ok ? fp.stages : 1)
                   .total;
     if (p->smem > 227 * 1024) return RS_ERR_UNSUPPORTED;
@@ -436,8 +440,9 @@ std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout)
                     c.n_sub = n_sub;
                     c.sub_h = sub_h;
                     const int w1 = (bw + 32 * V - 1) / (32 * V) * (32 * V);
-                    c.smem = fused::layout(esz, asz, c.box_h, bw, tile_h / G, ngx, band_stride(G, J), tile_h,
-                                           w1 | 1, stages)
+                    const int dup = p->work_double ? 1 : 2;
+                    c.smem = fused::layout(esz, asz, c.box_h, bw, tile_h / G, ngx, band_stride(G * dup, J),
+                                           band_stride(G, J), tile_h, w1 | 1, stages)
                                  .total;
                     if (c.smem > smem_cap) continue;
                     c.cost = model_cost(c, C, esz, asz, V);

@@ -82,15 +82,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// One wait attempt; the warp may be parked by the hardware for up to ~20 µs
+// while the phase is incomplete (it wakes as soon as the phase completes), so
+// waiting warps do not spin on the issue slots of working warps.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -110,7 +113,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < (1u << 26); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u && global_ns() - t0 > 2000000000ull) return false;
+        if ((it & 3u) == 3u && global_ns() - t0 > 2000000000ull) return false;
     }
     return false;
 }
@@ -146,7 +149,10 @@ struct Params {
     int64_t in_stride, out_stride;
     const int32_t *base_y, *base_x;
     const void *band_y, *band_x; // [groups][js] accumulation type
-    int32_t J, js;               // band width (inputs per group) and group stride (elements)
+    int32_t J;                   // band width (inputs per group)
+    int32_t js_y, js_x;          // group strides (elements) of the two bands; the
+                                 // vertical band of the FP32 path stores every
+                                 // weight twice (packed-pair FMAs)
     int32_t tile_h, tile_w;      // output tile (multiples of G)
     int32_t box_h, box_w;        // staged rows, staged samples (pitch of tin)
     int32_t sub_h, n_sub;        // TMA box height and copies per tile
@@ -207,16 +213,16 @@ struct Layout {
     size_t tin, wy, wx, stage, tt, rec2, total;
 };
 
-__host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int box_w, int ngy, int ngx, int js,
-                                         int tile_h, int pitch_t, int nstage)
+__host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int box_w, int ngy, int ngx, int js_y,
+                                         int js_x, int tile_h, int pitch_t, int nstage)
 {
     Layout L;
     L.tin = align_up(size_t(box_h) * box_w * elem, 128);
-    L.wy = align_up(size_t(ngy) * js * acc, 128);
-    L.wx = align_up(size_t(ngx) * js * acc, 128);
+    L.wy = align_up(size_t(ngy) * js_y * acc, 128);
+    L.wx = align_up(size_t(ngx) * js_x * acc, 128);
     L.stage = L.tin + L.wy + L.wx;
     L.tt = align_up(size_t(tile_h) * pitch_t * acc, 128);
-    L.rec2 = rec2_bytes(ngx, js, acc);
+    L.rec2 = rec2_bytes(ngx, js_x, acc);
     // + slack because the vertical pass reads whole 32*V-column chunks past
     // the last staged row
     L.total = 128 + size_t(nstage) * L.stage + 2 * L.tt + 2 * L.rec2 + align_up(2 * sizeof(TileInfo), 128) + 64 +
@@ -231,7 +237,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < (1u << 26); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 63u) {
+        if ((it & 3u) == 3u) {
             if (*abort_flag) return false;
             if (global_ns() - t0 > 2000000000ull) {
                 flag(err, kErrTimeout);
@@ -255,17 +261,54 @@ __device__ __forceinline__ void named_sync(int id, int threads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
+// Packed FP32 pairs (Blackwell fma.rn.f32x2: two independent round-to-nearest
+// FMAs in one instruction, bitwise equal to two scalar FMAs).
+__device__ __forceinline__ uint64_t pack2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// N consecutive 8-byte pairs from shared memory (16-byte loads when N is even).
+template <int N> __device__ __forceinline__ void load_pairs(uint64_t (&w)[N], const uint64_t *p)
+{
+    if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(p)[k];
+            w[2 * k] = v.x;
+            w[2 * k + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) w[k] = p[k];
+    }
+}
+
 template <typename T, int C, int G, int V>
 __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
 {
     using A = typename AccOf<T>::type;
+    // FP32 accumulation uses packed-pair FMAs (the FP64 path stays scalar)
+    constexpr bool kPacked = sizeof(A) == 4 && V % 2 == 0;
     constexpr int kVec = 16 / int(sizeof(T)); // elements per 16 bytes
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int ngy = p.tile_h / G, ngx = p.tile_w / G;
     const int nstage = (p.use_tma && p.stages == 2) ? 2 : 1;
-    const Layout L = layout(sizeof(T), sizeof(A), p.box_h, p.box_w, ngy, ngx, p.js, p.tile_h, p.pitch_t, nstage);
+    const Layout L =
+        layout(sizeof(T), sizeof(A), p.box_h, p.box_w, ngy, ngx, p.js_y, p.js_x, p.tile_h, p.pitch_t, nstage);
     unsigned char *after_stages = smem + nstage * L.stage;
     A *tt0 = reinterpret_cast<A *>(after_stages);
     unsigned char *rec_base = after_stages + 2 * L.tt;
@@ -337,15 +380,15 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
         if (lane == 0) {
             const TileInfo &ti = info[s];
             const int ty = t / p.tiles_x, tx = t % p.tiles_x;
-            const uint32_t by = uint32_t(ti.nvy) * p.js * sizeof(A);
-            const uint32_t bx = uint32_t(ti.nvx) * p.js * sizeof(A);
+            const uint32_t by = uint32_t(ti.nvy) * p.js_y * sizeof(A);
+            const uint32_t bx = uint32_t(ti.nvx) * p.js_x * sizeof(A);
             const uint32_t bt = uint32_t(p.n_sub) * p.sub_h * p.box_w * sizeof(T);
             mbar_arrive_expect_tx(&full[s], bt + by + bx);
             T *dst = stage_tin(s);
             for (int k = 0; k < p.n_sub; ++k)
                 tma_load_2d(dst + size_t(k) * p.sub_h * p.box_w, &tmap, &full[s], ti.xs, ti.ry0 + k * p.sub_h);
-            bulk_load(stage_wy(s), band_y + size_t(ty) * ngy * p.js, by, &full[s]);
-            bulk_load(stage_wx(s), band_x + size_t(tx) * ngx * p.js, bx, &full[s]);
+            bulk_load(stage_wy(s), band_y + size_t(ty) * ngy * p.js_y, by, &full[s]);
+            bulk_load(stage_wx(s), band_x + size_t(tx) * ngx * p.js_x, bx, &full[s]);
         }
     };
 
@@ -383,9 +426,9 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                     }
                 }
                 A *wy = stage_wy(0), *wx = stage_wx(0);
-                const A *sy = band_y + size_t(ty) * ngy * p.js, *sx = band_x + size_t(tx) * ngx * p.js;
-                for (int e = threadIdx.x; e < ti.nvy * p.js; e += t1n) wy[e] = __ldg(sy + e);
-                for (int e = threadIdx.x; e < ti.nvx * p.js; e += t1n) wx[e] = __ldg(sx + e);
+                const A *sy = band_y + size_t(ty) * ngy * p.js_y, *sx = band_x + size_t(tx) * ngx * p.js_x;
+                for (int e = threadIdx.x; e < ti.nvy * p.js_y; e += t1n) wy[e] = __ldg(sy + e);
+                for (int e = threadIdx.x; e < ti.nvx * p.js_x; e += t1n) wx[e] = __ldg(sx + e);
                 named_sync(1, t1n);
             }
             // the pass-2 warps must be done with buffer b (tile i - 2)
@@ -410,31 +453,67 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                     continue;
                 }
                 const int c0 = k * 32 * V + lane;
-                A acc[G][V];
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-#pragma unroll
-                    for (int v = 0; v < V; ++v) acc[g][v] = A(0);
                 const T *col = tin + rb * p.box_w + c0;
-                const A *wq = wys + q * p.js;
-#pragma unroll 4
-                for (int j = 0; j < J; ++j) {
-                    A w[G];
-                    load_w<A, G>(w, wq);
-                    wq += G;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const A d = to_acc<A, T>(col[32 * v]);
-#pragma unroll
-                        for (int g = 0; g < G; ++g) acc[g][v] = fma(w[g], d, acc[g][v]);
-                    }
-                    col += p.box_w;
-                }
                 A *dst = tt + q * G * p.pitch_t + c0;
+                if constexpr (kPacked) {
+                    // column pairs (v, v+1) share one packed FMA; the vertical
+                    // band holds every weight twice, so pairs load as they are
+                    uint64_t acc2[G][V / 2];
 #pragma unroll
-                for (int g = 0; g < G; ++g)
+                    for (int g = 0; g < G; ++g)
 #pragma unroll
-                    for (int v = 0; v < V; ++v) dst[g * p.pitch_t + 32 * v] = acc[g][v];
+                        for (int u = 0; u < V / 2; ++u) acc2[g][u] = 0ull;
+                    const uint64_t *wq = reinterpret_cast<const uint64_t *>(wys + q * p.js_y);
+#pragma unroll 4
+                    for (int j = 0; j < J; ++j) {
+                        uint64_t w2[G];
+                        load_pairs<G>(w2, wq);
+                        wq += G;
+                        float d[V];
+#pragma unroll
+                        for (int v = 0; v < V; ++v) d[v] = to_acc<A, T>(col[32 * v]);
+#pragma unroll
+                        for (int u = 0; u < V / 2; ++u) {
+                            const uint64_t dd = pack2(d[2 * u], d[2 * u + 1]);
+#pragma unroll
+                            for (int g = 0; g < G; ++g) acc2[g][u] = fma2(w2[g], dd, acc2[g][u]);
+                        }
+                        col += p.box_w;
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+#pragma unroll
+                        for (int u = 0; u < V / 2; ++u) {
+                            float lo, hi;
+                            unpack2(acc2[g][u], lo, hi);
+                            dst[g * p.pitch_t + 32 * (2 * u)] = lo;
+                            dst[g * p.pitch_t + 32 * (2 * u + 1)] = hi;
+                        }
+                } else {
+                    A acc[G][V];
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[g][v] = A(0);
+                    const A *wq = wys + q * p.js_y;
+#pragma unroll 4
+                    for (int j = 0; j < J; ++j) {
+                        A w[G];
+                        load_w<A, G>(w, wq);
+                        wq += G;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const A dv = to_acc<A, T>(col[32 * v]);
+#pragma unroll
+                            for (int g = 0; g < G; ++g) acc[g][v] = fma(w[g], dv, acc[g][v]);
+                        }
+                        col += p.box_w;
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) dst[g * p.pitch_t + 32 * v] = acc[g][v];
+                }
             }
             // hand the pass-2 record (offsets and x weights) over with buffer b
             Rec2 *r2 = rec2(b);
@@ -449,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
             {
                 const A *src = stage_wx(s);
                 A *dst = rec2_w(b);
-                for (int e = threadIdx.x; e < ti.nvx * p.js; e += t1n) dst[e] = src[e];
+                for (int e = threadIdx.x; e < ti.nvx * p.js_x; e += t1n) dst[e] = src[e];
             }
             mbar_arrive(&ttfull[b]);
             // every pass-1 warp is done with stage s before it is refilled
@@ -490,24 +569,53 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                     continue;
                 }
                 A acc[G][C];
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-#pragma unroll
-                    for (int c = 0; c < C; ++c) acc[g][c] = A(0);
                 const A *rowp = tt + row * p.pitch_t + cb;
-                const A *wq = wxs + q * p.js;
+                const A *wq = wxs + q * p.js_x;
+                if constexpr (kPacked && G % 2 == 0) {
+                    // member pairs (g, g+1) share one packed FMA; their weights
+                    // are adjacent in the band
+                    uint64_t acc2[G / 2][C];
+#pragma unroll
+                    for (int h = 0; h < G / 2; ++h)
+#pragma unroll
+                        for (int c = 0; c < C; ++c) acc2[h][c] = 0ull;
+                    const uint64_t *wq2 = reinterpret_cast<const uint64_t *>(wq);
 #pragma unroll 4
-                for (int j = 0; j < J; ++j) {
-                    A w[G];
-                    load_w<A, G>(w, wq);
-                    wq += G;
+                    for (int j = 0; j < J; ++j) {
+                        uint64_t w2[G / 2];
+                        load_pairs<G / 2>(w2, wq2);
+                        wq2 += G / 2;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        const A d = rowp[c];
+                        for (int c = 0; c < C; ++c) {
+                            const float dv = rowp[c];
+                            const uint64_t dd = pack2(dv, dv);
 #pragma unroll
-                        for (int g = 0; g < G; ++g) acc[g][c] = fma(w[g], d, acc[g][c]);
+                            for (int h = 0; h < G / 2; ++h) acc2[h][c] = fma2(w2[h], dd, acc2[h][c]);
+                        }
+                        rowp += C;
                     }
-                    rowp += C;
+#pragma unroll
+                    for (int h = 0; h < G / 2; ++h)
+#pragma unroll
+                        for (int c = 0; c < C; ++c) unpack2(acc2[h][c], acc[2 * h][c], acc[2 * h + 1][c]);
+                } else {
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+#pragma unroll
+                        for (int c = 0; c < C; ++c) acc[g][c] = A(0);
+#pragma unroll 4
+                    for (int j = 0; j < J; ++j) {
+                        A w[G];
+                        load_w<A, G>(w, wq);
+                        wq += G;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) {
+                            const A d = rowp[c];
+#pragma unroll
+                            for (int g = 0; g < G; ++g) acc[g][c] = fma(w[g], d, acc[g][c]);
+                        }
+                        rowp += C;
+                    }
                 }
                 // Store G*C contiguous samples of this row (clipped at the right edge).
                 const int64_t x0 = int64_t(gx) * G;

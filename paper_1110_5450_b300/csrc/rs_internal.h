@@ -40,11 +40,12 @@ struct AxisTables {
     double *w64 = nullptr;    // [n_out][t_eff] folded normalised FP64 weights
     void *wwork = nullptr;    // [n_out][t_eff] working precision (float or double)
     // Weight band for the fused kernel: outputs are grouped G at a time;
-    // group g reads inputs [base[g], base[g] + J) with weight
-    // band_w[g * band_stride(G, J) + j * G + r] for member r and input j.
+    // group g reads inputs [base[g], base[g] + J) with the weight of member r
+    // and input j stored `dup` times (1, or 2 for packed-pair FMAs) at
+    // band_w[g * band_stride(G * dup, J) + (j * G + r) * dup + d].
     int32_t *band_base = nullptr; // [groups]
-    void *band_w = nullptr;       // [groups][band_stride(G, J)] working precision
-    int32_t G = 0, J = 0, groups = 0;
+    void *band_w = nullptr;       // [groups][band_stride(G * dup, J)] working precision
+    int32_t G = 0, J = 0, groups = 0, dup = 1;
 };
 
 // Floats per band group: J * G rounded up to a multiple of 4, so that every

@@ -234,15 +234,14 @@ __global__ void __launch_bounds__(kThreadsW) weights_kernel(WeightArgs a0, Weigh
     if (nb > 0) axis_block(A, o0, nb, jlo_s, cnt_s, slot_s, val_s, sum_s, start_s);
 }
 
-// Band element (group grp, tap j, member r) of one axis.  Layout:
-// band_w[grp * JS + j * G + r], JS = band_stride(G, J) (a multiple of 4).
+// Band element e of group grp of one axis.  Layout:
+// band_w[grp * JS + (j * G + r) * dup + d], JS = band_stride(G * dup, J).
 template <typename W>
 __device__ void band_element(const WeightArgs &A, int64_t grp, int e)
 {
     const AxisGeom &g = A.g;
     const AxisTables &T = A.t;
-    const int G = T.G, J = T.J, te = g.t_eff;
-    const int JS = band_stride(G, J);
+    const int G = T.G, J = T.J, te = g.t_eff, dup = T.dup;
     int64_t b0 = g.n_in, hi = 0;
     for (int r = 0; r < G; ++r) {
         const int64_t i = grp * G + r;
@@ -258,18 +257,19 @@ __device__ void band_element(const WeightArgs &A, int64_t grp, int e)
         if (!fits) flag_error(A.err, kErrBand);
     }
     W v = W(0);
-    const int j = e / G, r = e % G;
+    const int idx = e / dup;
+    const int j = idx / G, r = idx % G;
     const int64_t i = grp * G + r;
     if (j < J && i < g.n_out && fits) {
         const int64_t off = T.start[i] - b;
         if (j >= off && j < off + te) v = static_cast<const W *>(T.wwork)[i * te + (j - off)];
     }
-    static_cast<W *>(T.band_w)[grp * JS + e] = v;
+    static_cast<W *>(T.band_w)[grp * band_stride(G * dup, J) + e] = v;
 }
 
 __global__ void band_kernel(WeightArgs a0, WeightArgs a1)
 {
-    const int64_t js0 = band_stride(a0.t.G, a0.t.J), js1 = band_stride(a1.t.G, a1.t.J);
+    const int64_t js0 = band_stride(a0.t.G * a0.t.dup, a0.t.J), js1 = band_stride(a1.t.G * a1.t.dup, a1.t.J);
     const int64_t n0 = int64_t(a0.t.groups) * js0, n1 = int64_t(a1.t.groups) * js1;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n0 + n1;
          t += int64_t(gridDim.x) * blockDim.x) {
@@ -309,8 +309,8 @@ cudaError_t launch_weights(const WeightArgs &a0, const WeightArgs &a1, cudaStrea
 
 cudaError_t launch_band(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s)
 {
-    const int64_t n = int64_t(a0.t.groups) * band_stride(a0.t.G, a0.t.J) +
-                      int64_t(a1.t.groups) * band_stride(a1.t.G, a1.t.J);
+    const int64_t n = int64_t(a0.t.groups) * band_stride(a0.t.G * a0.t.dup, a0.t.J) +
+                      int64_t(a1.t.groups) * band_stride(a1.t.G * a1.t.dup, a1.t.J);
     const int threads = 256;
     int64_t blocks = (n + threads - 1) / threads;
     if (blocks > 148 * 16) blocks = 148 * 16;
