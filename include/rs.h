@@ -212,6 +212,49 @@ RS_API rs_status rs_plan_get_tables(const rs_plan *plan, int axis, int32_t *h_jl
 #define RS_STATIC_SCRATCH_BYTES (32u << 20)
 RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in, void *d_out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: uneven images resampled by one persistent kernel launch.
+ *
+ * Every image keeps its own descriptor (size, scale, kernel, boundary and
+ * flags may differ); channels (1 or 3) and dtype must be equal across the
+ * batch.  Work items are (image, output tile) pairs handed out by an atomic
+ * counter, so images of very different sizes balance across the GPU.  The
+ * launch (parameter upload, counter reset, kernel) is a CUDA graph built at
+ * creation and replayed by rs_batch_run.
+ * ---------------------------------------------------------------------- */
+typedef struct rs_batch rs_batch;
+
+/* Plans n images (n >= 1) and builds the batch's CUDA graphs.  Synchronises
+ * `stream`.  Returns RS_ERR_UNSUPPORTED when an image cannot use the fused
+ * kernel (more than 4 channels, or bands too wide). */
+RS_API rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream, rs_batch **out);
+
+/* Resamples image i from d_in[i] into d_out[i] (device pointers laid
+ * out as for rs_resample of descriptor i) by replaying the batch graph on
+ * `stream`; asynchronous.  The host arrays are read during the call.  When the
+ * batch was planned for TMA (all row pitches 16-byte multiples), every d_in[i]
+ * must be 16-byte aligned (RS_ERR_INVALID_ARG otherwise). */
+RS_API rs_status rs_batch_run(rs_batch *batch, const void *const *d_in, void *const *d_out, void *stream);
+
+/* Measured autotuning of the batch launch (group size, per-image tile
+ * budget, warp split) on the given buffers (outputs are overwritten).
+ * Synchronises `stream`.  cache_path as for rs_plan_autotune (may be NULL). */
+RS_API rs_status rs_batch_autotune(rs_batch *batch, const void *const *d_in, void *const *d_out, void *stream,
+                                   const char *cache_path);
+
+typedef struct {
+    int32_t n_images, total_tiles;
+    int32_t group, warps_pass1, stages, use_tma;
+    int32_t smem_bytes, ctas_per_sm, grid;
+    int64_t out_pixels;          /* sum of out_h * out_w                      */
+    int64_t in_bytes, out_bytes; /* algorithmic bytes: every input and output once */
+} rs_batch_info;
+
+RS_API rs_status rs_batch_get_info(const rs_batch *batch, rs_batch_info *info);
+
+/* Frees the batch after waiting for its work.  NULL is accepted. */
+RS_API rs_status rs_batch_destroy(rs_batch *batch);
+
 /* Synchronise the device and report any device-side error word the plan's
  * kernels set (RS_CHECK builds and bounded waits); clears the word. */
 RS_API rs_status rs_plan_check(rs_plan *plan);

@@ -64,6 +64,15 @@ class rs_plan_info(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_int64)]
 
 
+class rs_batch_info(ctypes.Structure):
+    _fields_ = [("n_images", ctypes.c_int32), ("total_tiles", ctypes.c_int32),
+                ("group", ctypes.c_int32), ("warps_pass1", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("use_tma", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("out_pixels", ctypes.c_int64),
+                ("in_bytes", ctypes.c_int64), ("out_bytes", ctypes.c_int64)]
+
+
 _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -93,11 +102,23 @@ _lib.rs_plan_autotune.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_char_p]
 _lib.rs_resample_noalloc.restype = ctypes.c_int
 _lib.rs_resample_noalloc.argtypes = [ctypes.POINTER(rs_plan_desc), _vp, _vp, _vp]
 RS_STATIC_SCRATCH_BYTES = 32 << 20
+_vpp = ctypes.POINTER(ctypes.c_void_p)
+_lib.rs_batch_create.restype = ctypes.c_int
+_lib.rs_batch_create.argtypes = [ctypes.POINTER(rs_plan_desc), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
+_lib.rs_batch_run.restype = ctypes.c_int
+_lib.rs_batch_run.argtypes = [_vp, _vpp, _vpp, _vp]
+_lib.rs_batch_autotune.restype = ctypes.c_int
+_lib.rs_batch_autotune.argtypes = [_vp, _vpp, _vpp, _vp, ctypes.c_char_p]
+_lib.rs_batch_get_info.restype = ctypes.c_int
+_lib.rs_batch_get_info.argtypes = [_vp, ctypes.POINTER(rs_batch_info)]
+_lib.rs_batch_destroy.restype = ctypes.c_int
+_lib.rs_batch_destroy.argtypes = [_vp]
 
 # Every symbol include/rs.h declares (checked by the CPU test suite).
 EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
            "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version",
-           "rs_resample_noalloc", "rs_plan_autotune"]
+           "rs_resample_noalloc", "rs_plan_autotune", "rs_batch_create", "rs_batch_run",
+           "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy"]
 
 
 class RSError(RuntimeError):
@@ -182,6 +203,38 @@ def rs_plan_get_tables(plan: int, axis: int):
 
 def rs_plan_check(plan: int) -> None:
     _check(_lib.rs_plan_check(_vp(plan)), "rs_plan_check")
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[int(x) for x in ptrs])
+    return arr
+
+
+def rs_batch_create(descs, stream: int = 0) -> int:
+    arr = (rs_plan_desc * len(descs))(*descs)
+    h = _vp()
+    _check(_lib.rs_batch_create(arr, len(descs), _vp(stream), ctypes.byref(h)), "rs_batch_create")
+    return h.value
+
+
+def rs_batch_run(batch: int, d_in, d_out, stream: int = 0) -> None:
+    _check(_lib.rs_batch_run(_vp(batch), _ptr_array(d_in), _ptr_array(d_out), _vp(stream)), "rs_batch_run")
+
+
+def rs_batch_autotune(batch: int, d_in, d_out, stream: int = 0, cache_path=None) -> None:
+    cp = None if cache_path is None else os.fsencode(cache_path)
+    _check(_lib.rs_batch_autotune(_vp(batch), _ptr_array(d_in), _ptr_array(d_out), _vp(stream), cp),
+           "rs_batch_autotune")
+
+
+def rs_batch_get_info(batch: int) -> rs_batch_info:
+    info = rs_batch_info()
+    _check(_lib.rs_batch_get_info(_vp(batch), ctypes.byref(info)), "rs_batch_get_info")
+    return info
+
+
+def rs_batch_destroy(batch: int) -> None:
+    _check(_lib.rs_batch_destroy(_vp(batch)), "rs_batch_destroy")
 
 
 def out_size(n: int, scale: float) -> int:
@@ -283,6 +336,59 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             rs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Uneven images resampled by one persistent launch (replayed CUDA graph).
+
+    ``specs``: sequence of dicts with in_h, in_w and either out_h/out_w or
+    scale, plus kernel/param/boundary; channels and dtype are batch-wide.
+    """
+
+    def __init__(self, specs, channels=1, dtype=None, in_pitches=None, stream=None):
+        import torch
+
+        if dtype is None:
+            dtype = torch.float32
+        self.torch_dtype = dtype
+        self.channels = channels
+        descs = []
+        for i, sp in enumerate(specs):
+            sc = sp.get("scale", 0.0)
+            pitch = 0 if in_pitches is None else int(in_pitches[i])
+            descs.append(make_desc(sp["in_h"], sp["in_w"], channels, sp.get("out_h", 0), sp.get("out_w", 0),
+                                   sc, sc, sp.get("kernel", "lanczos"), sp.get("param"),
+                                   sp.get("boundary", "mirror"), _torch_dtype_code(dtype),
+                                   sp.get("flags", 0), pitch, 0))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = rs_batch_create(descs, s.cuda_stream)
+        self.descs = descs
+        self.info = rs_batch_get_info(self.handle)
+
+    def __call__(self, ins, outs, stream=None):
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rs_batch_run(self.handle, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], s.cuda_stream)
+
+    def autotune(self, ins, outs, stream=None, cache_path=None):
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rs_batch_autotune(self.handle, [t.data_ptr() for t in ins], [t.data_ptr() for t in outs], s.cuda_stream,
+                          cache_path)
+        self.info = rs_batch_get_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,514 @@
+// rs_batch.cu -- batches of uneven images in one persistent fused launch.
+//
+// Each image gets an ordinary plan (exact taps, FP64 weight tables); the batch
+// then re-plans every image's fused configuration under one launch-wide
+// choice (kernel variant = group size G, warp split n1, staged-buffer count,
+// shared-memory budget per CTA) and lays out device arrays of per-image kernel
+// parameters, per-image TMA tensor maps and the tile prefix sums.  A launch is
+// an explicitly built CUDA graph: upload of the parameters and tensor maps from
+// pinned host memory, reset of the work counter, the kernel.  Two such graphs
+// alternate over two pinned staging buffers, so the host can prepare run k+1
+// while run k is still on the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rs_plan.h"
+
+using namespace rs;
+
+struct rs_batch {
+    std::vector<rs_plan *> plans;
+    int dtype = 0, C = 0;
+    // launch-wide choice
+    int G = 0, n1 = 4, stages = 1, use_tma = 0, budget_ctas = 2;
+    const fused::Variant *variant = nullptr;
+    size_t smem = 0;
+    int grid = 0, ctas = 0;
+    int total_tiles = 0;
+    int64_t out_pixels = 0, in_bytes = 0, out_bytes = 0;
+    fused::Work work{};
+    fused::Params p0{}; // carries the error word
+    DeviceBuf dparams, dmaps, dtileoff, dcounter, derr;
+    // two pinned staging buffers (parameters + tensor maps) and their graphs
+    void *host_stage[2] = {nullptr, nullptr};
+    std::vector<const void *> staged_in[2];
+    std::vector<void *> staged_out[2];
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    int next = 0;
+    CUtensorMap dummy_map;
+
+    ~rs_batch()
+    {
+        for (int k = 0; k < 2; ++k) {
+            if (exec[k]) cudaGraphExecDestroy(exec[k]);
+            if (graph[k]) cudaGraphDestroy(graph[k]);
+            if (done[k]) cudaEventDestroy(done[k]);
+            if (host_stage[k]) cudaFreeHost(host_stage[k]);
+        }
+        for (rs_plan *p : plans) rs_destroy(p);
+    }
+};
+
+namespace {
+
+size_t stage_bytes(int n)
+{
+    // parameters, then the tensor maps at a 64-byte boundary
+    return ((sizeof(fused::Params) * size_t(n) + 63) / 64) * 64 + sizeof(CUtensorMap) * size_t(n);
+}
+
+// Combined shared memory of per-image configurations: each region sized for
+// the largest image.
+size_t combined_smem(const std::vector<Candidate> &pick, const std::vector<rs_plan *> &plans, int dtype,
+                     int stages)
+{
+    const size_t esz = dt_size(dtype), asz = dtype == RS_F64 ? 8 : 4;
+    size_t tin = 0, wy = 0, wx = 0, tt = 0, r2 = 0;
+    for (size_t i = 0; i < pick.size(); ++i) {
+        const Candidate &c = pick[i];
+        const int dup = plans[i]->work_double ? 1 : 2;
+        const int V = plans[i]->work_double ? 2 : 4;
+        const int w1 = (c.box_w + 32 * V - 1) / (32 * V) * (32 * V);
+        const fused::Layout L = fused::layout(esz, asz, c.box_h, c.box_w, c.tile_h / c.G, c.tile_w / c.G,
+                                              band_stride(c.G * dup, c.J), band_stride(c.G, c.J), c.tile_h,
+                                              w1 | 1, 1);
+        tin = std::max(tin, L.tin);
+        wy = std::max(wy, L.wy);
+        wx = std::max(wx, L.wx);
+        tt = std::max(tt, L.tt);
+        r2 = std::max(r2, L.rec2);
+    }
+    return fused::layout_of(tin, wy, wx, tt, r2, stages).total;
+}
+
+// Picks every image's configuration for a launch-wide (G, stages, budget):
+// the cheapest candidate per image under a per-image cap, the cap tightened
+// until the regions' maxima fit budget_ctas CTAs per SM.  Applies the picks
+// when `apply`; returns the modelled total cost in SM cycles (inf if some
+// image has no feasible configuration).
+double plan_images(rs_batch *b, cudaStream_t stream, int G, int stages, int budget_ctas, bool apply, rs_status *st)
+{
+    *st = RS_OK;
+    const size_t target = (227 * 1024) / size_t(budget_ctas);
+    std::vector<Candidate> pick(b->plans.size());
+    std::vector<std::vector<Candidate>> all(b->plans.size());
+    for (size_t i = 0; i < b->plans.size(); ++i) all[i] = enumerate_candidates(b->plans[i], b->use_tma != 0);
+    double total = INFINITY;
+    for (size_t cap = target; cap >= 8 * 1024; cap = cap * 85 / 100) {
+        total = 0.0;
+        bool ok = true;
+        for (size_t i = 0; i < b->plans.size() && ok; ++i) {
+            const Candidate *best = nullptr;
+            for (const Candidate &c : all[i]) {
+                if (c.G != G || c.stages != stages || c.smem > cap) continue;
+                if (!best || c.cost < best->cost) best = &c;
+            }
+            if (!best) {
+                ok = false;
+                break;
+            }
+            pick[i] = *best;
+            total += best->cost * double(b->plans[i]->gy.n_out) * double(b->plans[i]->gx.n_out);
+        }
+        if (!ok) return INFINITY;
+        if (combined_smem(pick, b->plans, b->dtype, b->use_tma ? stages : 1) <= target) break;
+        total = INFINITY;
+    }
+    if (!std::isfinite(total) || !apply) return total;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        Candidate c = pick[i];
+        c.n1 = b->n1;
+        *st = apply_fused(b->plans[i], stream, c, b->use_tma != 0);
+        if (*st != RS_OK) return INFINITY;
+    }
+    return total;
+}
+
+rs_status build_launch(rs_batch *b, cudaStream_t stream)
+{
+    const int n = int(b->plans.size());
+    // maxima over the images carve the shared memory identically in every CTA
+    fused::Work &w = b->work;
+    std::memset(&w, 0, sizeof w);
+    std::vector<int32_t> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const rs_plan *p = b->plans[i];
+        const fused::Params &fp = p->fp;
+        off[i + 1] = off[i] + fp.tiles_y * fp.tiles_x;
+        fused::Work r;
+        work_regions(p, &r);
+        w.tin_bytes = std::max(w.tin_bytes, r.tin_bytes);
+        w.wy_bytes = std::max(w.wy_bytes, r.wy_bytes);
+        w.wx_bytes = std::max(w.wx_bytes, r.wx_bytes);
+        w.tt_bytes = std::max(w.tt_bytes, r.tt_bytes);
+        w.rec2_bytes = std::max(w.rec2_bytes, r.rec2_bytes);
+    }
+    b->total_tiles = off[n];
+    w.n_images = n;
+    w.total_tiles = off[n];
+    w.stages = b->stages;
+    w.n1 = b->n1;
+    w.use_tma = b->use_tma;
+    b->smem = fused::layout_of(w.tin_bytes, w.wy_bytes, w.wx_bytes, w.tt_bytes, w.rec2_bytes,
+                               b->use_tma ? b->stages : 1)
+                  .total;
+    if (b->smem > 227 * 1024) return fail(RS_ERR_UNSUPPORTED, "batch: shared memory of the largest tiles too big");
+    b->variant = b->plans[0]->variant;
+    cudaError_t e = cudaFuncSetAttribute(b->variant->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    int occ = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->variant->fn, fused::kThreads, b->smem);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: occupancy");
+    if (occ < 1) return fail(RS_ERR_UNSUPPORTED, "batch: kernel does not fit on an SM");
+    b->ctas = occ;
+    b->grid = int(std::min<int64_t>(b->total_tiles, int64_t(occ) * b->plans[0]->num_sms));
+
+    // device arrays (re)allocated for this configuration
+    b->dparams.~DeviceBuf();
+    new (&b->dparams) DeviceBuf();
+    b->dmaps.~DeviceBuf();
+    new (&b->dmaps) DeviceBuf();
+    b->dtileoff.~DeviceBuf();
+    new (&b->dtileoff) DeviceBuf();
+    e = cudaMalloc(&b->dparams.p, sizeof(fused::Params) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dmaps.p, sizeof(CUtensorMap) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dtileoff.p, sizeof(int32_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->dtileoff.p, off.data(), sizeof(int32_t) * (n + 1),
+                                              cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: allocating launch arrays");
+    w.imgs = static_cast<const fused::Params *>(b->dparams.p);
+    w.maps = static_cast<const CUtensorMap *>(b->dmaps.p);
+    w.tile_off = static_cast<const int32_t *>(b->dtileoff.p);
+    w.counter = static_cast<int32_t *>(b->dcounter.p);
+    b->p0.err = static_cast<int *>(b->derr.p);
+
+    // the two launch graphs
+    for (int k = 0; k < 2; ++k) {
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+        b->exec[k] = nullptr;
+        b->graph[k] = nullptr;
+        b->staged_in[k].assign(n, nullptr);
+        b->staged_out[k].assign(n, nullptr);
+        e = cudaGraphCreate(&b->graph[k], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "batch: graph");
+        unsigned char *hs = static_cast<unsigned char *>(b->host_stage[k]);
+        const size_t pmap = ((sizeof(fused::Params) * size_t(n) + 63) / 64) * 64;
+        cudaGraphNode_t n_par, n_map, n_set, n_ker;
+        e = cudaGraphAddMemcpyNode1D(&n_par, b->graph[k], nullptr, 0, b->dparams.p, hs, sizeof(fused::Params) * n,
+                                     cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaGraphAddMemcpyNode1D(&n_map, b->graph[k], nullptr, 0, b->dmaps.p, hs + pmap,
+                                         sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice);
+        cudaMemsetParams ms;
+        std::memset(&ms, 0, sizeof ms);
+        ms.dst = b->dcounter.p;
+        ms.value = 0;
+        ms.elementSize = 4;
+        ms.width = 1;
+        ms.height = 1;
+        if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n_set, b->graph[k], nullptr, 0, &ms);
+        void *args[3] = {&b->dummy_map, &b->p0, &b->work};
+        cudaKernelNodeParams kp;
+        std::memset(&kp, 0, sizeof kp);
+        kp.func = const_cast<void *>(b->variant->fn);
+        kp.gridDim = dim3(b->grid);
+        kp.blockDim = dim3(fused::kThreads);
+        kp.sharedMemBytes = unsigned(b->smem);
+        kp.kernelParams = args;
+        cudaGraphNode_t deps[3] = {n_par, n_map, n_set};
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_ker, b->graph[k], deps, 3, &kp);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "batch: building the launch graph");
+    }
+    return RS_OK;
+}
+
+rs_status configure(rs_batch *b, cudaStream_t stream, int G, int stages, int budget, int n1)
+{
+    b->G = G;
+    b->stages = stages;
+    b->budget_ctas = budget;
+    b->n1 = n1;
+    rs_status st;
+    const double cost = plan_images(b, stream, G, stages, budget, true, &st);
+    if (st != RS_OK) return st;
+    if (!std::isfinite(cost)) return fail(RS_ERR_UNSUPPORTED, "batch: no configuration fits every image");
+    return build_launch(b, stream);
+}
+
+bool valid_ptrs(const rs_batch *b, const void *const *d_in, void *const *d_out)
+{
+    if (!d_in || !d_out) return false;
+    for (size_t i = 0; i < b->plans.size(); ++i)
+        if (!d_in[i] || !d_out[i]) return false;
+    return true;
+}
+
+} // namespace
+
+extern "C" {
+
+rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, rs_batch **out)
+{
+    if (!out) return fail(RS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || n < 1 || n > (1 << 20)) return fail(RS_ERR_INVALID_ARG, "batch: need 1 .. 2^20 descriptors");
+    for (int i = 1; i < n; ++i)
+        if (descs[i].channels != descs[0].channels || descs[i].in_dtype != descs[0].in_dtype)
+            return fail(RS_ERR_UNSUPPORTED, "batch: channels and dtype must be equal across the batch");
+    if (descs[0].channels != 1 && descs[0].channels != 3)
+        return fail(RS_ERR_UNSUPPORTED, "batch: 1 or 3 channels");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    rs_batch *b = new (std::nothrow) rs_batch();
+    if (!b) return fail(RS_ERR_OOM, "host allocation failed");
+    b->dtype = descs[0].in_dtype;
+    b->C = descs[0].channels;
+    bool all_tma = true;
+    for (int i = 0; i < n; ++i) {
+        rs_plan_desc d = descs[i];
+        d.flags &= ~uint32_t(RS_TWO_PASS);
+        rs_plan *p = nullptr;
+        rs_status st = rs_plan_create(&d, stream, &p);
+        if (st != RS_OK) {
+            delete b;
+            return st;
+        }
+        b->plans.push_back(p);
+        if (p->path != 0) {
+            delete b;
+            return fail(RS_ERR_UNSUPPORTED, "batch: an image cannot use the fused kernel");
+        }
+        all_tma = all_tma && tma_layout_ok(p);
+        b->out_pixels += int64_t(p->gy.n_out) * p->gx.n_out;
+        b->in_bytes += int64_t(p->gy.n_in) * p->gx.n_in * b->C * int64_t(dt_size(b->dtype));
+        b->out_bytes += int64_t(p->gy.n_out) * p->gx.n_out * b->C * int64_t(dt_size(b->dtype));
+    }
+    b->use_tma = all_tma ? 1 : 0;
+    cudaError_t e = cudaMalloc(&b->dcounter.p, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&b->derr.p, 16);
+    if (e == cudaSuccess) e = cudaMemset(b->derr.p, 0, 16);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaHostAlloc(&b->host_stage[k], stage_bytes(n), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(b->done[k], stream);
+    }
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch: allocations");
+    }
+    std::memset(&b->dummy_map, 0, sizeof b->dummy_map);
+    // model-chosen launch-wide configuration: the cheapest (G, stages, budget)
+    double best = INFINITY;
+    int bg = 0, bs = 1, bb = 2;
+    for (int G : {4, 2, 1}) {
+        if (!b->plans[0]->variant) break;
+        for (int stages : {2, 1}) {
+            if (stages == 2 && !b->use_tma) continue;
+            for (int budget : {2, 3}) {
+                rs_status st;
+                const double c = plan_images(b, stream, G, stages, budget, false, &st);
+                if (c < best) {
+                    best = c;
+                    bg = G;
+                    bs = stages;
+                    bb = budget;
+                }
+            }
+        }
+    }
+    if (!std::isfinite(best)) {
+        delete b;
+        return fail(RS_ERR_UNSUPPORTED, "batch: no configuration fits every image");
+    }
+    rs_status st = configure(b, stream, bg, bs, bb, 4);
+    if (st != RS_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return RS_OK;
+}
+
+rs_status rs_batch_run(rs_batch *b, const void *const *d_in, void *const *d_out, void *stream_v)
+{
+    if (!b || !valid_ptrs(b, d_in, d_out)) return fail(RS_ERR_INVALID_ARG, "batch: NULL batch or buffer");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const int n = int(b->plans.size());
+    if (b->use_tma)
+        for (int i = 0; i < n; ++i)
+            if (reinterpret_cast<uintptr_t>(d_in[i]) & 15u)
+                return fail(RS_ERR_INVALID_ARG, "batch: inputs must be 16-byte aligned (planned for TMA)");
+    const int k = b->next;
+    b->next ^= 1;
+    // the staging buffer k was last read by the run recorded on done[k]
+    cudaError_t e = cudaEventSynchronize(b->done[k]);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: waiting for the staging buffer");
+    unsigned char *hs = static_cast<unsigned char *>(b->host_stage[k]);
+    fused::Params *hp = reinterpret_cast<fused::Params *>(hs);
+    CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(hs + ((sizeof(fused::Params) * size_t(n) + 63) / 64) * 64);
+    for (int i = 0; i < n; ++i) {
+        if (b->staged_in[k][i] == d_in[i] && b->staged_out[k][i] == d_out[i]) continue;
+        fused::Params fp = b->plans[i]->fp;
+        fp.in = d_in[i];
+        fp.out = d_out[i];
+        fp.use_tma = b->use_tma;
+        fp.err = b->p0.err;
+        hp[i] = fp;
+        if (b->use_tma) {
+            rs_status st = encode_tensor_map(b->plans[i], d_in[i], &hm[i]);
+            if (st != RS_OK) return st;
+        } else {
+            std::memset(&hm[i], 0, sizeof(CUtensorMap));
+        }
+        b->staged_in[k][i] = d_in[i];
+        b->staged_out[k][i] = d_out[i];
+    }
+    e = cudaGraphLaunch(b->exec[k], stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->done[k], stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: graph launch");
+    return RS_OK;
+}
+
+rs_status rs_batch_autotune(rs_batch *b, const void *const *d_in, void *const *d_out, void *stream_v,
+                            const char *cache_path)
+{
+    if (!b || !valid_ptrs(b, d_in, d_out)) return fail(RS_ERR_INVALID_ARG, "batch: NULL batch or buffer");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    // cache key: the count and a hash of the descriptors
+    uint64_t h = 1469598103934665603ull;
+    for (rs_plan *p : b->plans) {
+        const unsigned char *q = reinterpret_cast<const unsigned char *>(&p->desc);
+        for (size_t i = 0; i < sizeof(rs_plan_desc); ++i) h = (h ^ q[i]) * 1099511628211ull;
+    }
+    char key[128];
+    std::snprintf(key, sizeof key, "batch|n%zu|h%016llx", b->plans.size(), (unsigned long long)h);
+    if (cache_path) {
+        FILE *f = std::fopen(cache_path, "r");
+        if (f) {
+            char line[512];
+            int G = 0, st = 0, bud = 0, n1 = 0;
+            bool hit = false;
+            while (std::fgets(line, sizeof line, f)) {
+                if (!std::strstr(line, key)) continue;
+                const char *q = std::strstr(line, "\"G\":");
+                if (q && std::sscanf(q, "\"G\": %d, \"stages\": %d, \"budget\": %d, \"n1\": %d", &G, &st, &bud,
+                                     &n1) == 4)
+                    hit = true;
+            }
+            std::fclose(f);
+            if (hit) return configure(b, stream, G, st, bud, n1);
+        }
+    }
+    auto time_run = [&](double *ms_out) -> rs_status {
+        cudaEvent_t a, c;
+        cudaEventCreate(&a);
+        cudaEventCreate(&c);
+        rs_status s = rs_batch_run(b, d_in, d_out, stream);
+        cudaEventRecord(a, stream);
+        for (int r = 0; r < 3 && s == RS_OK; ++r) s = rs_batch_run(b, d_in, d_out, stream);
+        cudaEventRecord(c, stream);
+        cudaError_t e = cudaEventSynchronize(c);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, c);
+        cudaEventDestroy(a);
+        cudaEventDestroy(c);
+        if (s != RS_OK) return s;
+        if (e != cudaSuccess) return cuda_fail(e, "batch: timing");
+        int herr = 0;
+        e = cudaMemcpy(&herr, b->derr.p, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "batch: error word");
+        if (herr) return fail(RS_ERR_DEVICE, "batch: device error word set while tuning");
+        *ms_out = ms / 3.0;
+        return RS_OK;
+    };
+    struct Cfg {
+        int G, stages, budget, n1;
+    };
+    Cfg best{b->G, b->stages, b->budget_ctas, b->n1};
+    double best_ms = INFINITY;
+    std::vector<Cfg> trial;
+    for (int G : {4, 2, 1})
+        for (int stages : {2, 1})
+            for (int budget : {2, 3}) {
+                if (stages == 2 && !b->use_tma) continue;
+                trial.push_back({G, stages, budget, 4});
+            }
+    for (const Cfg &c : trial) {
+        if (configure(b, stream, c.G, c.stages, c.budget, c.n1) != RS_OK) continue;
+        double ms;
+        rs_status s = time_run(&ms);
+        if (s != RS_OK) return s;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    const Cfg coarse = best;
+    for (int n1 = 2; n1 <= 6; ++n1) {
+        if (n1 == coarse.n1) continue;
+        Cfg c = coarse;
+        c.n1 = n1;
+        if (configure(b, stream, c.G, c.stages, c.budget, c.n1) != RS_OK) continue;
+        double ms;
+        rs_status s = time_run(&ms);
+        if (s != RS_OK) return s;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    rs_status s = configure(b, stream, best.G, best.stages, best.budget, best.n1);
+    if (s != RS_OK) return s;
+    if (cache_path && std::isfinite(best_ms)) {
+        FILE *f = std::fopen(cache_path, "a");
+        if (f) {
+            std::fprintf(f, "{\"key\": \"%s\", \"G\": %d, \"stages\": %d, \"budget\": %d, \"n1\": %d, \"ms\": %.4f}\n",
+                         key, best.G, best.stages, best.budget, best.n1, best_ms);
+            std::fclose(f);
+        }
+    }
+    return RS_OK;
+}
+
+rs_status rs_batch_get_info(const rs_batch *b, rs_batch_info *info)
+{
+    if (!b || !info) return fail(RS_ERR_INVALID_ARG, "NULL argument");
+    std::memset(info, 0, sizeof *info);
+    info->n_images = int32_t(b->plans.size());
+    info->total_tiles = b->total_tiles;
+    info->group = b->G;
+    info->warps_pass1 = b->n1;
+    info->stages = b->use_tma ? b->stages : 1;
+    info->use_tma = b->use_tma;
+    info->smem_bytes = int32_t(b->smem);
+    info->ctas_per_sm = b->ctas;
+    info->grid = b->grid;
+    info->out_pixels = b->out_pixels;
+    info->in_bytes = b->in_bytes;
+    info->out_bytes = b->out_bytes;
+    return RS_OK;
+}
+
+rs_status rs_batch_destroy(rs_batch *b)
+{
+    if (!b) return RS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    // report a device-side error raised by the batch kernel before freeing
+    int herr = 0;
+    if (e == cudaSuccess && b->derr.p) e = cudaMemcpy(&herr, b->derr.p, 4, cudaMemcpyDeviceToHost);
+    delete b;
+    if (e != cudaSuccess) return cuda_fail(e, "batch: synchronising before destroy");
+    if (herr) return fail(RS_ERR_DEVICE, "batch: device error word set");
+    return RS_OK;
+}
+
+} // extern "C"

@@ -12,8 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "rs_fused.cuh"
-#include "rs_internal.h"
+#include "rs_plan.h"
 
 namespace rs {
 
@@ -78,63 +77,14 @@ int support_radius(int kernel, double param)
     return 0;
 }
 
-struct DeviceBuf {
-    void *p = nullptr;
-    size_t n = 0;
-    ~DeviceBuf()
-    {
-        if (p) cudaFree(p);
-    }
-};
 
-// Carve 256-byte aligned pieces out of one allocation.
-struct Carver {
-    size_t off = 0;
-    size_t take(size_t bytes)
-    {
-        size_t o = off;
-        off += (bytes + 255) & ~size_t(255);
-        return o;
-    }
-};
-
-struct Candidate {
-    int G = 0, J = 0, tile_h = 0, tile_w = 0, stages = 1, box_h = 0, box_w = 0, n_sub = 1, sub_h = 0, n1 = 4;
-    size_t smem = 0;
-    double cost = 0.0; // modelled SM cycles per output pixel
-};
 
 } // namespace
 } // namespace rs
 
 using namespace rs;
 
-struct rs_plan {
-    rs_plan_desc desc{};
-    int device = 0;
-    int num_sms = 0;
-    AxisGeom gy, gx;
-    AxisTables ty, tx;
-    int work_double = 0;
-    int path = 1; // 0 fused, 1 two-pass
-    DeviceBuf tables, bands, tmp, errbuf;
-    int *d_err = nullptr;
-    // fused
-    fused::Params fp{};
-    const fused::Variant *variant = nullptr;
-    int G = 0, J = 0;
-    size_t smem = 0;
-    int grid = 0;
-    int ctas_per_sm = 0;
-    int tma_ok = 0;
-    CUtensorMap tmap;
-    const void *tmap_ptr = nullptr;
-    int64_t scratch_bytes = 0;
-    std::vector<int32_t> host_start_y, host_start_x; // for re-planning and tuning
-    Candidate chosen;                                // fused configuration in use
-};
-
-namespace {
+namespace rs {
 
 rs_status fail(rs_status s, const std::string &msg)
 {
@@ -480,9 +430,8 @@ rs_status choose_fused(rs_plan *p, cudaStream_t stream)
     return apply_fused(p, stream, *best, tma);
 }
 
-rs_status encode_map(rs_plan *p, const void *d_in)
+rs_status encode_tensor_map(const rs_plan *p, const void *d_in, CUtensorMap *map)
 {
-    if (p->tmap_ptr == d_in) return RS_OK;
     const rs_plan_desc &d = p->desc;
     CUtensorMapDataType t = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     switch (d.in_dtype) {
@@ -496,7 +445,7 @@ rs_status encode_map(rs_plan *p, const void *d_in)
     cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * int64_t(esz))};
     cuuint32_t box[2] = {cuuint32_t(p->fp.box_w), cuuint32_t(p->fp.sub_h)};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode_fn()(&p->tmap, t, 2, const_cast<void *>(d_in), dims, strides, box, estr,
+    CUresult r = encode_fn()(map, t, 2, const_cast<void *>(d_in), dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -504,8 +453,43 @@ rs_status encode_map(rs_plan *p, const void *d_in)
         std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", int(r));
         return fail(RS_ERR_CUDA, buf);
     }
+    return RS_OK;
+}
+
+rs_status encode_map(rs_plan *p, const void *d_in)
+{
+    if (p->tmap_ptr == d_in) return RS_OK;
+    rs_status s = encode_tensor_map(p, d_in, &p->tmap);
+    if (s != RS_OK) return s;
     p->tmap_ptr = d_in;
     return RS_OK;
+}
+
+void work_regions(const rs_plan *p, fused::Work *w)
+{
+    const fused::Params &fp = p->fp;
+    const size_t esz = dt_size(p->desc.in_dtype), asz = p->work_double ? 8 : 4;
+    const fused::Layout L = fused::layout(esz, asz, fp.box_h, fp.box_w, fp.tile_h / p->G, fp.tile_w / p->G,
+                                          fp.js_y, fp.js_x, fp.tile_h, fp.pitch_t, 1);
+    w->tin_bytes = int32_t(L.tin);
+    w->wy_bytes = int32_t(L.wy);
+    w->wx_bytes = int32_t(L.wx);
+    w->tt_bytes = int32_t(L.tt);
+    w->rec2_bytes = int32_t(L.rec2);
+}
+
+fused::Work single_work(const rs_plan *p, int use_tma)
+{
+    fused::Work w;
+    std::memset(&w, 0, sizeof w);
+    const fused::Params &fp = p->fp;
+    w.n_images = 1;
+    w.total_tiles = fp.tiles_y * fp.tiles_x;
+    work_regions(p, &w);
+    w.stages = use_tma ? fp.stages : 1;
+    w.n1 = fp.n1;
+    w.use_tma = use_tma;
+    return w;
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -559,7 +543,7 @@ void cache_store(const char *path, const std::string &key, const Candidate &c, d
 // Mean launch time (µs) of the plan's current configuration.
 rs_status time_plan(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s, double *us);
 
-} // namespace
+} // namespace rs
 
 extern "C" {
 
@@ -726,7 +710,8 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
         } else {
             fp.stages = 1;
         }
-        void *args[2] = {&p->tmap, &fp};
+        fused::Work w = single_work(p, fp.use_tma);
+        void *args[3] = {&p->tmap, &fp, &w};
         e = cudaLaunchKernel(p->variant->fn, dim3(p->grid), dim3(fused::kThreads), args, smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
         return RS_OK;
@@ -911,7 +896,7 @@ rs_status rs_plan_check(rs_plan *p)
 
 } // extern "C"
 
-namespace {
+namespace rs {
 rs_status time_plan(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s, double *us)
 {
     cudaEvent_t a, b;
@@ -950,4 +935,4 @@ rs_status time_plan(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s, d
     *us = 1000.0 * ms / reps;
     return RS_OK;
 }
-} // namespace
+} // namespace rs

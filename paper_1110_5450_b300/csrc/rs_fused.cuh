@@ -166,7 +166,25 @@ struct Params {
     int *err;
 };
 
+// Work of one launch: a single image (tiles in a static round-robin order),
+// or a batch of images whose tiles are handed out by an atomic counter.
+struct Work {
+    const Params *imgs;      // batch: device array of per-image parameters; nullptr: single image
+    const CUtensorMap *maps; // batch: per-image tensor maps in global memory (64-byte aligned)
+    const int32_t *tile_off; // batch: tiles of images [0, k) = tile_off[k], n_images + 1 entries
+    int32_t n_images;
+    int32_t total_tiles;
+    int32_t *counter;        // batch: work counter, zero at launch
+    // shared-memory carving: byte sizes of the regions (maxima over the
+    // images), and launch-wide choices
+    int32_t tin_bytes, wy_bytes, wx_bytes, tt_bytes, rec2_bytes;
+    int32_t stages, n1, use_tma;
+};
+
 struct TileInfo {
+    Params P;       // parameters of the tile's image
+    int32_t img;    // image index, -1 marks the end of the work
+    int32_t t;      // tile index within the image
     int32_t ry0;    // first staged input row
     int32_t xs;     // first staged input sample (aligned down to 16 bytes)
     int32_t nvy;    // valid y-groups in the tile
@@ -198,7 +216,8 @@ template <typename A, int G> __device__ __forceinline__ void load_w(A (&w)[G], c
 
 // Pass-2 record of one intermediate buffer (written by the pass-1 warps).
 struct Rec2 {
-    int32_t ty, tx, nvx, pad;
+    Params P;   // parameters of the tile's image
+    int32_t img, ty, tx, nvx;
     int32_t cb[32];
 };
 
@@ -212,6 +231,20 @@ __host__ __device__ inline size_t rec2_bytes(int ngx, int js, size_t acc)
 struct Layout {
     size_t tin, wy, wx, stage, tt, rec2, total;
 };
+
+__host__ __device__ inline Layout layout_of(size_t tin, size_t wy, size_t wx, size_t tt, size_t rec2, int nstage)
+{
+    Layout L;
+    L.tin = tin;
+    L.wy = wy;
+    L.wx = wx;
+    L.stage = L.tin + L.wy + L.wx;
+    L.tt = tt;
+    L.rec2 = rec2;
+    L.total = 128 + size_t(nstage) * L.stage + 2 * L.tt + 2 * L.rec2 + align_up(2 * sizeof(TileInfo), 128) + 64 +
+              1024;
+    return L;
+}
 
 __host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int box_w, int ngy, int ngx, int js_y,
                                          int js_x, int tile_h, int pitch_t, int nstage)
@@ -296,7 +329,8 @@ template <int N> __device__ __forceinline__ void load_pairs(uint64_t (&w)[N], co
 }
 
 template <typename T, int C, int G, int V>
-__global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+__global__ void __launch_bounds__(kThreads, 3)
+    fused_kernel(const __grid_constant__ CUtensorMap tmap, const Params p0, const Work w)
 {
     using A = typename AccOf<T>::type;
     // FP32 accumulation uses packed-pair FMAs (the FP64 path stays scalar)
@@ -305,10 +339,9 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    const int ngy = p.tile_h / G, ngx = p.tile_w / G;
-    const int nstage = (p.use_tma && p.stages == 2) ? 2 : 1;
-    const Layout L =
-        layout(sizeof(T), sizeof(A), p.box_h, p.box_w, ngy, ngx, p.js_y, p.js_x, p.tile_h, p.pitch_t, nstage);
+    const bool batch = w.imgs != nullptr;
+    const int nstage = (w.use_tma && w.stages == 2) ? 2 : 1;
+    const Layout L = layout_of(w.tin_bytes, w.wy_bytes, w.wx_bytes, w.tt_bytes, w.rec2_bytes, nstage);
     unsigned char *after_stages = smem + nstage * L.stage;
     A *tt0 = reinterpret_cast<A *>(after_stages);
     unsigned char *rec_base = after_stages + 2 * L.tt;
@@ -319,13 +352,9 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 6);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n1 = p.n1;                 // pass-1 (and staging) warps
-    const int n2 = kWarps - n1;          // pass-2 warps
-    const int total = p.tiles_y * p.tiles_x;
-    const T *in = static_cast<const T *>(p.in);
-    T *out = static_cast<T *>(p.out);
-    const A *band_y = static_cast<const A *>(p.band_y);
-    const A *band_x = static_cast<const A *>(p.band_x);
+    const int n1 = w.n1;        // staging + pass-1 warps
+    const int n2 = kWarps - n1; // pass-2 warps
+    int *err = p0.err;
 
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
@@ -346,15 +375,53 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
     auto rec2 = [&](int b) { return reinterpret_cast<Rec2 *>(rec_base + b * L.rec2); };
     auto rec2_w = [&](int b) { return reinterpret_cast<A *>(rec_base + b * L.rec2 + sizeof(Rec2)); };
 
-    // Staged rectangle, valid groups and per-group band offsets of tile t
-    // (one full warp; lane 0 writes the scalars).
-    auto rect = [&](int t, TileInfo *rec) {
-        const int ty = t / p.tiles_x, tx = t % p.tiles_x;
+    // The producer (warp 0) takes the k-th tile of this CTA: its image, the
+    // image's parameters, the staged rectangle and the per-group offsets.
+    // Returns false (and records img = -1) when the work is exhausted.
+    auto take_tile = [&](int k, TileInfo *rec) -> bool {
+        int item = -1, img = 0, t = 0;
+        if (lane == 0) {
+            if (!batch) {
+                const int total = p0.tiles_y * p0.tiles_x;
+                const int it = int(blockIdx.x) + k * int(gridDim.x);
+                item = it < total ? it : -1;
+                t = item;
+            } else {
+                const int it = atomicAdd(w.counter, 1);
+                if (it < w.total_tiles) {
+                    item = it;
+                    int lo = 0, hi = w.n_images - 1; // last image with tile_off[img] <= it
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (__ldg(w.tile_off + mid) <= it) lo = mid; else hi = mid - 1;
+                    }
+                    img = lo;
+                    t = it - __ldg(w.tile_off + lo);
+                }
+            }
+        }
+        item = __shfl_sync(0xffffffffu, item, 0);
+        img = __shfl_sync(0xffffffffu, img, 0);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (item < 0) {
+            if (lane == 0) rec->img = -1;
+            __syncwarp();
+            return false;
+        }
+        {   // copy the image's parameters into the record (word by word)
+            const int32_t *src = reinterpret_cast<const int32_t *>(batch ? w.imgs + img : &p0);
+            int32_t *dst = reinterpret_cast<int32_t *>(&rec->P);
+            for (int e = lane; e < int(sizeof(Params) / 4); e += 32) dst[e] = src[e];
+        }
+        __syncwarp();
+        const Params &P = rec->P;
+        const int ngy = P.tile_h / G, ngx = P.tile_w / G;
+        const int ty = t / P.tiles_x, tx = t % P.tiles_x;
         const int gy0 = ty * ngy, gx0 = tx * ngx;
-        const bool vy = lane < ngy && gy0 + lane < p.groups_y;
-        const bool vx = lane < ngx && gx0 + lane < p.groups_x;
-        const int by = vy ? __ldg(p.base_y + gy0 + lane) : INT_MAX;
-        const int bx = vx ? __ldg(p.base_x + gx0 + lane) : INT_MAX;
+        const bool vy = lane < ngy && gy0 + lane < P.groups_y;
+        const bool vx = lane < ngx && gx0 + lane < P.groups_x;
+        const int by = vy ? __ldg(P.base_y + gy0 + lane) : INT_MAX;
+        const int bx = vx ? __ldg(P.base_x + gx0 + lane) : INT_MAX;
         int ylo = by, xlo = bx;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -366,74 +433,97 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
         if (vy) rec->rb[lane] = by - ylo;
         if (vx) rec->cb[lane] = bx * C - xs;
         if (lane == 0) {
+            rec->img = img;
+            rec->t = t;
             rec->ry0 = ylo;
             rec->xs = xs;
-            rec->nvy = min(ngy, p.groups_y - gy0);
-            rec->nvx = min(ngx, p.groups_x - gx0);
+            rec->nvy = min(ngy, P.groups_y - gy0);
+            rec->nvx = min(ngx, P.groups_x - gx0);
         }
         __syncwarp();
+        return true;
     };
 
-    // TMA producer (warp 0): rectangle, then lane 0 issues the copies of stage s.
-    auto produce = [&](int t, int s) {
-        rect(t, &info[s]);
+    // TMA producer (warp 0): take the k-th tile, lane 0 issues its copies into
+    // stage s (or arrives without bytes at the end of the work).
+    auto produce = [&](int k, int s) {
+        const bool ok = take_tile(k, &info[s]);
         if (lane == 0) {
+            if (!ok) {
+                mbar_arrive(&full[s]);
+                return;
+            }
             const TileInfo &ti = info[s];
-            const int ty = t / p.tiles_x, tx = t % p.tiles_x;
-            const uint32_t by = uint32_t(ti.nvy) * p.js_y * sizeof(A);
-            const uint32_t bx = uint32_t(ti.nvx) * p.js_x * sizeof(A);
-            const uint32_t bt = uint32_t(p.n_sub) * p.sub_h * p.box_w * sizeof(T);
+            const Params &P = ti.P;
+            const int ngy = P.tile_h / G, ngx = P.tile_w / G;
+            const int ty = ti.t / P.tiles_x, tx = ti.t % P.tiles_x;
+            const uint32_t by = uint32_t(ti.nvy) * P.js_y * sizeof(A);
+            const uint32_t bx = uint32_t(ti.nvx) * P.js_x * sizeof(A);
+            const uint32_t bt = uint32_t(P.n_sub) * P.sub_h * P.box_w * sizeof(T);
             mbar_arrive_expect_tx(&full[s], bt + by + bx);
+            const CUtensorMap *map = batch ? w.maps + ti.img : &tmap;
             T *dst = stage_tin(s);
-            for (int k = 0; k < p.n_sub; ++k)
-                tma_load_2d(dst + size_t(k) * p.sub_h * p.box_w, &tmap, &full[s], ti.xs, ti.ry0 + k * p.sub_h);
-            bulk_load(stage_wy(s), band_y + size_t(ty) * ngy * p.js_y, by, &full[s]);
-            bulk_load(stage_wx(s), band_x + size_t(tx) * ngx * p.js_x, bx, &full[s]);
+            for (int q = 0; q < P.n_sub; ++q)
+                tma_load_2d(dst + size_t(q) * P.sub_h * P.box_w, map, &full[s], ti.xs, ti.ry0 + q * P.sub_h);
+            bulk_load(stage_wy(s), static_cast<const A *>(P.band_y) + size_t(ty) * ngy * P.js_y, by, &full[s]);
+            bulk_load(stage_wx(s), static_cast<const A *>(P.band_x) + size_t(tx) * ngx * P.js_x, bx, &full[s]);
         }
     };
-
-    const int J = p.J;
-    const int my_tiles = int(blockIdx.x) < total ? (total - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
 
     if (warp < n1) {
         // ======================= staging + pass 1 =======================
         const int t1n = 32 * n1;
-        if (p.use_tma && warp == 0) {
-            for (int k = 0; k < nstage && k < my_tiles; ++k) produce(blockIdx.x + k * gridDim.x, k);
+        if (w.use_tma && warp == 0) {
+            for (int k = 0; k < nstage; ++k) produce(k, k);
         }
-        for (int i = 0; i < my_tiles; ++i) {
-            const int t = blockIdx.x + i * gridDim.x;
-            const int ty = t / p.tiles_x, tx = t % p.tiles_x;
+        for (int i = 0;; ++i) {
             const int s = nstage == 2 ? (i & 1) : 0;
             const int b = i & 1;
-            if (p.use_tma) {
+            if (w.use_tma) {
                 const uint32_t par = nstage == 2 ? uint32_t((i >> 1) & 1) : uint32_t(i & 1);
-                if (!wait_or_abort(&full[s], par, abort_flag, p.err)) break;
+                if (!wait_or_abort(&full[s], par, abort_flag, err)) break;
             } else {
-                if (warp == 0) rect(t, &info[0]);
+                if (warp == 0) take_tile(i, &info[0]);
                 named_sync(1, t1n);
                 const TileInfo &ti = info[0];
-                const int64_t row_len = p.in_w * C;
-                T *tin = stage_tin(0);
-                for (int r = warp; r < p.box_h; r += n1) {
-                    const int64_t gy = int64_t(ti.ry0) + r;
-                    T *dst = tin + size_t(r) * p.box_w;
-                    for (int c = lane; c < p.box_w; c += 32) {
-                        const int64_t gx = int64_t(ti.xs) + c;
-                        T v = from_acc<T, A>(A(0));
-                        if (gy < p.in_h && gx < row_len) v = in[gy * p.in_stride + gx];
-                        dst[c] = v;
+                if (ti.img >= 0) {
+                    const Params &P = ti.P;
+                    const T *in = static_cast<const T *>(P.in);
+                    const int ngy = P.tile_h / G, ngx = P.tile_w / G;
+                    const int ty = ti.t / P.tiles_x, tx = ti.t % P.tiles_x;
+                    const int64_t row_len = P.in_w * C;
+                    T *tin = stage_tin(0);
+                    for (int r = warp; r < P.box_h; r += n1) {
+                        const int64_t gy = int64_t(ti.ry0) + r;
+                        T *dst = tin + size_t(r) * P.box_w;
+                        for (int c = lane; c < P.box_w; c += 32) {
+                            const int64_t gx = int64_t(ti.xs) + c;
+                            T v = from_acc<T, A>(A(0));
+                            if (gy < P.in_h && gx < row_len) v = in[gy * P.in_stride + gx];
+                            dst[c] = v;
+                        }
                     }
+                    A *wy = stage_wy(0), *wx = stage_wx(0);
+                    const A *sy = static_cast<const A *>(P.band_y) + size_t(ty) * ngy * P.js_y;
+                    const A *sx = static_cast<const A *>(P.band_x) + size_t(tx) * ngx * P.js_x;
+                    for (int e = threadIdx.x; e < ti.nvy * P.js_y; e += t1n) wy[e] = __ldg(sy + e);
+                    for (int e = threadIdx.x; e < ti.nvx * P.js_x; e += t1n) wx[e] = __ldg(sx + e);
                 }
-                A *wy = stage_wy(0), *wx = stage_wx(0);
-                const A *sy = band_y + size_t(ty) * ngy * p.js_y, *sx = band_x + size_t(tx) * ngx * p.js_x;
-                for (int e = threadIdx.x; e < ti.nvy * p.js_y; e += t1n) wy[e] = __ldg(sy + e);
-                for (int e = threadIdx.x; e < ti.nvx * p.js_x; e += t1n) wx[e] = __ldg(sx + e);
                 named_sync(1, t1n);
             }
             // the pass-2 warps must be done with buffer b (tile i - 2)
-            if (i >= 2 && !wait_or_abort(&ttempty[b], uint32_t(((i >> 1) - 1) & 1), abort_flag, p.err)) break;
+            if (i >= 2 && !wait_or_abort(&ttempty[b], uint32_t(((i >> 1) - 1) & 1), abort_flag, err)) break;
             const TileInfo &ti = info[s];
+            Rec2 *r2 = rec2(b);
+            if (ti.img < 0) {
+                // end of the work: pass it on to the pass-2 warps and stop
+                if (threadIdx.x == 0) r2->img = -1;
+                mbar_arrive(&ttfull[b]);
+                break;
+            }
+            const Params &P = ti.P;
+            const int J = P.J;
+            const int box_w = P.box_w, pitch_t = P.pitch_t;
             const T *tin = stage_tin(s);
             const A *wys = stage_wy(s);
             A *tt = tt_buf(b);
@@ -441,20 +531,20 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
             // pass 1: lanes along samples; V columns 32 apart per lane.  Chunks
             // past box_w read harmless staged data and land in the padding of
             // the intermediate (pitch_t >= w1): no predicate in the inner loop.
-            const int nchunk = p.w1 / (32 * V);
+            const int nchunk = P.w1 / (32 * V);
             const int ntask = ti.nvy * nchunk;
             const int per = (ntask + n1 - 1) / n1;
             const int k0 = warp * per, k1 = min(ntask, k0 + per);
             for (int task = k0; task < k1; ++task) {
                 const int q = task / nchunk, k = task - q * nchunk;
                 const int rb = ti.rb[q];
-                if (rb < 0 || rb + J > p.box_h) {
-                    if (lane == 0) flag(p.err, kErrBounds);
+                if (rb < 0 || rb + J > P.box_h) {
+                    if (lane == 0) flag(err, kErrBounds);
                     continue;
                 }
                 const int c0 = k * 32 * V + lane;
-                const T *col = tin + rb * p.box_w + c0;
-                A *dst = tt + q * G * p.pitch_t + c0;
+                const T *col = tin + rb * box_w + c0;
+                A *dst = tt + q * G * pitch_t + c0;
                 if constexpr (kPacked) {
                     // column pairs (v, v+1) share one packed FMA; the vertical
                     // band holds every weight twice, so pairs load as they are
@@ -463,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                     for (int g = 0; g < G; ++g)
 #pragma unroll
                         for (int u = 0; u < V / 2; ++u) acc2[g][u] = 0ull;
-                    const uint64_t *wq = reinterpret_cast<const uint64_t *>(wys + q * p.js_y);
+                    const uint64_t *wq = reinterpret_cast<const uint64_t *>(wys + q * P.js_y);
 #pragma unroll 4
                     for (int j = 0; j < J; ++j) {
                         uint64_t w2[G];
@@ -478,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
 #pragma unroll
                             for (int g = 0; g < G; ++g) acc2[g][u] = fma2(w2[g], dd, acc2[g][u]);
                         }
-                        col += p.box_w;
+                        col += box_w;
                     }
 #pragma unroll
                     for (int g = 0; g < G; ++g)
@@ -486,8 +576,8 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                         for (int u = 0; u < V / 2; ++u) {
                             float lo, hi;
                             unpack2(acc2[g][u], lo, hi);
-                            dst[g * p.pitch_t + 32 * (2 * u)] = lo;
-                            dst[g * p.pitch_t + 32 * (2 * u + 1)] = hi;
+                            dst[g * pitch_t + 32 * (2 * u)] = lo;
+                            dst[g * pitch_t + 32 * (2 * u + 1)] = hi;
                         }
                 } else {
                     A acc[G][V];
@@ -495,82 +585,90 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                     for (int g = 0; g < G; ++g)
 #pragma unroll
                         for (int v = 0; v < V; ++v) acc[g][v] = A(0);
-                    const A *wq = wys + q * p.js_y;
+                    const A *wq = wys + q * P.js_y;
 #pragma unroll 4
                     for (int j = 0; j < J; ++j) {
-                        A w[G];
-                        load_w<A, G>(w, wq);
+                        A wv[G];
+                        load_w<A, G>(wv, wq);
                         wq += G;
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             const A dv = to_acc<A, T>(col[32 * v]);
 #pragma unroll
-                            for (int g = 0; g < G; ++g) acc[g][v] = fma(w[g], dv, acc[g][v]);
+                            for (int g = 0; g < G; ++g) acc[g][v] = fma(wv[g], dv, acc[g][v]);
                         }
-                        col += p.box_w;
+                        col += box_w;
                     }
 #pragma unroll
                     for (int g = 0; g < G; ++g)
 #pragma unroll
-                        for (int v = 0; v < V; ++v) dst[g * p.pitch_t + 32 * v] = acc[g][v];
+                        for (int v = 0; v < V; ++v) dst[g * pitch_t + 32 * v] = acc[g][v];
                 }
             }
-            // hand the pass-2 record (offsets and x weights) over with buffer b
-            Rec2 *r2 = rec2(b);
+            // hand the pass-2 record (parameters, offsets and x weights) over with buffer b
+            {
+                const int32_t *src = reinterpret_cast<const int32_t *>(&ti.P);
+                int32_t *dstp = reinterpret_cast<int32_t *>(&r2->P);
+                for (int e = threadIdx.x; e < int(sizeof(Params) / 4); e += t1n) dstp[e] = src[e];
+            }
             if (threadIdx.x < 32) {
-                if (lane < ngx) r2->cb[lane] = ti.cb[lane];
+                if (lane < P.tile_w / G) r2->cb[lane] = ti.cb[lane];
                 if (lane == 0) {
-                    r2->ty = ty;
-                    r2->tx = tx;
+                    r2->img = ti.img;
+                    r2->ty = ti.t / P.tiles_x;
+                    r2->tx = ti.t % P.tiles_x;
                     r2->nvx = ti.nvx;
                 }
             }
             {
                 const A *src = stage_wx(s);
-                A *dst = rec2_w(b);
-                for (int e = threadIdx.x; e < ti.nvx * p.js_x; e += t1n) dst[e] = src[e];
+                A *dstw = rec2_w(b);
+                for (int e = threadIdx.x; e < ti.nvx * P.js_x; e += t1n) dstw[e] = src[e];
             }
             mbar_arrive(&ttfull[b]);
             // every pass-1 warp is done with stage s before it is refilled
             named_sync(1, t1n);
-            if (p.use_tma && warp == 0) {
-                const int in_ = i + nstage;
-                if (in_ < my_tiles) produce(blockIdx.x + in_ * gridDim.x, s);
-            }
+            if (w.use_tma && warp == 0) produce(i + nstage, s);
         }
     } else {
         // =========================== pass 2 ============================
         const int w2 = warp - n1;
-        const int RB = p.tile_h < 32 ? p.tile_h : 32; // rows per warp task
-        const int GPW = 32 / RB;                      // groups per warp task
-        const int rsub = lane % RB, gsub = lane / RB;
-        for (int i = 0; i < my_tiles; ++i) {
+        for (int i = 0;; ++i) {
             const int b = i & 1;
-            if (!wait_or_abort(&ttfull[b], uint32_t((i >> 1) & 1), abort_flag, p.err)) break;
+            if (!wait_or_abort(&ttfull[b], uint32_t((i >> 1) & 1), abort_flag, err)) break;
             const Rec2 *r2 = rec2(b);
+            if (r2->img < 0) break;
+            const Params &P = r2->P;
             const A *tt = tt_buf(b);
             const A *wxs = rec2_w(b);
+            const int J = P.J;
+            const int pitch_t = P.pitch_t;
+            const int ngx = P.tile_w / G;
             const int ty = r2->ty, tx = r2->tx, nvx = r2->nvx;
-            const int nrb = (p.tile_h + RB - 1) / RB;
+            const int RB = P.tile_h < 32 ? P.tile_h : 32; // rows per warp task
+            const int GPW = 32 / RB;                      // groups per warp task
+            const int rsub = lane % RB, gsub = lane / RB;
+            const int nrb = (P.tile_h + RB - 1) / RB;
             const int npg = (nvx + GPW - 1) / GPW;
             const int ntask = nrb * npg;
             const int per = (ntask + n2 - 1) / n2;
             const int k0 = w2 * per, k1 = min(ntask, k0 + per);
+            T *out = static_cast<T *>(P.out);
             for (int task = k0; task < k1; ++task) {
                 const int rbk = task / npg, pg = task - rbk * npg;
                 const int q = pg * GPW + gsub;
                 const int row = rbk * RB + rsub;
-                const int64_t yo = int64_t(ty) * p.tile_h + row;
+                const int64_t yo = int64_t(ty) * P.tile_h + row;
                 const int gx = tx * ngx + q;
-                if (q >= nvx || row >= p.tile_h || yo >= p.out_h) continue;
+                if (q >= nvx || row >= P.tile_h || yo >= P.out_h) continue;
                 const int cb = r2->cb[q];
-                if (cb < 0 || cb + J * C > p.box_w) {
-                    flag(p.err, kErrBounds);
+                if (cb < 0 || cb + J * C > P.box_w) {
+                    flag(err, kErrBounds);
                     continue;
                 }
                 A acc[G][C];
-                const A *rowp = tt + row * p.pitch_t + cb;
-                const A *wq = wxs + q * p.js_x;
+                const A *rowp = tt + row * pitch_t + cb;
+                const A *wq = wxs + q * P.js_x;
                 if constexpr (kPacked && G % 2 == 0) {
                     // member pairs (g, g+1) share one packed FMA; their weights
                     // are adjacent in the band
@@ -582,15 +680,15 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                     const uint64_t *wq2 = reinterpret_cast<const uint64_t *>(wq);
 #pragma unroll 4
                     for (int j = 0; j < J; ++j) {
-                        uint64_t w2[G / 2];
-                        load_pairs<G / 2>(w2, wq2);
+                        uint64_t wp[G / 2];
+                        load_pairs<G / 2>(wp, wq2);
                         wq2 += G / 2;
 #pragma unroll
                         for (int c = 0; c < C; ++c) {
                             const float dv = rowp[c];
                             const uint64_t dd = pack2(dv, dv);
 #pragma unroll
-                            for (int h = 0; h < G / 2; ++h) acc2[h][c] = fma2(w2[h], dd, acc2[h][c]);
+                            for (int h = 0; h < G / 2; ++h) acc2[h][c] = fma2(wp[h], dd, acc2[h][c]);
                         }
                         rowp += C;
                     }
@@ -605,22 +703,22 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
                         for (int c = 0; c < C; ++c) acc[g][c] = A(0);
 #pragma unroll 4
                     for (int j = 0; j < J; ++j) {
-                        A w[G];
-                        load_w<A, G>(w, wq);
+                        A wv[G];
+                        load_w<A, G>(wv, wq);
                         wq += G;
 #pragma unroll
                         for (int c = 0; c < C; ++c) {
                             const A d = rowp[c];
 #pragma unroll
-                            for (int g = 0; g < G; ++g) acc[g][c] = fma(w[g], d, acc[g][c]);
+                            for (int g = 0; g < G; ++g) acc[g][c] = fma(wv[g], d, acc[g][c]);
                         }
                         rowp += C;
                     }
                 }
                 // Store G*C contiguous samples of this row (clipped at the right edge).
                 const int64_t x0 = int64_t(gx) * G;
-                T *o = out + yo * p.out_stride + x0 * C;
-                const int nvalid = p.out_w - x0 < G ? int(p.out_w - x0) : G;
+                T *o = out + yo * P.out_stride + x0 * C;
+                const int nvalid = P.out_w - x0 < G ? int(P.out_w - x0) : G;
                 constexpr int kRun = G * C;
                 constexpr int kRunBytes = kRun * int(sizeof(T));
                 if (nvalid == G && (kRunBytes % 16) == 0 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
@@ -648,7 +746,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_kernel(const __grid_constan
     }
     // On an abort some TMA copies may still be in flight; let them land
     // (bounded) before the CTA's shared memory is released.
-    if (*abort_flag && p.use_tma && warp == 0) {
+    if (*abort_flag && w.use_tma && warp == 0) {
         mbar_wait_bounded(&full[0], 0u);
         mbar_wait_bounded(&full[1], 0u);
     }

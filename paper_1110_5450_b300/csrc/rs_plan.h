@@ -1,0 +1,89 @@
+// rs_plan.h -- internal: the plan object and the host helpers shared by the
+// single-image entry points (rs_capi.cu) and the batch / serving code.
+#pragma once
+
+#include <cuda.h>
+
+#include <string>
+#include <vector>
+
+#include "rs_fused.cuh"
+#include "rs_internal.h"
+
+namespace rs {
+
+// One fused-kernel configuration of a plan.
+struct Candidate {
+    int G = 0, J = 0, tile_h = 0, tile_w = 0, stages = 1, box_h = 0, box_w = 0, n_sub = 1, sub_h = 0, n1 = 4;
+    size_t smem = 0;
+    double cost = 0.0; // modelled SM cycles per output pixel
+};
+
+struct DeviceBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    ~DeviceBuf()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+// Carve 256-byte aligned pieces out of one allocation.
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+} // namespace rs
+
+// The plan object behind the opaque rs_plan handle.
+struct rs_plan {
+    rs_plan_desc desc{};
+    int device = 0;
+    int num_sms = 0;
+    rs::AxisGeom gy, gx;
+    rs::AxisTables ty, tx;
+    int work_double = 0;
+    int path = 1; // 0 fused, 1 two-pass
+    rs::DeviceBuf tables, bands, tmp, errbuf;
+    int *d_err = nullptr;
+    // fused path
+    rs::fused::Params fp{};
+    const rs::fused::Variant *variant = nullptr;
+    int G = 0, J = 0;
+    size_t smem = 0;
+    int grid = 0;
+    int ctas_per_sm = 0;
+    int tma_ok = 0;
+    CUtensorMap tmap;
+    const void *tmap_ptr = nullptr;
+    int64_t scratch_bytes = 0;
+    std::vector<int32_t> host_start_y, host_start_x; // for re-planning and tuning
+    rs::Candidate chosen;                            // fused configuration in use
+};
+
+namespace rs {
+
+rs_status fail(rs_status s, const std::string &msg);
+rs_status cuda_fail(cudaError_t e, const char *what);
+// Every feasible fused configuration (needs the host start tables).
+std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout);
+// Builds the band tables of a configuration and the kernel parameters.
+rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool tma_layout);
+// Whether the plan's row pitch allows TMA tile copies.
+bool tma_layout_ok(const rs_plan *p);
+// Encodes the plan's input tensor map for d_in into *map.
+rs_status encode_tensor_map(const rs_plan *p, const void *d_in, CUtensorMap *map);
+// Shared-memory region sizes of a fused plan's configuration.
+void work_regions(const rs_plan *p, fused::Work *w);
+// Single-image work description of a fused plan.
+fused::Work single_work(const rs_plan *p, int use_tma);
+// Cost of a candidate in modelled SM cycles per output pixel (also sets n1).
+double model_cost(Candidate &c, int C, size_t esz, size_t asz, int V);
+
+} // namespace rs
