@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the model-chosen kernel configuration")
+    ap.add_argument("--batch-n", type=int, default=512, help="images in the batched section")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched section (profiling); prints its object")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines autotuner cache (a hit skips the tuning launches)")
     ap.add_argument("--size", type=int, default=4096,
@@ -192,6 +196,111 @@ def cpu_baseline(img, budget_s: float):
     return value, o.default_threads(), sample
 
 
+def batched_section(args, dev, stream):
+    """Uneven batch (512 single-channel FP16 images, sides U{64..2048}, scale
+    logU[1/4, 4], kernel U{tent, Keys -1/2, Lanczos-3}, mirror) in one
+    persistent launch replayed as a CUDA graph, against the plain per-image
+    FP32 path on the same images; error vs the FP64 oracle on a sample."""
+    import numpy as np
+    import torch
+
+    import paper_1110_5450_b300 as rs
+    import synth
+
+    specs = synth.batch_specs(args.batch_n)
+    tdt = torch.float16
+    ins16, ins32, exact, pitches, descs = [], [], [], [], []
+    for sp in specs:
+        img = synth.sinusoids(sp.in_h, sp.in_w, 1, seed=sp.seed)
+        t16 = torch.from_numpy(img).to(tdt)
+        pitch = (sp.in_w + 7) // 8 * 8          # 16-byte row pitch (TMA eligible)
+        b16 = torch.zeros((sp.in_h, pitch), dtype=tdt, device=dev)
+        b16[:, :sp.in_w] = t16[:, :, 0].to(dev)
+        ins16.append(b16)
+        ins32.append(torch.from_numpy(img).to(dev))
+        pitches.append(pitch)
+        exact.append(t16.double().numpy())
+    bspecs = [dict(in_h=sp.in_h, in_w=sp.in_w, scale=sp.scale, kernel=sp.kernel, param=sp.param,
+                   boundary="mirror") for sp in specs]
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        batch = rs.Batch(bspecs, channels=1, dtype=tdt, in_pitches=pitches, stream=stream)
+    create_s = time.perf_counter() - t0
+    outs16 = []
+    for sp, d in zip(specs, batch.descs):
+        oh = rs.out_size(sp.in_h, sp.scale)
+        ow = rs.out_size(sp.in_w, sp.scale)
+        outs16.append(torch.empty((oh, ow, 1), dtype=tdt, device=dev))
+    t0 = time.perf_counter()
+    if not args.no_tune:
+        batch.autotune(ins16, outs16, stream=stream, cache_path=args.tune_cache)
+    tune_s = time.perf_counter() - t0
+    info = batch.info
+    for _ in range(3):
+        batch(ins16, outs16, stream=stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record(stream)
+    for _ in range(reps):
+        batch(ins16, outs16, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = a.elapsed_time(b) / reps
+    # plain per-image FP32 path: one plan and one launch per image
+    plans, outs32 = [], []
+    with torch.cuda.stream(stream):
+        for sp in specs:
+            pl = rs.Plan(sp.in_h, sp.in_w, 1, scale=sp.scale, kernel=sp.kernel, param=sp.param,
+                         boundary="mirror", dtype=torch.float32, stream=stream)
+            plans.append(pl)
+            outs32.append(torch.empty(pl.out_shape, dtype=torch.float32, device=dev))
+    torch.cuda.synchronize()
+
+    def plain():
+        for pl, x, y in zip(plans, ins32, outs32):
+            pl(x, out=y, stream=stream)
+
+    plain()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(3):
+        plain()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = a.elapsed_time(b) / 3
+    # error of the batched FP16 results against the FP64 oracle (every 64th image)
+    import oracle
+
+    errs, rms = [], []
+    for i in range(0, len(specs), 64):
+        sp = specs[i]
+        got = outs16[i].double().cpu().numpy()
+        want = oracle.resample(exact[i], got.shape[0], got.shape[1], sp.kernel, "mirror", param=sp.param)
+        errs.append(float(np.abs(got - want).max()))
+        rms.append(float(np.sqrt(np.mean((got - want) ** 2))))
+    for pl in plans:
+        pl.close()
+    batch.close()
+    peak, _ = measured_peaks()
+    mpx = info.out_pixels / 1e6
+    alg = info.in_bytes + info.out_bytes
+    return {"workload": "%d single-channel FP16 images, sides U{64..2048}, scale logU[1/4,4], "
+                        "kernel U{tent, Keys -1/2, Lanczos-3}, mirror; one persistent launch (CUDA graph)"
+                        % len(specs),
+            "value": mpx / (ms_batch / 1e3), "unit": UNIT, "ms_per_batch": ms_batch,
+            "hbm_frac": alg / (ms_batch / 1e3) / 1e9 / peak, "algorithmic_bytes": alg,
+            "plain_fp32_per_image": {"value": mpx / (ms_plain / 1e3), "unit": UNIT, "ms": ms_plain,
+                                     "launches": len(specs)},
+            "speedup_vs_plain_fp32": ms_plain / ms_batch,
+            "max_abs_err_fp16_vs_oracle": max(errs), "rms_err_fp16_vs_oracle": float(np.mean(rms)),
+            "err_sample": "every 64th image", "create_s": round(create_s, 2), "autotune_s": round(tune_s, 2),
+            "config": {"group": info.group, "warps_pass1": info.warps_pass1, "stages": info.stages,
+                       "use_tma": info.use_tma, "smem": info.smem_bytes, "ctas_per_sm": info.ctas_per_sm,
+                       "tiles": info.total_tiles}}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -241,6 +350,9 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
     outs = out_sizes()
+    if args.batch_only:
+        print(json.dumps(batched_section(args, dev, stream)), flush=True)
+        return
 
     img = synth.sinusoids(N_IN, N_IN, C, seed=synth.SEED_C2 + rank)
     x = torch.from_numpy(img).to(dev)
@@ -341,6 +453,10 @@ def main():
     for p in plans:
         p.check()
 
+    batched = None
+    if not args.no_batch:
+        batched = batched_section(args, dev, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline(img, args.cpu_sample_s)
@@ -370,6 +486,7 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     for p in plans:

@@ -217,10 +217,10 @@ RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in,
  *
  * Every image keeps its own descriptor (size, scale, kernel, boundary and
  * flags may differ); channels (1 or 3) and dtype must be equal across the
- * batch.  Work items are (image, output tile) pairs handed out by an atomic
- * counter, so images of very different sizes balance across the GPU.  The
- * launch (parameter upload, counter reset, kernel) is a CUDA graph built at
- * creation and replayed by rs_batch_run.
+ * batch.  Work items are (image, output tile) pairs of the concatenated tile
+ * list, dealt round-robin to the persistent CTAs, so every image's tiles
+ * spread over the whole GPU.  The launch (parameter upload, kernel) is a CUDA
+ * graph built at creation and replayed by rs_batch_run.
  * ---------------------------------------------------------------------- */
 typedef struct rs_batch rs_batch;
 
@@ -254,6 +254,69 @@ RS_API rs_status rs_batch_get_info(const rs_batch *batch, rs_batch_info *info);
 
 /* Frees the batch after waiting for its work.  NULL is accepted. */
 RS_API rs_status rs_batch_destroy(rs_batch *batch);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop on one device.
+ *
+ * Requests (one image each; size, scale, kernel and boundary free) are
+ * submitted from any host thread.  A scheduler thread admits them in arrival
+ * order while their device state (weight and band tables, and the output
+ * when the request passes d_out = NULL) fits the server's memory budget -- a
+ * device arena allocated once -- plans each one without any host
+ * synchronisation, and launches everything admitted since the previous launch
+ * as one persistent fused launch per (channels, dtype, group size, TMA)
+ * class, on up to max_inflight streams at once.  Requests arriving while
+ * others run are admitted as memory frees and run concurrently with them.
+ * Completion is timestamped (host steady clock) by a host callback queued
+ * behind each launch.  Every request's result is bit-identical to the same
+ * resample run alone (rs_resample of the same descriptor).
+ * ---------------------------------------------------------------------- */
+typedef struct rs_server rs_server;
+
+typedef struct {
+    uint64_t budget_bytes; /* device bytes for in-flight requests (>= 1 MiB)      */
+    int32_t max_inflight;  /* launches in flight (1..8), one stream each         */
+    int32_t max_batch;     /* requests per launch (1..4096)                      */
+    int32_t warps_pass1;   /* fused-kernel warp split (0 => 4)                   */
+    int32_t reserved;
+} rs_server_desc;
+
+typedef struct {
+    rs_plan_desc desc; /* one image; channels 1 or 3; in_dtype == out_dtype            */
+    const void *d_in;  /* device input laid out as for rs_resample (client-owned)      */
+    void *d_out;       /* device output, or NULL: the server allocates it in its budget
+                          and keeps it until rs_server_release                        */
+} rs_request;
+
+typedef struct {
+    int32_t status;         /* RS_ERR_BUSY while pending, RS_OK when done, else the error */
+    int32_t launch_id;      /* launch that ran the request                              */
+    int32_t batch_size;     /* requests in that launch                                  */
+    int32_t out_h, out_w;
+    int64_t out_row_stride; /* elements                                                 */
+    void *d_out;            /* the result (device), valid once status == RS_OK          */
+    uint64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns;
+} rs_request_state;
+
+typedef struct {
+    uint64_t completed, rejected, launches, out_pixels, pending;
+    uint64_t bytes_in_use, max_bytes_in_use, max_batch;
+} rs_server_stats;
+
+RS_API rs_status rs_server_create(const rs_server_desc *desc, rs_server **out);
+/* Enqueues n requests; tickets first_ticket .. first_ticket + n - 1.  Requests
+ * that can never fit the budget complete with RS_ERR_BUDGET; malformed ones
+ * with RS_ERR_INVALID_ARG / RS_ERR_UNSUPPORTED. */
+RS_API rs_status rs_batch_submit(rs_server *server, const rs_request *reqs, int32_t n, uint64_t *first_ticket);
+RS_API rs_status rs_batch_poll(rs_server *server, uint64_t ticket, rs_request_state *state);
+/* Forgets a finished request and returns its server-allocated output to the budget. */
+RS_API rs_status rs_server_release(rs_server *server, uint64_t ticket);
+/* Waits (host, bounded by timeout_ms) until nothing is pending or in flight,
+ * then reports any device-side error word (RS_ERR_DEVICE). */
+RS_API rs_status rs_server_drain(rs_server *server, int64_t timeout_ms);
+RS_API rs_status rs_server_get_stats(rs_server *server, rs_server_stats *stats);
+/* Drains (up to 60 s), stops the scheduler and frees the server.  NULL is accepted. */
+RS_API rs_status rs_server_destroy(rs_server *server);
 
 /* Synchronise the device and report any device-side error word the plan's
  * kernels set (RS_CHECK builds and bounded waits); clears the word. */

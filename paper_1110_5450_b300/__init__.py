@@ -73,6 +73,28 @@ class rs_batch_info(ctypes.Structure):
                 ("in_bytes", ctypes.c_int64), ("out_bytes", ctypes.c_int64)]
 
 
+class rs_server_desc(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("warps_pass1", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class rs_request(ctypes.Structure):
+    _fields_ = [("desc", rs_plan_desc), ("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p)]
+
+
+class rs_request_state(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("launch_id", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("out_h", ctypes.c_int32), ("out_w", ctypes.c_int32), ("out_row_stride", ctypes.c_int64),
+                ("d_out", ctypes.c_void_p), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
+                ("t_launch_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+
+
+class rs_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("completed", "rejected", "launches", "out_pixels", "pending",
+                                               "bytes_in_use", "max_bytes_in_use", "max_batch")]
+
+
 _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -113,12 +135,28 @@ _lib.rs_batch_get_info.restype = ctypes.c_int
 _lib.rs_batch_get_info.argtypes = [_vp, ctypes.POINTER(rs_batch_info)]
 _lib.rs_batch_destroy.restype = ctypes.c_int
 _lib.rs_batch_destroy.argtypes = [_vp]
+_lib.rs_server_create.restype = ctypes.c_int
+_lib.rs_server_create.argtypes = [ctypes.POINTER(rs_server_desc), ctypes.POINTER(_vp)]
+_lib.rs_batch_submit.restype = ctypes.c_int
+_lib.rs_batch_submit.argtypes = [_vp, ctypes.POINTER(rs_request), ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+_lib.rs_batch_poll.restype = ctypes.c_int
+_lib.rs_batch_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(rs_request_state)]
+_lib.rs_server_release.restype = ctypes.c_int
+_lib.rs_server_release.argtypes = [_vp, ctypes.c_uint64]
+_lib.rs_server_drain.restype = ctypes.c_int
+_lib.rs_server_drain.argtypes = [_vp, ctypes.c_int64]
+_lib.rs_server_get_stats.restype = ctypes.c_int
+_lib.rs_server_get_stats.argtypes = [_vp, ctypes.POINTER(rs_server_stats)]
+_lib.rs_server_destroy.restype = ctypes.c_int
+_lib.rs_server_destroy.argtypes = [_vp]
 
 # Every symbol include/rs.h declares (checked by the CPU test suite).
 EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
            "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version",
            "rs_resample_noalloc", "rs_plan_autotune", "rs_batch_create", "rs_batch_run",
-           "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy"]
+           "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
+           "rs_batch_submit", "rs_batch_poll", "rs_server_release", "rs_server_drain", "rs_server_get_stats",
+           "rs_server_destroy"]
 
 
 class RSError(RuntimeError):
@@ -235,6 +273,44 @@ def rs_batch_get_info(batch: int) -> rs_batch_info:
 
 def rs_batch_destroy(batch: int) -> None:
     _check(_lib.rs_batch_destroy(_vp(batch)), "rs_batch_destroy")
+
+
+def rs_server_create(budget_bytes: int, max_inflight: int = 4, max_batch: int = 256, warps_pass1: int = 0) -> int:
+    d = rs_server_desc(int(budget_bytes), int(max_inflight), int(max_batch), int(warps_pass1), 0)
+    h = _vp()
+    _check(_lib.rs_server_create(ctypes.byref(d), ctypes.byref(h)), "rs_server_create")
+    return h.value
+
+
+def rs_batch_submit(server: int, reqs) -> int:
+    arr = (rs_request * len(reqs))(*reqs)
+    t = ctypes.c_uint64()
+    _check(_lib.rs_batch_submit(_vp(server), arr, len(reqs), ctypes.byref(t)), "rs_batch_submit")
+    return int(t.value)
+
+
+def rs_batch_poll(server: int, ticket: int) -> rs_request_state:
+    st = rs_request_state()
+    _check(_lib.rs_batch_poll(_vp(server), ctypes.c_uint64(ticket), ctypes.byref(st)), "rs_batch_poll")
+    return st
+
+
+def rs_server_release(server: int, ticket: int) -> None:
+    _check(_lib.rs_server_release(_vp(server), ctypes.c_uint64(ticket)), "rs_server_release")
+
+
+def rs_server_drain(server: int, timeout_ms: int = 60000) -> None:
+    _check(_lib.rs_server_drain(_vp(server), int(timeout_ms)), "rs_server_drain")
+
+
+def rs_server_get_stats(server: int) -> rs_server_stats:
+    st = rs_server_stats()
+    _check(_lib.rs_server_get_stats(_vp(server), ctypes.byref(st)), "rs_server_get_stats")
+    return st
+
+
+def rs_server_destroy(server: int) -> None:
+    _check(_lib.rs_server_destroy(_vp(server)), "rs_server_destroy")
 
 
 def out_size(n: int, scale: float) -> int:

@@ -6,7 +6,7 @@
 // shared-memory budget per CTA) and lays out device arrays of per-image kernel
 // parameters, per-image TMA tensor maps and the tile prefix sums.  A launch is
 // an explicitly built CUDA graph: upload of the parameters and tensor maps from
-// pinned host memory, reset of the work counter, the kernel.  Two such graphs
+// pinned host memory, then the kernel.  Two such graphs
 // alternate over two pinned staging buffers, so the host can prepare run k+1
 // while run k is still on the GPU.
 #include <algorithm>
@@ -33,7 +33,7 @@ struct rs_batch {
     int64_t out_pixels = 0, in_bytes = 0, out_bytes = 0;
     fused::Work work{};
     fused::Params p0{}; // carries the error word
-    DeviceBuf dparams, dmaps, dtileoff, dcounter, derr;
+    DeviceBuf dparams, dmaps, dtileoff, derr;
     // two pinned staging buffers (parameters + tensor maps) and their graphs
     void *host_stage[2] = {nullptr, nullptr};
     std::vector<const void *> staged_in[2];
@@ -158,7 +158,8 @@ rs_status build_launch(rs_batch *b, cudaStream_t stream)
     w.use_tma = b->use_tma;
     b->smem = fused::layout_of(w.tin_bytes, w.wy_bytes, w.wx_bytes, w.tt_bytes, w.rec2_bytes,
                                b->use_tma ? b->stages : 1)
-                  .total;
+                  .total +
+              fused::batch_extra(n);
     if (b->smem > 227 * 1024) return fail(RS_ERR_UNSUPPORTED, "batch: shared memory of the largest tiles too big");
     b->variant = b->plans[0]->variant;
     cudaError_t e = cudaFuncSetAttribute(b->variant->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -187,7 +188,6 @@ rs_status build_launch(rs_batch *b, cudaStream_t stream)
     w.imgs = static_cast<const fused::Params *>(b->dparams.p);
     w.maps = static_cast<const CUtensorMap *>(b->dmaps.p);
     w.tile_off = static_cast<const int32_t *>(b->dtileoff.p);
-    w.counter = static_cast<int32_t *>(b->dcounter.p);
     b->p0.err = static_cast<int *>(b->derr.p);
 
     // the two launch graphs
@@ -202,20 +202,12 @@ rs_status build_launch(rs_batch *b, cudaStream_t stream)
         if (e != cudaSuccess) return cuda_fail(e, "batch: graph");
         unsigned char *hs = static_cast<unsigned char *>(b->host_stage[k]);
         const size_t pmap = ((sizeof(fused::Params) * size_t(n) + 63) / 64) * 64;
-        cudaGraphNode_t n_par, n_map, n_set, n_ker;
+        cudaGraphNode_t n_par, n_map, n_ker;
         e = cudaGraphAddMemcpyNode1D(&n_par, b->graph[k], nullptr, 0, b->dparams.p, hs, sizeof(fused::Params) * n,
                                      cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaGraphAddMemcpyNode1D(&n_map, b->graph[k], nullptr, 0, b->dmaps.p, hs + pmap,
                                          sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice);
-        cudaMemsetParams ms;
-        std::memset(&ms, 0, sizeof ms);
-        ms.dst = b->dcounter.p;
-        ms.value = 0;
-        ms.elementSize = 4;
-        ms.width = 1;
-        ms.height = 1;
-        if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n_set, b->graph[k], nullptr, 0, &ms);
         void *args[3] = {&b->dummy_map, &b->p0, &b->work};
         cudaKernelNodeParams kp;
         std::memset(&kp, 0, sizeof kp);
@@ -224,8 +216,8 @@ rs_status build_launch(rs_batch *b, cudaStream_t stream)
         kp.blockDim = dim3(fused::kThreads);
         kp.sharedMemBytes = unsigned(b->smem);
         kp.kernelParams = args;
-        cudaGraphNode_t deps[3] = {n_par, n_map, n_set};
-        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_ker, b->graph[k], deps, 3, &kp);
+        cudaGraphNode_t deps[2] = {n_par, n_map};
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n_ker, b->graph[k], deps, 2, &kp);
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
         if (e != cudaSuccess) return cuda_fail(e, "batch: building the launch graph");
     }
@@ -293,8 +285,7 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
         b->out_bytes += int64_t(p->gy.n_out) * p->gx.n_out * b->C * int64_t(dt_size(b->dtype));
     }
     b->use_tma = all_tma ? 1 : 0;
-    cudaError_t e = cudaMalloc(&b->dcounter.p, 16);
-    if (e == cudaSuccess) e = cudaMalloc(&b->derr.p, 16);
+    cudaError_t e = cudaMalloc(&b->derr.p, 16);
     if (e == cudaSuccess) e = cudaMemset(b->derr.p, 0, 16);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaHostAlloc(&b->host_stage[k], stage_bytes(n), cudaHostAllocDefault);

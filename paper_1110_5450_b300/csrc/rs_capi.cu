@@ -27,8 +27,6 @@ const Variant *variants_f16(int *n);
 const Variant *variants_bf16(int *n);
 } // namespace fused
 
-namespace {
-
 const fused::Variant *find_variant(int dtype, int C, int G)
 {
     int n = 0;
@@ -44,10 +42,6 @@ const fused::Variant *find_variant(int dtype, int C, int G)
         if (v[i].C == C && v[i].G == G) return &v[i];
     return nullptr;
 }
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn()
 {
@@ -79,7 +73,6 @@ int support_radius(int kernel, double param)
 
 
 
-} // namespace
 } // namespace rs
 
 using namespace rs;

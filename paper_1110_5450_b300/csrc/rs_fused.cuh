@@ -43,6 +43,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kErrBounds = 201;  // a band would read outside the staged tile
 constexpr int kErrTimeout = 202; // an mbarrier wait ran out
+constexpr int kOffCache = 2048;  // batch tile prefix sums kept in shared memory
 
 template <typename A, typename T> __device__ __forceinline__ A to_acc(T v);
 template <> __device__ __forceinline__ float to_acc<float, float>(float v) { return v; }
@@ -166,15 +167,15 @@ struct Params {
     int *err;
 };
 
-// Work of one launch: a single image (tiles in a static round-robin order),
-// or a batch of images whose tiles are handed out by an atomic counter.
+// Work of one launch: a single image, or a batch of images whose tiles are
+// concatenated image after image.  CTA b takes tiles b, b + grid, b + 2 grid,
+// ... of that list, so every image's tiles spread over all CTAs.
 struct Work {
     const Params *imgs;      // batch: device array of per-image parameters; nullptr: single image
     const CUtensorMap *maps; // batch: per-image tensor maps in global memory (64-byte aligned)
     const int32_t *tile_off; // batch: tiles of images [0, k) = tile_off[k], n_images + 1 entries
     int32_t n_images;
     int32_t total_tiles;
-    int32_t *counter;        // batch: work counter, zero at launch
     // shared-memory carving: byte sizes of the regions (maxima over the
     // images), and launch-wide choices
     int32_t tin_bytes, wy_bytes, wx_bytes, tt_bytes, rec2_bytes;
@@ -244,6 +245,12 @@ __host__ __device__ inline Layout layout_of(size_t tin, size_t wy, size_t wx, si
     L.total = 128 + size_t(nstage) * L.stage + 2 * L.tt + 2 * L.rec2 + align_up(2 * sizeof(TileInfo), 128) + 64 +
               1024;
     return L;
+}
+
+// Extra dynamic shared memory of a batch launch: its tile prefix sums.
+__host__ __device__ inline size_t batch_extra(int n_images)
+{
+    return n_images + 1 <= kOffCache ? align_up(size_t(n_images + 1) * 4, 128) : 0;
 }
 
 __host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int box_w, int ngy, int ngx, int js_y,
@@ -350,6 +357,8 @@ __global__ void __launch_bounds__(kThreads, 3)
                                                   align_up(2 * sizeof(TileInfo), 128));
     uint64_t *full = bars, *ttfull = bars + 2, *ttempty = bars + 4;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 6);
+    // batch tile prefix sums cached in shared memory (up to kOffCache entries)
+    int32_t *off_s = (batch && w.n_images + 1 <= kOffCache) ? reinterpret_cast<int32_t *>(bars + 8) : nullptr;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n1 = w.n1;        // staging + pass-1 warps
@@ -366,6 +375,8 @@ __global__ void __launch_bounds__(kThreads, 3)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (off_s)
+        for (int e = threadIdx.x; e <= w.n_images; e += kThreads) off_s[e] = __ldg(w.tile_off + e);
     __syncthreads();
 
     auto stage_tin = [&](int s) { return reinterpret_cast<T *>(smem + s * L.stage); };
@@ -381,22 +392,22 @@ __global__ void __launch_bounds__(kThreads, 3)
     auto take_tile = [&](int k, TileInfo *rec) -> bool {
         int item = -1, img = 0, t = 0;
         if (lane == 0) {
-            if (!batch) {
-                const int total = p0.tiles_y * p0.tiles_x;
-                const int it = int(blockIdx.x) + k * int(gridDim.x);
-                item = it < total ? it : -1;
-                t = item;
-            } else {
-                const int it = atomicAdd(w.counter, 1);
-                if (it < w.total_tiles) {
-                    item = it;
-                    int lo = 0, hi = w.n_images - 1; // last image with tile_off[img] <= it
+            const int total = batch ? w.total_tiles : p0.tiles_y * p0.tiles_x;
+            const int it = int(blockIdx.x) + k * int(gridDim.x);
+            if (it < total) {
+                item = it;
+                t = it;
+                if (batch) {
+                    // last image with tile_off[img] <= it (prefix sums in shared memory
+                    // when they fit, else in global memory)
+                    const int32_t *off = off_s ? off_s : w.tile_off;
+                    int lo = 0, hi = w.n_images - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
-                        if (__ldg(w.tile_off + mid) <= it) lo = mid; else hi = mid - 1;
+                        if (off[mid] <= it) lo = mid; else hi = mid - 1;
                     }
                     img = lo;
-                    t = it - __ldg(w.tile_off + lo);
+                    t = it - off[lo];
                 }
             }
         }

@@ -70,6 +70,15 @@ struct rs_plan {
 namespace rs {
 
 rs_status fail(rs_status s, const std::string &msg);
+// Instantiated fused kernel for (dtype, channels, group size), or nullptr.
+const fused::Variant *find_variant(int dtype, int C, int G);
+// Support radius of a kernel (0 for an invalid Lanczos parameter).
+int support_radius(int kernel, double param);
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (nullptr if unavailable).
+EncodeTiledFn encode_fn();
 rs_status cuda_fail(cudaError_t e, const char *what);
 // Every feasible fused configuration (needs the host start tables).
 std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout);
