@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the model-chosen kernel configuration")
     ap.add_argument("--batch-n", type=int, default=512, help="images in the batched section")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving trace")
+    ap.add_argument("--serve-plain-n", type=int, default=300, help="requests of the plain FP32 comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched section (profiling); prints its object")
@@ -301,6 +305,115 @@ def batched_section(args, dev, stream):
                        "tiles": info.total_tiles}}
 
 
+def serving_section(args, dev):
+    """Open-loop serving trace: Poisson arrivals at 2000 req/s, square BF16
+    images (side logU[32, 4096], 1 or 3 channels, scale logU[1/8, 8], kernel
+    U{Keys -1/2, Lanczos-3}, mirror), continuous batching under a 40 GB budget.
+    Inputs are crops of two resident 4096x4096 base images; outputs are
+    allocated by the server and released as soon as each request completes.
+    Latency = completion (host callback) - submission.  The plain FP32 path
+    (one plan + one resample per request, back to back) runs on a prefix of
+    the same trace for comparison."""
+    import numpy as np
+    import torch
+
+    import paper_1110_5450_b300 as rs
+    import synth
+
+    trace = synth.serving_trace(duration_s=args.serve_seconds)
+    bases, bases32 = {}, {}
+    for C in (1, 3):
+        img = synth.sinusoids(4096, 4096, C, seed=synth.SEED_C5 + C)
+        bases[C] = torch.from_numpy(img).to(torch.bfloat16).to(dev).reshape(4096, 4096 * C)
+        bases32[C] = torch.from_numpy(img).to(dev).reshape(4096, 4096 * C)
+    descs = []
+    for r in trace:
+        sp = r.spec
+        descs.append(rs.make_desc(sp.in_h, sp.in_w, sp.channels, scale_h=sp.scale, scale_w=sp.scale,
+                                  kernel=sp.kernel, param=sp.param, boundary="mirror", dtype=torch.bfloat16,
+                                  in_row_stride=4096 * sp.channels))
+    srv = rs.rs_server_create(40 << 30, max_inflight=4, max_batch=256)
+    torch.cuda.synchronize()
+    outstanding = {}
+    lat, out_px, batch_sizes = [], 0, []
+    t0 = time.perf_counter()
+    i = 0
+    n = len(trace)
+    lag = []
+    while i < n or outstanding:
+        now = time.perf_counter() - t0
+        # submit everything whose arrival time has come
+        first = i
+        while i < n and trace[i].arrival_s <= now:
+            i += 1
+        if i > first:
+            reqs = [rs.rs_request(descs[k], bases[trace[k].spec.channels].data_ptr(), None) for k in range(first, i)]
+            tk = rs.rs_batch_submit(srv, reqs)
+            for k in range(first, i):
+                outstanding[tk + (k - first)] = k
+                lag.append(now - trace[k].arrival_s)
+        # collect completions
+        done = []
+        for tk in list(outstanding.keys())[:512]:
+            st = rs.rs_batch_poll(srv, tk)
+            if st.status == rs.RS_ERR_BUSY:
+                continue
+            if st.status == rs.RS_OK:
+                lat.append((st.t_done_ns - st.t_submit_ns) / 1e6)
+                out_px += st.out_h * st.out_w
+                batch_sizes.append(st.batch_size)
+            rs.rs_server_release(srv, tk)
+            done.append(tk)
+        for tk in done:
+            del outstanding[tk]
+        if not done and i < n:
+            time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    stats = rs.rs_server_get_stats(srv)
+    rs.rs_server_drain(srv)
+    rs.rs_server_destroy(srv)
+    lat = np.array(lat)
+    # plain per-request FP32 path on a prefix of the trace (back to back)
+    m = min(len(trace), args.serve_plain_n)
+    t1 = time.perf_counter()
+    svc, px32 = [], 0
+    for r in trace[:m]:
+        sp = r.spec
+        ts = time.perf_counter()
+        pl = rs.Plan(sp.in_h, sp.in_w, sp.channels, scale=sp.scale, kernel=sp.kernel, param=sp.param,
+                     boundary="mirror", dtype=torch.float32)
+        y = torch.empty(pl.out_shape, dtype=torch.float32, device=dev)
+        d = pl.desc
+        h = pl.handle
+        # the crop of the resident FP32 base (row pitch 4096*C) through the C ABI
+        dd = rs.make_desc(sp.in_h, sp.in_w, sp.channels, pl.info.out_h, pl.info.out_w, kernel=sp.kernel,
+                          param=sp.param, boundary="mirror", dtype=torch.float32,
+                          in_row_stride=4096 * sp.channels)
+        pl.close()
+        hh = rs.rs_plan_create(dd, 0)
+        rs.rs_resample(hh, bases32[sp.channels].data_ptr(), y.data_ptr(), 0)
+        torch.cuda.synchronize()
+        rs.rs_destroy(hh)
+        svc.append((time.perf_counter() - ts) * 1e3)
+        px32 += y.shape[0] * y.shape[1]
+        del y, d, h
+    plain_wall = time.perf_counter() - t1
+    svc = np.array(svc)
+    return {"workload": "Poisson %d req/s for %.0f s, square BF16, side logU[32,4096], C in {1,3}, "
+                        "scale logU[1/8,8], kernel U{Keys -1/2, Lanczos-3}, mirror; 40 GB budget"
+                        % (2000, args.serve_seconds),
+            "requests": int(len(lat)), "rejected": int(stats.rejected), "launches": int(stats.launches),
+            "value": out_px / wall / 1e6, "unit": UNIT, "wall_s": wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+            "max_bytes_in_use": int(stats.max_bytes_in_use),
+            "submit_lag_p99_ms": float(np.percentile(lag, 99) * 1e3) if lag else 0.0,
+            "plain_fp32_per_request": {"requests": m, "value": px32 / plain_wall / 1e6, "unit": UNIT,
+                                       "p50_ms": float(np.percentile(svc, 50)),
+                                       "p99_ms": float(np.percentile(svc, 99)),
+                                       "how": "closed loop, one plan + resample + sync per request"}}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -352,6 +465,9 @@ def main():
     outs = out_sizes()
     if args.batch_only:
         print(json.dumps(batched_section(args, dev, stream)), flush=True)
+        return
+    if args.serve_only:
+        print(json.dumps(serving_section(args, dev)), flush=True)
         return
 
     img = synth.sinusoids(N_IN, N_IN, C, seed=synth.SEED_C2 + rank)
@@ -456,6 +572,9 @@ def main():
     batched = None
     if not args.no_batch:
         batched = batched_section(args, dev, stream)
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = serving_section(args, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -487,6 +606,7 @@ def main():
             "clocks": clocks,
             "cpu_baseline": cpu,
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     for p in plans:
