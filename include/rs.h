@@ -103,6 +103,13 @@ typedef enum {
 #define RS_NO_ANTIALIAS 0x01u /* do not widen the kernel when downscaling        */
 #define RS_FORCE_SIMT 0x02u   /* never pick the tensor-core (tcgen05) path        */
 #define RS_FORCE_TC 0x04u     /* pick the tcgen05 banded-GEMM path (F16/BF16)     */
+/* The tcgen05 path runs the vertical (first) pass of the fused kernel as a
+ * banded GEMM on the tensor cores.  It needs F16/BF16 storage, a row pitch of
+ * whole 16 bytes, in_w * channels a multiple of 8, and at rs_resample an input
+ * pointer aligned to 16 bytes (RS_ERR_INVALID_ARG otherwise).  Without a flag
+ * it is chosen for such plans when the vertical axis has 16 or more taps
+ * (wide antialiasing); with RS_FORCE_TC a plan that cannot take it fails with
+ * RS_ERR_UNSUPPORTED.  Batches and the server always run the SIMT kernel. */
 #define RS_TWO_PASS 0x08u     /* separate H-then-V kernels through an HBM buffer  */
 #define RS_CHECK 0x10u        /* device bounds checks that set an error word      */
 
@@ -317,6 +324,20 @@ RS_API rs_status rs_server_drain(rs_server *server, int64_t timeout_ms);
 RS_API rs_status rs_server_get_stats(rs_server *server, rs_server_stats *stats);
 /* Drains (up to 60 s), stops the scheduler and frees the server.  NULL is accepted. */
 RS_API rs_status rs_server_destroy(rs_server *server);
+
+/* Tensor-core self-test.  The paper has no counterpart: this checks the
+ * fifth-generation tensor-core building blocks the banded-GEMM passes use.
+ * One CTA computes D = A * B^T with tcgen05 MMAs (16-bit operands, FP32
+ * accumulators in tensor memory): A is m x k, B is n x k, both row-major
+ * 16-bit patterns on the host (bf16 != 0: BF16, else FP16), D is m x n
+ * floats on the host.  a_mn / b_mn store A / B MN-major in shared memory
+ * (else K-major); variant 0 encodes the core-matrix stride along K as the
+ * descriptor's leading offset and the stride along M (N) as its stride
+ * offset, variant 1 the other way round.  m = 128, n and k multiples of
+ * 16 up to 256 with n * k <= 49152.  Synchronous; allocates and frees its own
+ * device buffers. */
+RS_API rs_status rs_tc_selftest(int32_t m, int32_t n, int32_t k, int32_t a_mn, int32_t b_mn, int32_t variant,
+                                int32_t bf16, const uint16_t *h_a, const uint16_t *h_b, float *h_d);
 
 /* Synchronise the device and report any device-side error word the plan's
  * kernels set (RS_CHECK builds and bounded waits); clears the word. */

@@ -135,6 +135,8 @@ _lib.rs_batch_get_info.restype = ctypes.c_int
 _lib.rs_batch_get_info.argtypes = [_vp, ctypes.POINTER(rs_batch_info)]
 _lib.rs_batch_destroy.restype = ctypes.c_int
 _lib.rs_batch_destroy.argtypes = [_vp]
+_lib.rs_tc_selftest.restype = ctypes.c_int
+_lib.rs_tc_selftest.argtypes = [ctypes.c_int32] * 7 + [_vp, _vp, _vp]
 _lib.rs_server_create.restype = ctypes.c_int
 _lib.rs_server_create.argtypes = [ctypes.POINTER(rs_server_desc), ctypes.POINTER(_vp)]
 _lib.rs_batch_submit.restype = ctypes.c_int
@@ -156,7 +158,7 @@ EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "
            "rs_resample_noalloc", "rs_plan_autotune", "rs_batch_create", "rs_batch_run",
            "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
            "rs_batch_submit", "rs_batch_poll", "rs_server_release", "rs_server_drain", "rs_server_get_stats",
-           "rs_server_destroy"]
+           "rs_server_destroy", "rs_tc_selftest"]
 
 
 class RSError(RuntimeError):
@@ -273,6 +275,21 @@ def rs_batch_get_info(batch: int) -> rs_batch_info:
 
 def rs_batch_destroy(batch: int) -> None:
     _check(_lib.rs_batch_destroy(_vp(batch)), "rs_batch_destroy")
+
+
+def rs_tc_selftest(a16, b16, a_mn: int = 0, b_mn: int = 0, variant: int = 0, bf16: int = 1):
+    """D = A * B^T on the tensor cores; a16 (m x k) and b16 (n x k) are uint16
+    numpy arrays of 16-bit float patterns.  Returns D (m x n float32)."""
+    import numpy as np
+
+    a16 = np.ascontiguousarray(a16, dtype=np.uint16)
+    b16 = np.ascontiguousarray(b16, dtype=np.uint16)
+    m, k = a16.shape
+    n = b16.shape[0]
+    d = np.zeros((m, n), np.float32)
+    _check(_lib.rs_tc_selftest(m, n, k, a_mn, b_mn, variant, bf16, a16.ctypes.data, b16.ctypes.data,
+                               d.ctypes.data), "rs_tc_selftest")
+    return d
 
 
 def rs_server_create(budget_bytes: int, max_inflight: int = 4, max_batch: int = 256, warps_pass1: int = 0) -> int:

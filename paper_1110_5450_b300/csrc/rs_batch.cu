@@ -267,7 +267,9 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
     bool all_tma = true;
     for (int i = 0; i < n; ++i) {
         rs_plan_desc d = descs[i];
-        d.flags &= ~uint32_t(RS_TWO_PASS);
+        // one persistent launch runs every image on the SIMT kernel
+        d.flags &= ~uint32_t(RS_TWO_PASS | RS_FORCE_TC);
+        d.flags |= RS_FORCE_SIMT;
         rs_plan *p = nullptr;
         rs_status st = rs_plan_create(&d, stream, &p);
         if (st != RS_OK) {

@@ -247,8 +247,9 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     p->tmap_ptr = nullptr;
     p->G = c.G;
     p->J = c.J;
-    // the vertical band of the FP32 path stores every weight twice (packed pairs)
-    p->ty.dup = p->work_double ? 1 : 2;
+    // the vertical band of the FP32 SIMT path stores every weight twice (packed
+    // pairs); the tensor-core path reads it once per weight-matrix element
+    p->ty.dup = (p->work_double || c.tc) ? 1 : 2;
     p->tx.dup = 1;
     const int js_y = band_stride(c.G * p->ty.dup, c.J), js_x = band_stride(c.G, c.J);
     p->ty.G = p->tx.G = c.G;
@@ -302,43 +303,110 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     fp.js_x = js_x;
     fp.tile_h = c.tile_h;
     fp.tile_w = c.tile_w;
-    fp.n_sub = (rows + 255) / 256;
-    fp.sub_h = sub_height(rows, fp.n_sub);
-    fp.box_h = fp.n_sub * fp.sub_h;
-    fp.box_w = bw;
-    const int V = p->variant->V;
-    fp.w1 = (bw + 32 * V - 1) / (32 * V) * (32 * V);
-    fp.pitch_t = fp.w1 | 1;
+    if (c.tc) {
+        // whole 128-sample M blocks, K rows padded to the MMA's 16
+        const int kpad = (rows + 15) / 16 * 16;
+        const int nmb = (tile_extent(bx, ngx, c.J, C, 8) + 127) / 128;
+        int cols = 32;
+        while (cols < nmb * c.tile_h) cols <<= 1;
+        if (!tma_layout || kpad > 256 || nmb * 16 > 256 || cols > 512 || c.tile_h % 16 || c.tile_h > 256)
+            return RS_ERR_UNSUPPORTED;
+        fp.n_sub = 1;
+        fp.sub_h = kpad;
+        fp.box_h = kpad;
+        fp.box_w = nmb * 128;
+        fp.w1 = fp.box_w;
+        fp.pitch_t = fp.box_w + 1;
+        fp.tc_nmb = nmb;
+        fp.tc_kpad = kpad;
+    } else {
+        fp.n_sub = (rows + 255) / 256;
+        fp.sub_h = sub_height(rows, fp.n_sub);
+        fp.box_h = fp.n_sub * fp.sub_h;
+        fp.box_w = bw;
+        const int V = p->variant->V;
+        fp.w1 = (bw + 32 * V - 1) / (32 * V) * (32 * V);
+        fp.pitch_t = fp.w1 | 1;
+    }
     fp.groups_y = p->ty.groups;
     fp.groups_x = p->tx.groups;
     fp.tiles_y = int32_t((p->gy.n_out + c.tile_h - 1) / c.tile_h);
     fp.tiles_x = int32_t((p->gx.n_out + c.tile_w - 1) / c.tile_w);
     fp.stages = c.stages;
-    fp.n1 = c.n1;
+    fp.n1 = c.tc ? 4 : c.n1; // the tensor-memory epilogue needs four warps (128 lanes)
     fp.err = p->d_err;
-    p->tma_ok = (tma_layout && bw <= 256) ? 1 : 0;
+    p->tma_ok = (tma_layout && (c.tc || bw <= 256)) ? 1 : 0;
     p->smem = fused::layout(esz, asz, fp.box_h, fp.box_w, ngy, ngx, js_y, js_x, fp.tile_h, fp.pitch_t,
                             p->tma_ok ? fp.stages : 1)
-                  .total;
+                  .total +
+              (c.tc ? fused::align_up(size_t(4) * fp.tile_h * fp.tc_kpad, 128) : 0);
     if (p->smem > 227 * 1024) return RS_ERR_UNSUPPORTED;
+    p->kernel_fn = c.tc ? p->variant->fn_tc : p->variant->fn;
     // The limit is a property of the kernel function, shared by every plan that
     // uses this variant, so opt in to the whole per-block maximum once rather
     // than to this plan's size (occupancy follows the size passed at launch).
-    e = cudaFuncSetAttribute(p->variant->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    e = cudaFuncSetAttribute(p->kernel_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "setting shared memory size");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p->variant->fn, fused::kThreads, p->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p->kernel_fn, fused::kThreads, p->smem);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (c.tc) {
+        // Resident CTAs hold their tensor memory for the whole launch: pad the
+        // shared-memory request until they fit the SM's 512 columns together,
+        // so that no allocation has to wait for another CTA to finish.
+        int cols = 32;
+        while (cols < fp.tc_nmb * fp.tile_h) cols <<= 1;
+        const int max_ctas = 512 / cols;
+        while (occ > max_ctas && p->smem < 227 * 1024) {
+            p->smem = std::min<size_t>(227 * 1024, p->smem + 8 * 1024);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p->kernel_fn, fused::kThreads, p->smem);
+            if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        }
+        if (occ > max_ctas || occ < 1) return RS_ERR_UNSUPPORTED;
+    }
     if (occ < 1) return RS_ERR_UNSUPPORTED;
     const int64_t tiles = int64_t(fp.tiles_y) * fp.tiles_x;
     p->grid = int(std::min<int64_t>(tiles, int64_t(occ) * p->num_sms));
     p->ctas_per_sm = occ;
     p->chosen = c;
+    p->chosen.n1 = fp.n1;
     return RS_OK;
 }
 
-// Every feasible fused configuration of a plan (host start tables needed).
-std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout)
+// Cost of a tensor-core candidate in modelled SM cycles per output pixel.
+// Pass 1 (four warps): building the hi/lo weight matrices, the MMAs (two per
+// 128 x N x 16 step at ~8K FLOP per SM cycle) and the tensor-memory epilogue;
+// pass 2 as in the SIMT model on the other four warps; the tile fill at
+// ~64 B per cycle.
+double model_cost_tc(const Candidate &c, int C, int kpad, int nmb, size_t esz, size_t asz)
+{
+    const int ngx = c.tile_w / c.G;
+    const int N = c.tile_h;
+    const double build = double(N) * kpad * 12.0 / 128.0;
+    const double mma = 4.0 * 128.0 * N * kpad * nmb / 8192.0;
+    const double epi = double(nmb) * N * 2.0;
+    const double pass1 = build + mma + epi + 300.0;
+    const int rb = std::min(32, c.tile_h);
+    const int t2 = ((c.tile_h + rb - 1) / rb) * ((ngx + 32 / rb - 1) / (32 / rb));
+    const double task2 = c.J * (double(c.G * C) + 1.0 + C + 2.0) + 24.0 + C * c.G;
+    const double pass2 = std::ceil(double(t2) / (fused::kWarps - 4)) * task2;
+    const double fill = (double(kpad) * nmb * 128 * esz + double(c.tile_h / c.G + ngx) * band_stride(c.G, c.J) * asz) / 64.0;
+    return std::max(std::max(pass1, pass2), fill) / (double(c.tile_h) * c.tile_w);
+}
+
+// Whether a plan can run its vertical pass on the tensor cores: 16-bit
+// storage, TMA tile copies, and rows of whole 8-sample (16-byte) chunks so
+// that the 3-D tensor map never reads past a row.
+bool tc_eligible(const rs_plan *p, bool tma_layout)
+{
+    const rs_plan_desc &d = p->desc;
+    return tma_layout && (d.in_dtype == RS_F16 || d.in_dtype == RS_BF16) && (int64_t(d.in_w) * d.channels) % 8 == 0 &&
+           !(d.flags & RS_FORCE_SIMT);
+}
+
+// Every feasible fused configuration of a plan (host start tables needed):
+// SIMT configurations, or with tc the tensor-core ones.
+std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout, bool tc)
 {
     const rs_plan_desc &d = p->desc;
     const int C = d.channels;
@@ -349,6 +417,52 @@ std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout)
     const size_t smem_cap = 227 * 1024;
     const std::vector<int32_t> &sy = p->host_start_y, &sx = p->host_start_x;
     std::vector<Candidate> out;
+    if (tc) {
+        if (!tc_eligible(p, tma_layout)) return out;
+        for (int G : {4, 2, 1}) {
+            if (!find_variant(dt, C, G)) continue;
+            const int J = std::max(band_needed(sy, G, p->gy.t_eff), band_needed(sx, G, p->gx.t_eff));
+            if (J > 256) continue;
+            const std::vector<int32_t> by = group_bases(sy, G, J, p->gy.n_in, p->gy.t_eff);
+            const std::vector<int32_t> bx = group_bases(sx, G, J, p->gx.n_in, p->gx.t_eff);
+            for (int tile_h : {16, 32, 64, 128}) {
+                if (tile_h / G > 32) continue;
+                if (tile_h > 16 && tile_h / 2 >= p->gy.n_out) continue;
+                const int rows = tile_extent(by, tile_h / G, J, 1, 1);
+                const int kpad = (rows + 15) / 16 * 16;
+                if (kpad > 256) continue;
+                for (int ngx = 1; ngx <= 32; ++ngx) {
+                    const int tile_w = ngx * G;
+                    if (tile_w > ((p->gx.n_out + G - 1) / G) * G && ngx > 1) break;
+                    const int nmb = (tile_extent(bx, ngx, J, C, 8) + 127) / 128;
+                    if (nmb > 16 || nmb * tile_h > 512) break;
+                    const int box_w = nmb * 128;
+                    for (int stages : {2, 1}) {
+                        Candidate c;
+                        c.tc = 1;
+                        c.G = G;
+                        c.J = J;
+                        c.tile_h = tile_h;
+                        c.tile_w = tile_w;
+                        c.stages = stages;
+                        c.box_h = kpad;
+                        c.sub_h = kpad;
+                        c.n_sub = 1;
+                        c.box_w = box_w;
+                        c.n1 = 4;
+                        c.smem = fused::layout(esz, asz, kpad, box_w, tile_h / G, ngx, band_stride(G, J),
+                                               band_stride(G, J), tile_h, box_w + 1, stages)
+                                     .total +
+                                 fused::align_up(size_t(4) * tile_h * kpad, 128);
+                        if (c.smem > smem_cap) continue;
+                        c.cost = model_cost_tc(c, C, kpad, nmb, esz, asz);
+                        out.push_back(c);
+                    }
+                }
+            }
+        }
+        return out;
+    }
     for (int G : {4, 2, 1}) {
         const fused::Variant *var = find_variant(dt, C, G);
         if (!var) continue;
@@ -402,6 +516,14 @@ bool tma_layout_ok(const rs_plan *p)
     return ((p->desc.in_row_stride * int64_t(dt_size(p->desc.in_dtype))) % 16) == 0 && encode_fn() != nullptr;
 }
 
+// Tensor-core vertical pass for wide antialiasing (16 or more vertical taps)
+// on 16-bit storage, or whenever the plan asks for it.
+bool use_tc(const rs_plan *p, bool tma_layout)
+{
+    if (!tc_eligible(p, tma_layout)) return false;
+    return (p->desc.flags & RS_FORCE_TC) || p->gy.t_raw >= 16;
+}
+
 rs_status choose_fused(rs_plan *p, cudaStream_t stream)
 {
     // start tables back to the host (plan creation synchronises once)
@@ -415,12 +537,23 @@ rs_status choose_fused(rs_plan *p, cudaStream_t stream)
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "reading weight tables");
     const bool tma = tma_layout_ok(p);
-    const std::vector<Candidate> cands = enumerate_candidates(p, tma);
-    if (cands.empty()) return RS_ERR_UNSUPPORTED;
-    const Candidate *best = &cands[0];
-    for (const Candidate &c : cands)
-        if (c.cost < best->cost) best = &c;
-    return apply_fused(p, stream, *best, tma);
+    const bool tc = use_tc(p, tma);
+    if ((p->desc.flags & RS_FORCE_TC) && !tc)
+        return fail(RS_ERR_UNSUPPORTED, "tensor-core path needs F16/BF16 storage, a 16-byte row pitch and rows of "
+                                        "whole 8-sample chunks");
+    // cheapest modelled configuration first; a tensor-core plan with no
+    // feasible tile falls back to the SIMT kernel unless it was forced
+    for (int mode = tc ? 1 : 0; mode >= 0; --mode) {
+        std::vector<Candidate> cands = enumerate_candidates(p, tma, mode == 1);
+        std::stable_sort(cands.begin(), cands.end(),
+                         [](const Candidate &a, const Candidate &b) { return a.cost < b.cost; });
+        for (const Candidate &c : cands) {
+            const rs_status s = apply_fused(p, stream, c, tma);
+            if (s != RS_ERR_UNSUPPORTED) return s;
+        }
+        if (p->desc.flags & RS_FORCE_TC) return fail(RS_ERR_UNSUPPORTED, "no tensor-core tile fits this plan");
+    }
+    return RS_ERR_UNSUPPORTED;
 }
 
 rs_status encode_tensor_map(const rs_plan *p, const void *d_in, CUtensorMap *map)
@@ -434,13 +567,27 @@ rs_status encode_tensor_map(const rs_plan *p, const void *d_in, CUtensorMap *map
     case RS_BF16: t = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
     }
     const size_t esz = dt_size(d.in_dtype);
-    cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};
-    cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * int64_t(esz))};
-    cuuint32_t box[2] = {cuuint32_t(p->fp.box_w), cuuint32_t(p->fp.sub_h)};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode_fn()(map, t, 2, const_cast<void *>(d_in), dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r;
+    if (p->chosen.tc) {
+        // {8 samples, rows, 8-sample chunks}: the box lands in the tensor cores'
+        // canonical MN-major layout (rows 16 bytes apart, chunks rows*16 apart)
+        const int64_t row = p->gx.n_in * d.channels;
+        cuuint64_t dims[3] = {8, cuuint64_t(p->gy.n_in), cuuint64_t((row + 7) / 8)};
+        cuuint64_t strides[2] = {cuuint64_t(d.in_row_stride * int64_t(esz)), 16};
+        cuuint32_t box[3] = {8, cuuint32_t(p->fp.tc_kpad), cuuint32_t(p->fp.box_w / 8)};
+        cuuint32_t estr[3] = {1, 1, 1};
+        r = encode_fn()(map, t, 3, const_cast<void *>(d_in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};
+        cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * int64_t(esz))};
+        cuuint32_t box[2] = {cuuint32_t(p->fp.box_w), cuuint32_t(p->fp.sub_h)};
+        cuuint32_t estr[2] = {1, 1};
+        r = encode_fn()(map, t, 2, const_cast<void *>(d_in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS) {
         char buf[96];
         std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", int(r));
@@ -482,6 +629,12 @@ fused::Work single_work(const rs_plan *p, int use_tma)
     w.stages = use_tma ? fp.stages : 1;
     w.n1 = fp.n1;
     w.use_tma = use_tma;
+    if (p->chosen.tc) {
+        w.tc_b_bytes = int32_t(4 * fp.tile_h * fp.tc_kpad);
+        int cols = 32;
+        while (cols < fp.tc_nmb * fp.tile_h) cols <<= 1;
+        w.tc_cols = cols;
+    }
     return w;
 }
 
@@ -496,9 +649,9 @@ std::string tune_key(const rs_plan *p)
         if (ch == '"' || ch == '|') ch = '_';
     const rs_plan_desc &d = p->desc;
     char buf[320];
-    std::snprintf(buf, sizeof buf, "%s|v1|dt%d|c%d|k%d|p%.17g|b%d|f%u|%dx%d->%dx%d|is%lld", dev.c_str(), d.in_dtype,
-                  d.channels, d.kernel, d.param, d.boundary, d.flags & RS_NO_ANTIALIAS, d.in_h, d.in_w, d.out_h,
-                  d.out_w, (long long)d.in_row_stride);
+    std::snprintf(buf, sizeof buf, "%s|v1|dt%d|c%d|k%d|p%.17g|b%d|f%u|%dx%d->%dx%d|is%lld|tc%d", dev.c_str(),
+                  d.in_dtype, d.channels, d.kernel, d.param, d.boundary, d.flags & RS_NO_ANTIALIAS, d.in_h, d.in_w,
+                  d.out_h, d.out_w, (long long)d.in_row_stride, p->chosen.tc);
     return buf;
 }
 
@@ -589,8 +742,6 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     if (d.out_row_stride == 0) d.out_row_stride = int64_t(d.out_w) * d.channels;
     if (d.in_row_stride < int64_t(d.in_w) * d.channels || d.out_row_stride < int64_t(d.out_w) * d.channels)
         return fail(RS_ERR_INVALID_ARG, "row stride smaller than a row");
-    if (d.flags & RS_FORCE_TC)
-        return fail(RS_ERR_UNSUPPORTED, "tensor-core path not available for this plan");
 
     rs_plan *p = new (std::nothrow) rs_plan();
     if (!p) return fail(RS_ERR_OOM, "host allocation failed");
@@ -647,9 +798,13 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
 
     rs_status st = RS_ERR_UNSUPPORTED;
     const bool fusable = !(d.flags & RS_TWO_PASS) && (d.channels == 1 || d.channels == 3);
+    if ((d.flags & RS_FORCE_TC) && !fusable) {
+        delete p;
+        return fail(RS_ERR_UNSUPPORTED, "tensor-core path needs the fused kernel (1 or 3 channels, no RS_TWO_PASS)");
+    }
     if (fusable) {
         st = choose_fused(p, stream);
-        if (st != RS_OK && st != RS_ERR_UNSUPPORTED) {
+        if (st != RS_OK && (st != RS_ERR_UNSUPPORTED || (d.flags & RS_FORCE_TC))) {
             delete p;
             return st;
         }
@@ -696,6 +851,8 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
         fp.in = d_in;
         fp.out = d_out;
         fp.use_tma = (p->tma_ok && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1 : 0;
+        if (p->chosen.tc && !fp.use_tma)
+            return fail(RS_ERR_INVALID_ARG, "tensor-core plan: the input must be 16-byte aligned");
         size_t smem = p->smem;
         if (fp.use_tma) {
             rs_status s = encode_map(p, d_in);
@@ -705,7 +862,7 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
         }
         fused::Work w = single_work(p, fp.use_tma);
         void *args[3] = {&p->tmap, &fp, &w};
-        e = cudaLaunchKernel(p->variant->fn, dim3(p->grid), dim3(fused::kThreads), args, smem, stream);
+        e = cudaLaunchKernel(p->kernel_fn, dim3(p->grid), dim3(fused::kThreads), args, smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
         return RS_OK;
     }
@@ -738,7 +895,8 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     if (p->path != 0) return RS_OK; // only the fused path has choices to tune
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     const bool tma = tma_layout_ok(p);
-    std::vector<Candidate> cands = enumerate_candidates(p, tma);
+    const bool tc = p->chosen.tc != 0;
+    std::vector<Candidate> cands = enumerate_candidates(p, tma, tc);
     if (cands.empty()) return RS_OK;
     const std::string key = tune_key(p);
     int G, th, tw, st, n1;
@@ -781,7 +939,7 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     }
     // Stage 2: every warp split for the four fastest.
     std::sort(scored.begin(), scored.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
-    for (size_t r = 0; r < scored.size() && r < 4; ++r) {
+    for (size_t r = 0; r < scored.size() && r < 4 && !tc; ++r) {
         for (int k1 = 1; k1 < fused::kWarps; ++k1) {
             Candidate c = scored[r].second;
             if (c.n1 == k1) continue;
@@ -831,7 +989,7 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
     info->taps_w = p->gx.t_raw;
     info->table_h = p->gy.t_eff;
     info->table_w = p->gx.t_eff;
-    info->path = p->path;
+    info->path = (p->path == 0 && p->chosen.tc) ? 2 : p->path;
     if (p->path == 0) {
         info->tile_h = p->fp.tile_h;
         info->tile_w = p->fp.tile_w;

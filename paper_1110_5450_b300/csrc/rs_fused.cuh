@@ -33,8 +33,10 @@
 #include <cuda.h>
 
 #include <climits>
+#include <type_traits>
 
 #include "rs_internal.h"
+#include "rs_tc.cuh"
 
 namespace rs {
 namespace fused {
@@ -128,6 +130,18 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// 3-D tile copy; used with the box {8 samples, rows, sample chunks}, which
+// lands an input tile in the canonical MN-major operand layout of the tensor
+// cores (8 x 8 core matrices, rows 16 bytes apart, chunks rows*16 bytes apart).
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // 1-D bulk copy global -> shared (16-byte aligned addresses, size multiple of 16).
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
@@ -165,7 +179,11 @@ struct Params {
     int stages;                  // staged buffers (2 = prefetch the next tile; TMA only)
     int n1;                      // warps running staging + pass 1 (the rest run pass 2)
     int *err;
+    // tensor-core vertical pass: M blocks of 128 staged samples, staged rows
+    // (= box_h, the GEMM's K, a multiple of 16); zero on the SIMT path
+    int32_t tc_nmb, tc_kpad, tc_pad0, tc_pad1;
 };
+static_assert(sizeof(Params) % 16 == 0, "Params must keep 16-byte multiples (records copy it word by word)");
 
 // Work of one launch: a single image, or a batch of images whose tiles are
 // concatenated image after image.  CTA b takes tiles b, b + grid, b + 2 grid,
@@ -180,6 +198,8 @@ struct Work {
     // images), and launch-wide choices
     int32_t tin_bytes, wy_bytes, wx_bytes, tt_bytes, rec2_bytes;
     int32_t stages, n1, use_tma;
+    int32_t tc_b_bytes; // tensor-core path: weight matrices (hi + lo) region
+    int32_t tc_cols;    // tensor-core path: tensor-memory columns to allocate
 };
 
 struct TileInfo {
@@ -228,12 +248,14 @@ __host__ __device__ inline size_t rec2_bytes(int ngx, int js, size_t acc)
 }
 
 // Shared-memory layout: stages x (tin, wy, wx) | 2 x tt | 2 x (Rec2 + wx copy)
-// | 2 x TileInfo | 6 mbarriers | abort flag | read slack.
+// | tensor-core weight matrices (TC path) | 2 x TileInfo | 7 mbarriers, abort
+// flag, tensor-memory address | batch tile prefix sums | read slack.
 struct Layout {
-    size_t tin, wy, wx, stage, tt, rec2, total;
+    size_t tin, wy, wx, stage, tt, rec2, bmat, total;
 };
 
-__host__ __device__ inline Layout layout_of(size_t tin, size_t wy, size_t wx, size_t tt, size_t rec2, int nstage)
+__host__ __device__ inline Layout layout_of(size_t tin, size_t wy, size_t wx, size_t tt, size_t rec2, int nstage,
+                                            size_t bmat = 0)
 {
     Layout L;
     L.tin = tin;
@@ -242,8 +264,9 @@ __host__ __device__ inline Layout layout_of(size_t tin, size_t wy, size_t wx, si
     L.stage = L.tin + L.wy + L.wx;
     L.tt = tt;
     L.rec2 = rec2;
-    L.total = 128 + size_t(nstage) * L.stage + 2 * L.tt + 2 * L.rec2 + align_up(2 * sizeof(TileInfo), 128) + 64 +
-              1024;
+    L.bmat = align_up(bmat, 128);
+    L.total = 128 + size_t(nstage) * L.stage + 2 * L.tt + 2 * L.rec2 + L.bmat + align_up(2 * sizeof(TileInfo), 128) +
+              64 + 1024;
     return L;
 }
 
@@ -263,6 +286,7 @@ __host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int
     L.stage = L.tin + L.wy + L.wx;
     L.tt = align_up(size_t(tile_h) * pitch_t * acc, 128);
     L.rec2 = rec2_bytes(ngx, js_x, acc);
+    L.bmat = 0;
     // + slack because the vertical pass reads whole 32*V-column chunks past
     // the last staged row
     L.total = 128 + size_t(nstage) * L.stage + 2 * L.tt + 2 * L.rec2 + align_up(2 * sizeof(TileInfo), 128) + 64 +
@@ -335,11 +359,12 @@ template <int N> __device__ __forceinline__ void load_pairs(uint64_t (&w)[N], co
     }
 }
 
-template <typename T, int C, int G, int V>
+template <typename T, int C, int G, int V, bool TC = false>
 __global__ void __launch_bounds__(kThreads, 3)
     fused_kernel(const __grid_constant__ CUtensorMap tmap, const Params p0, const Work w)
 {
     using A = typename AccOf<T>::type;
+    static_assert(!TC || sizeof(T) == 2, "the tensor-core path takes 16-bit storage");
     // FP32 accumulation uses packed-pair FMAs (the FP64 path stays scalar)
     constexpr bool kPacked = sizeof(A) == 4 && V % 2 == 0;
     constexpr int kVec = 16 / int(sizeof(T)); // elements per 16 bytes
@@ -348,15 +373,18 @@ __global__ void __launch_bounds__(kThreads, 3)
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const bool batch = w.imgs != nullptr;
     const int nstage = (w.use_tma && w.stages == 2) ? 2 : 1;
-    const Layout L = layout_of(w.tin_bytes, w.wy_bytes, w.wx_bytes, w.tt_bytes, w.rec2_bytes, nstage);
+    const Layout L =
+        layout_of(w.tin_bytes, w.wy_bytes, w.wx_bytes, w.tt_bytes, w.rec2_bytes, nstage, TC ? w.tc_b_bytes : 0);
     unsigned char *after_stages = smem + nstage * L.stage;
     A *tt0 = reinterpret_cast<A *>(after_stages);
     unsigned char *rec_base = after_stages + 2 * L.tt;
-    TileInfo *info = reinterpret_cast<TileInfo *>(rec_base + 2 * L.rec2);
+    unsigned char *bmat = rec_base + 2 * L.rec2; // TC: weight matrices, hi then lo
+    TileInfo *info = reinterpret_cast<TileInfo *>(bmat + L.bmat);
     uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(info) +
                                                   align_up(2 * sizeof(TileInfo), 128));
-    uint64_t *full = bars, *ttfull = bars + 2, *ttempty = bars + 4;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 6);
+    uint64_t *full = bars, *ttfull = bars + 2, *ttempty = bars + 4, *mma_bar = bars + 6;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 7);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 7) + 1;
     // batch tile prefix sums cached in shared memory (up to kOffCache entries)
     int32_t *off_s = (batch && w.n_images + 1 <= kOffCache) ? reinterpret_cast<int32_t *>(bars + 8) : nullptr;
 
@@ -372,12 +400,18 @@ __global__ void __launch_bounds__(kThreads, 3)
         mbar_init(&ttfull[1], 32 * n1);
         mbar_init(&ttempty[0], 32 * n2);
         mbar_init(&ttempty[1], 32 * n2);
+        mbar_init(mma_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (off_s)
         for (int e = threadIdx.x; e <= w.n_images; e += kThreads) off_s[e] = __ldg(w.tile_off + e);
+    if constexpr (TC) {
+        if (warp == 0) tc::tmem_alloc(tmem_slot, uint32_t(w.tc_cols));
+        tc::fence_before_sync();
+    }
     __syncthreads();
+    if constexpr (TC) tc::fence_after_sync();
 
     auto stage_tin = [&](int s) { return reinterpret_cast<T *>(smem + s * L.stage); };
     auto stage_wy = [&](int s) { return reinterpret_cast<A *>(smem + s * L.stage + L.tin); };
@@ -474,8 +508,12 @@ __global__ void __launch_bounds__(kThreads, 3)
             mbar_arrive_expect_tx(&full[s], bt + by + bx);
             const CUtensorMap *map = batch ? w.maps + ti.img : &tmap;
             T *dst = stage_tin(s);
-            for (int q = 0; q < P.n_sub; ++q)
-                tma_load_2d(dst + size_t(q) * P.sub_h * P.box_w, map, &full[s], ti.xs, ti.ry0 + q * P.sub_h);
+            if constexpr (TC) {
+                tma_load_3d(dst, map, &full[s], 0, ti.ry0, ti.xs / 8);
+            } else {
+                for (int q = 0; q < P.n_sub; ++q)
+                    tma_load_2d(dst + size_t(q) * P.sub_h * P.box_w, map, &full[s], ti.xs, ti.ry0 + q * P.sub_h);
+            }
             bulk_load(stage_wy(s), static_cast<const A *>(P.band_y) + size_t(ty) * ngy * P.js_y, by, &full[s]);
             bulk_load(stage_wx(s), static_cast<const A *>(P.band_x) + size_t(tx) * ngx * P.js_x, bx, &full[s]);
         }
@@ -539,81 +577,143 @@ __global__ void __launch_bounds__(kThreads, 3)
             const A *wys = stage_wy(s);
             A *tt = tt_buf(b);
 
-            // pass 1: lanes along samples; V columns 32 apart per lane.  Chunks
-            // past box_w read harmless staged data and land in the padding of
-            // the intermediate (pitch_t >= w1): no predicate in the inner loop.
-            const int nchunk = P.w1 / (32 * V);
-            const int ntask = ti.nvy * nchunk;
-            const int per = (ntask + n1 - 1) / n1;
-            const int k0 = warp * per, k1 = min(ntask, k0 + per);
-            for (int task = k0; task < k1; ++task) {
-                const int q = task / nchunk, k = task - q * nchunk;
-                const int rb = ti.rb[q];
-                if (rb < 0 || rb + J > P.box_h) {
-                    if (lane == 0) flag(err, kErrBounds);
-                    continue;
+            if constexpr (TC) {
+                // pass 1 on the tensor cores: D[sample][row] = sum_j In[j][sample] W[row][j]
+                // A = staged input (MN-major canonical layout from the 3-D TMA box),
+                // B = the tile's weight matrix (K-major), split into hi + lo 16-bit
+                // parts so that weight rounding costs no accuracy; FP32 in tensor memory.
+                const int N = P.tile_h, K = P.tc_kpad, nmb = P.tc_nmb;
+                const uint32_t sbo = uint32_t(K) * 16u; // 8-sample (A) or 8-row (B) group stride
+                const size_t bbytes = size_t(N) * K * 2;
+                unsigned char *bhi = bmat, *blo = bmat + bbytes;
+                if (threadIdx.x < ti.nvy && (ti.rb[threadIdx.x] < 0 || ti.rb[threadIdx.x] + J > K))
+                    flag(err, kErrBounds); // a band past the staged rows would lose weights
+                for (int e = threadIdx.x; e < N * K; e += t1n) {
+                    const int y = e / K, j = e - y * K;
+                    const int q = y / G, r = y - q * G;
+                    float wv = 0.f;
+                    if (q < ti.nvy) {
+                        const int jj = j - ti.rb[q];
+                        if (jj >= 0 && jj < J) wv = float(wys[q * P.js_y + jj * G + r]);
+                    }
+                    const T hi = from_acc<T, A>(wv);
+                    const T lo = from_acc<T, A>(wv - to_acc<A, T>(hi));
+                    const uint32_t off = uint32_t(y / 8) * sbo + uint32_t(j / 8) * 128u + uint32_t(y % 8) * 16u +
+                                         uint32_t(j % 8) * 2u;
+                    *reinterpret_cast<T *>(bhi + off) = hi;
+                    *reinterpret_cast<T *>(blo + off) = lo;
                 }
-                const int c0 = k * 32 * V + lane;
-                const T *col = tin + rb * box_w + c0;
-                A *dst = tt + q * G * pitch_t + c0;
-                if constexpr (kPacked) {
-                    // column pairs (v, v+1) share one packed FMA; the vertical
-                    // band holds every weight twice, so pairs load as they are
-                    uint64_t acc2[G][V / 2];
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-#pragma unroll
-                        for (int u = 0; u < V / 2; ++u) acc2[g][u] = 0ull;
-                    const uint64_t *wq = reinterpret_cast<const uint64_t *>(wys + q * P.js_y);
-#pragma unroll 4
-                    for (int j = 0; j < J; ++j) {
-                        uint64_t w2[G];
-                        load_pairs<G>(w2, wq);
-                        wq += G;
-                        float d[V];
-#pragma unroll
-                        for (int v = 0; v < V; ++v) d[v] = to_acc<A, T>(col[32 * v]);
-#pragma unroll
-                        for (int u = 0; u < V / 2; ++u) {
-                            const uint64_t dd = pack2(d[2 * u], d[2 * u + 1]);
-#pragma unroll
-                            for (int g = 0; g < G; ++g) acc2[g][u] = fma2(w2[g], dd, acc2[g][u]);
+                tc::fence_proxy_async();
+                named_sync(1, t1n);
+                const uint32_t tmem = *tmem_slot;
+                if (threadIdx.x == 0) {
+                    tc::fence_after_sync();
+                    const uint32_t idesc = tc::idesc_f16(sizeof(T) == 2 && !std::is_same<T, __half>::value,
+                                                         true, false, 128, N);
+                    const uint32_t abase = smem_addr(tin), bh = smem_addr(bhi), bl = smem_addr(blo);
+                    for (int mb = 0; mb < nmb; ++mb) {
+                        for (int kb = 0; kb < K / 16; ++kb) {
+                            const uint64_t ad =
+                                tc::smem_desc(abase + uint32_t(mb) * 16u * sbo + uint32_t(kb) * 256u, 128u, sbo);
+                            const uint32_t d = tmem + uint32_t(mb * N);
+                            tc::mma_f16(d, ad, tc::smem_desc(bh + uint32_t(kb) * 256u, 128u, sbo), idesc,
+                                        kb > 0 ? 1u : 0u);
+                            tc::mma_f16(d, ad, tc::smem_desc(bl + uint32_t(kb) * 256u, 128u, sbo), idesc, 1u);
                         }
-                        col += box_w;
                     }
+                    tc::mma_commit(mma_bar);
+                }
+                if (!wait_or_abort(mma_bar, uint32_t(i & 1), abort_flag, err)) break;
+                tc::fence_after_sync();
+                // accumulators -> intermediate rows: warp wq reads lanes 32 wq .. 32 wq + 31
+                for (int mb = 0; mb < nmb; ++mb) {
+                    for (int c0 = 0; c0 < N; c0 += 16) {
+                        uint32_t r16[16];
+                        tc::tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(mb * N + c0), r16);
+                        tc::tmem_ld_wait();
+                        A *dst = tt + mb * 128 + warp * 32 + lane;
 #pragma unroll
-                    for (int g = 0; g < G; ++g)
-#pragma unroll
-                        for (int u = 0; u < V / 2; ++u) {
-                            float lo, hi;
-                            unpack2(acc2[g][u], lo, hi);
-                            dst[g * pitch_t + 32 * (2 * u)] = lo;
-                            dst[g * pitch_t + 32 * (2 * u + 1)] = hi;
-                        }
-                } else {
-                    A acc[G][V];
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-#pragma unroll
-                        for (int v = 0; v < V; ++v) acc[g][v] = A(0);
-                    const A *wq = wys + q * P.js_y;
-#pragma unroll 4
-                    for (int j = 0; j < J; ++j) {
-                        A wv[G];
-                        load_w<A, G>(wv, wq);
-                        wq += G;
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            const A dv = to_acc<A, T>(col[32 * v]);
-#pragma unroll
-                            for (int g = 0; g < G; ++g) acc[g][v] = fma(wv[g], dv, acc[g][v]);
-                        }
-                        col += box_w;
+                        for (int k = 0; k < 16; ++k) dst[(c0 + k) * pitch_t] = A(__uint_as_float(r16[k]));
                     }
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-#pragma unroll
-                        for (int v = 0; v < V; ++v) dst[g * pitch_t + 32 * v] = acc[g][v];
+                }
+                tc::fence_before_sync();
+            } else {
+            // pass 1: lanes along samples; V columns 32 apart per lane.  Chunks
+                // past box_w read harmless staged data and land in the padding of
+                // the intermediate (pitch_t >= w1): no predicate in the inner loop.
+                const int nchunk = P.w1 / (32 * V);
+                const int ntask = ti.nvy * nchunk;
+                const int per = (ntask + n1 - 1) / n1;
+                const int k0 = warp * per, k1 = min(ntask, k0 + per);
+                for (int task = k0; task < k1; ++task) {
+                    const int q = task / nchunk, k = task - q * nchunk;
+                    const int rb = ti.rb[q];
+                    if (rb < 0 || rb + J > P.box_h) {
+                        if (lane == 0) flag(err, kErrBounds);
+                        continue;
+                    }
+                    const int c0 = k * 32 * V + lane;
+                    const T *col = tin + rb * box_w + c0;
+                    A *dst = tt + q * G * pitch_t + c0;
+                    if constexpr (kPacked) {
+                        // column pairs (v, v+1) share one packed FMA; the vertical
+                        // band holds every weight twice, so pairs load as they are
+                        uint64_t acc2[G][V / 2];
+    #pragma unroll
+                        for (int g = 0; g < G; ++g)
+    #pragma unroll
+                            for (int u = 0; u < V / 2; ++u) acc2[g][u] = 0ull;
+                        const uint64_t *wq = reinterpret_cast<const uint64_t *>(wys + q * P.js_y);
+    #pragma unroll 4
+                        for (int j = 0; j < J; ++j) {
+                            uint64_t w2[G];
+                            load_pairs<G>(w2, wq);
+                            wq += G;
+                            float d[V];
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) d[v] = to_acc<A, T>(col[32 * v]);
+    #pragma unroll
+                            for (int u = 0; u < V / 2; ++u) {
+                                const uint64_t dd = pack2(d[2 * u], d[2 * u + 1]);
+    #pragma unroll
+                                for (int g = 0; g < G; ++g) acc2[g][u] = fma2(w2[g], dd, acc2[g][u]);
+                            }
+                            col += box_w;
+                        }
+    #pragma unroll
+                        for (int g = 0; g < G; ++g)
+    #pragma unroll
+                            for (int u = 0; u < V / 2; ++u) {
+                                float lo, hi;
+                                unpack2(acc2[g][u], lo, hi);
+                                dst[g * pitch_t + 32 * (2 * u)] = lo;
+                                dst[g * pitch_t + 32 * (2 * u + 1)] = hi;
+                            }
+                    } else {
+                        A acc[G][V];
+    #pragma unroll
+                        for (int g = 0; g < G; ++g)
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) acc[g][v] = A(0);
+                        const A *wq = wys + q * P.js_y;
+    #pragma unroll 4
+                        for (int j = 0; j < J; ++j) {
+                            A wv[G];
+                            load_w<A, G>(wv, wq);
+                            wq += G;
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                const A dv = to_acc<A, T>(col[32 * v]);
+    #pragma unroll
+                                for (int g = 0; g < G; ++g) acc[g][v] = fma(wv[g], dv, acc[g][v]);
+                            }
+                            col += box_w;
+                        }
+    #pragma unroll
+                        for (int g = 0; g < G; ++g)
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) dst[g * pitch_t + 32 * v] = acc[g][v];
+                    }
                 }
             }
             // hand the pass-2 record (parameters, offsets and x weights) over with buffer b
@@ -640,6 +740,15 @@ __global__ void __launch_bounds__(kThreads, 3)
             // every pass-1 warp is done with stage s before it is refilled
             named_sync(1, t1n);
             if (w.use_tma && warp == 0) produce(i + nstage, s);
+        }
+        if constexpr (TC) {
+            // every pass-1 warp is done with the tensor memory before it is freed
+            tc::fence_before_sync();
+            named_sync(1, t1n);
+            if (warp == 0) {
+                tc::fence_after_sync();
+                tc::tmem_dealloc(*tmem_slot, uint32_t(w.tc_cols));
+            }
         }
     } else {
         // =========================== pass 2 ============================
@@ -763,14 +872,20 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
 }
 
-// One instantiated kernel variant.
+// One instantiated kernel variant: the SIMT kernel and, for 16-bit storage,
+// the kernel whose vertical pass runs on the tensor cores (else the SIMT one again).
 struct Variant {
     int dtype, C, G, V;
     const void *fn;
+    const void *fn_tc;
 };
 
 #define RS_FUSED_VARIANT(T, DT, C, G, V) \
-    { DT, C, G, V, reinterpret_cast<const void *>(&fused_kernel<T, C, G, V>) }
+    { DT, C, G, V, reinterpret_cast<const void *>(&fused_kernel<T, C, G, V>), \
+      reinterpret_cast<const void *>(&fused_kernel<T, C, G, V, false>) }
+#define RS_FUSED_VARIANT_TC(T, DT, C, G, V) \
+    { DT, C, G, V, reinterpret_cast<const void *>(&fused_kernel<T, C, G, V>), \
+      reinterpret_cast<const void *>(&fused_kernel<T, C, G, V, true>) }
 
 } // namespace fused
 } // namespace rs

@@ -8,12 +8,12 @@ namespace rs {
 namespace fused {
 
 static const Variant kVariants[] = {
-    RS_FUSED_VARIANT(__half, RS_F16, 1, 4, 4),
-    RS_FUSED_VARIANT(__half, RS_F16, 1, 2, 4),
-    RS_FUSED_VARIANT(__half, RS_F16, 1, 1, 4),
-    RS_FUSED_VARIANT(__half, RS_F16, 3, 4, 4),
-    RS_FUSED_VARIANT(__half, RS_F16, 3, 2, 4),
-    RS_FUSED_VARIANT(__half, RS_F16, 3, 1, 4),
+    RS_FUSED_VARIANT_TC(__half, RS_F16, 1, 4, 4),
+    RS_FUSED_VARIANT_TC(__half, RS_F16, 1, 2, 4),
+    RS_FUSED_VARIANT_TC(__half, RS_F16, 1, 1, 4),
+    RS_FUSED_VARIANT_TC(__half, RS_F16, 3, 4, 4),
+    RS_FUSED_VARIANT_TC(__half, RS_F16, 3, 2, 4),
+    RS_FUSED_VARIANT_TC(__half, RS_F16, 3, 1, 4),
 };
 
 const Variant *variants_f16(int *n)

@@ -15,6 +15,7 @@ namespace rs {
 // One fused-kernel configuration of a plan.
 struct Candidate {
     int G = 0, J = 0, tile_h = 0, tile_w = 0, stages = 1, box_h = 0, box_w = 0, n_sub = 1, sub_h = 0, n1 = 4;
+    int tc = 0; // 1: vertical pass on the tensor cores
     size_t smem = 0;
     double cost = 0.0; // modelled SM cycles per output pixel
 };
@@ -55,6 +56,7 @@ struct rs_plan {
     // fused path
     rs::fused::Params fp{};
     const rs::fused::Variant *variant = nullptr;
+    const void *kernel_fn = nullptr; // the variant's SIMT or tensor-core kernel
     int G = 0, J = 0;
     size_t smem = 0;
     int grid = 0;
@@ -80,8 +82,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // cuTensorMapEncodeTiled through the runtime's driver entry point (nullptr if unavailable).
 EncodeTiledFn encode_fn();
 rs_status cuda_fail(cudaError_t e, const char *what);
-// Every feasible fused configuration (needs the host start tables).
-std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout);
+// Every feasible fused configuration (needs the host start tables); with tc
+// the tensor-core configurations instead of the SIMT ones.
+std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout, bool tc = false);
 // Builds the band tables of a configuration and the kernel parameters.
 rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool tma_layout);
 // Whether the plan's row pitch allows TMA tile copies.
