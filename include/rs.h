@@ -112,6 +112,16 @@ typedef enum {
  * RS_ERR_UNSUPPORTED.  Batches and the server always run the SIMT kernel. */
 #define RS_TWO_PASS 0x08u     /* separate H-then-V kernels through an HBM buffer  */
 #define RS_CHECK 0x10u        /* device bounds checks that set an error word      */
+#define RS_NO_STREAM 0x20u    /* never pick the row-streaming kernel              */
+#define RS_FORCE_STREAM 0x40u /* pick the row-streaming kernel (FP32, 1 or 3 channels,
+                                 horizontal band <= 16 taps); RS_ERR_UNSUPPORTED where
+                                 it cannot apply                                  */
+/* The row-streaming kernel runs the horizontal pass first on staged input rows
+ * and the vertical pass on a ring of filtered rows, with deep TMA prefetch and
+ * coalesced output rows.  It is chosen for FP32 plans of 1 or 3 channels whose
+ * horizontal band (groups of 4 outputs) needs at most 16 input pixels, with a
+ * 16-byte row pitch; an input pointer that is not 16-byte aligned at
+ * rs_resample falls back to the tile kernel of the same plan. */
 
 /* Plan descriptor.  Sizes are in samples/elements, not bytes. */
 typedef struct {
@@ -169,7 +179,8 @@ typedef struct {
     int32_t out_h, out_w;     /* derived output size                              */
     int32_t taps_h, taps_w;   /* raw taps per output (max over outputs), per axis */
     int32_t table_h, table_w; /* stored (boundary-folded) taps per output         */
-    int32_t path;             /* 0 = fused SIMT, 1 = two-pass SIMT, 2 = tcgen05    */
+    int32_t path;             /* 0 = fused tiles (SIMT), 1 = two-pass SIMT, 2 = fused
+                                 tiles with the tcgen05 vertical pass, 3 = row-streaming */
     int32_t tile_h, tile_w;   /* output tile of the chosen pass kernel            */
     int32_t group_h, group_w; /* outputs per thread group along each axis         */
     int32_t span_h, span_w;   /* band width (inputs per group)                    */

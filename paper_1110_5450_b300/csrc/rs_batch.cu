@@ -77,7 +77,7 @@ size_t combined_smem(const std::vector<Candidate> &pick, const std::vector<rs_pl
         const int V = plans[i]->work_double ? 2 : 4;
         const int w1 = (c.box_w + 32 * V - 1) / (32 * V) * (32 * V);
         const fused::Layout L = fused::layout(esz, asz, c.box_h, c.box_w, c.tile_h / c.G, c.tile_w / c.G,
-                                              band_stride(c.G * dup, c.J), band_stride(c.G, c.J), c.tile_h,
+                                              band_stride(c.G * dup, c.J), band_stride(2 * c.G, c.J), c.tile_h,
                                               w1 | 1, 1);
         tin = std::max(tin, L.tin);
         wy = std::max(wy, L.wy);
@@ -268,8 +268,8 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
     for (int i = 0; i < n; ++i) {
         rs_plan_desc d = descs[i];
         // one persistent launch runs every image on the SIMT kernel
-        d.flags &= ~uint32_t(RS_TWO_PASS | RS_FORCE_TC);
-        d.flags |= RS_FORCE_SIMT;
+        d.flags &= ~uint32_t(RS_TWO_PASS | RS_FORCE_TC | RS_FORCE_STREAM);
+        d.flags |= RS_FORCE_SIMT | RS_NO_STREAM;
         rs_plan *p = nullptr;
         rs_status st = rs_plan_create(&d, stream, &p);
         if (st != RS_OK) {

@@ -212,10 +212,12 @@ double model_cost(Candidate &c, int C, size_t esz, size_t asz, int V)
     const int nchunk = w1 / (32 * V);
     const int rb = std::min(32, c.tile_h);
     const int t1 = ngy * nchunk;
-    const int t2 = ((c.tile_h + rb - 1) / rb) * ((ngx + 32 / rb - 1) / (32 / rb));
+    const int npairs = fused::pair_slots(ngx);
+    const int t2 = ((c.tile_h + rb - 1) / rb) * ((npairs + 32 / rb - 1) / (32 / rb));
     const int W = fused::kWarps;
-    const double task1 = c.J * (double(c.G * V) + 1.0 + V + 2.0) + 24.0 + c.G * V;
-    const double task2 = c.J * (double(c.G * C) + 1.0 + C + 2.0) + 24.0 + C * c.G;
+    // per tap: packed FMAs + sample loads + weight loads, plus a fixed tail
+    const double task1 = c.J * (double(c.G * V) / 2.0 + V / 2.0 + c.G / 2.0 + 1.0) + 24.0 + c.G * V;
+    const double task2 = c.J * (double(c.G * C) + 2.0 * C + c.G / 2.0 + 1.0) + 30.0 + 2.0 * C * c.G;
     const double issue = (t1 * task1 + t2 * task2 + 200.0) / 4.0 * 1.25;
     const double fill = (double(c.box_h) * c.box_w * esz + double(ngy + ngx) * band_stride(c.G, c.J) * asz) / 64.0;
     const int ctas = int(std::min<size_t>(8, (227 * 1024) / std::max<size_t>(c.smem, 1)));
@@ -251,16 +253,17 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     // pairs); the tensor-core path reads it once per weight-matrix element
     p->ty.dup = (p->work_double || c.tc) ? 1 : 2;
     p->tx.dup = 1;
-    const int js_y = band_stride(c.G * p->ty.dup, c.J), js_x = band_stride(c.G, c.J);
+    p->tx.pair_ngx = c.tile_w / c.G; // the horizontal band interleaves group pairs
     p->ty.G = p->tx.G = c.G;
     p->ty.J = p->tx.J = c.J;
+    const int js_y = band_stride(c.G * p->ty.dup, c.J), js_x = band_slot_stride(p->tx);
     p->ty.groups = int32_t((p->gy.n_out + c.G - 1) / c.G);
     p->tx.groups = int32_t((p->gx.n_out + c.G - 1) / c.G);
     Carver cv;
     const size_t o_by = cv.take(size_t(p->ty.groups) * 4);
     const size_t o_bx = cv.take(size_t(p->tx.groups) * 4);
     const size_t o_wy = cv.take(size_t(p->ty.groups) * js_y * asz);
-    const size_t o_wx = cv.take(size_t(p->tx.groups) * js_x * asz);
+    const size_t o_wx = cv.take(size_t(band_slots(p->tx)) * js_x * asz);
     if (p->bands.p) {
         cudaFree(p->bands.p);
         p->bands.p = nullptr;
@@ -387,8 +390,9 @@ double model_cost_tc(const Candidate &c, int C, int kpad, int nmb, size_t esz, s
     const double epi = double(nmb) * N * 2.0;
     const double pass1 = build + mma + epi + 300.0;
     const int rb = std::min(32, c.tile_h);
-    const int t2 = ((c.tile_h + rb - 1) / rb) * ((ngx + 32 / rb - 1) / (32 / rb));
-    const double task2 = c.J * (double(c.G * C) + 1.0 + C + 2.0) + 24.0 + C * c.G;
+    const int npairs = fused::pair_slots(ngx);
+    const int t2 = ((c.tile_h + rb - 1) / rb) * ((npairs + 32 / rb - 1) / (32 / rb));
+    const double task2 = c.J * (double(c.G * C) + 2.0 * C + c.G / 2.0 + 1.0) + 30.0 + 2.0 * C * c.G;
     const double pass2 = std::ceil(double(t2) / (fused::kWarps - 4)) * task2;
     const double fill = (double(kpad) * nmb * 128 * esz + double(c.tile_h / c.G + ngx) * band_stride(c.G, c.J) * asz) / 64.0;
     return std::max(std::max(pass1, pass2), fill) / (double(c.tile_h) * c.tile_w);
@@ -451,7 +455,7 @@ std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout, bool tc
                         c.box_w = box_w;
                         c.n1 = 4;
                         c.smem = fused::layout(esz, asz, kpad, box_w, tile_h / G, ngx, band_stride(G, J),
-                                               band_stride(G, J), tile_h, box_w + 1, stages)
+                                               band_stride(2 * G, J), tile_h, box_w + 1, stages)
                                      .total +
                                  fused::align_up(size_t(4) * tile_h * kpad, 128);
                         if (c.smem > smem_cap) continue;
@@ -499,7 +503,7 @@ std::vector<Candidate> enumerate_candidates(rs_plan *p, bool tma_layout, bool tc
                     const int w1 = (bw + 32 * V - 1) / (32 * V) * (32 * V);
                     const int dup = p->work_double ? 1 : 2;
                     c.smem = fused::layout(esz, asz, c.box_h, bw, tile_h / G, ngx, band_stride(G * dup, J),
-                                           band_stride(G, J), tile_h, w1 | 1, stages)
+                                           band_stride(2 * G, J), tile_h, w1 | 1, stages)
                                  .total;
                     if (c.smem > smem_cap) continue;
                     c.cost = model_cost(c, C, esz, asz, V);
@@ -655,7 +659,8 @@ std::string tune_key(const rs_plan *p)
     return buf;
 }
 
-bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int *tw, int *st, int *n1)
+bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int *tw, int *st, int *n1,
+                  int *use_stream)
 {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
@@ -667,22 +672,25 @@ bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int
         if (!std::strstr(line, needle.c_str())) continue;
         const char *q = std::strstr(line, "\"G\":");
         if (q && std::sscanf(q, "\"G\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, \"n1\": %d", G, th, tw,
-                             st, n1) == 5)
+                             st, n1) == 5) {
             found = true; // the last matching line wins
+            const char *r = std::strstr(line, "\"stream\":");
+            *use_stream = (r && std::sscanf(r, "\"stream\": %d", use_stream) == 1) ? *use_stream : 0;
+        }
     }
     std::fclose(f);
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, const Candidate &c, double us)
+void cache_store(const char *path, const std::string &key, const Candidate &c, double us, int use_stream)
 {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"G\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, \"n1\": %d, "
-                 "\"band\": %d, \"us\": %.3f}\n",
-                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us);
+                 "\"band\": %d, \"us\": %.3f, \"stream\": %d}\n",
+                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us, use_stream);
     std::fclose(f);
 }
 
@@ -728,7 +736,7 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.out_dtype < RS_F64 || d.out_dtype > RS_BF16)
         return fail(RS_ERR_INVALID_ARG, "unknown dtype");
     if (d.in_dtype != d.out_dtype) return fail(RS_ERR_UNSUPPORTED, "in_dtype and out_dtype must be equal");
-    if (d.flags & ~uint32_t(0x1f)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
+    if (d.flags & ~uint32_t(0x7f)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
     if (support_radius(d.kernel, d.param) == 0)
         return fail(RS_ERR_INVALID_ARG, "Lanczos needs an integer R in 1..16");
     if (d.kernel == RS_K_CUBIC && !std::isfinite(d.param)) return fail(RS_ERR_INVALID_ARG, "cubic a not finite");
@@ -811,7 +819,22 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     }
     if (st == RS_OK) {
         p->path = 0;
-    } else {
+        // the row-streaming kernel, where it applies, replaces the tile kernel
+        // (which stays configured for inputs it cannot take)
+        const rs_status ss = stream::setup(p, stream);
+        if (ss == RS_OK) {
+            p->use_stream = 1;
+        } else if (ss != RS_ERR_UNSUPPORTED) {
+            delete p;
+            return ss;
+        }
+    }
+    if ((d.flags & RS_FORCE_STREAM) && !p->stream_ok) {
+        delete p;
+        return fail(RS_ERR_UNSUPPORTED, "row-streaming kernel needs FP32, 1 or 3 channels, a 16-byte row pitch "
+                                        "and a horizontal band of at most 16 input pixels");
+    }
+    if (st != RS_OK) {
         p->path = 1;
         const size_t bytes = size_t(d.in_h) * size_t(d.out_w) * size_t(d.channels) * wsz;
         e = cudaMalloc(&p->tmp.p, bytes);
@@ -853,6 +876,7 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
         fp.use_tma = (p->tma_ok && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0) ? 1 : 0;
         if (p->chosen.tc && !fp.use_tma)
             return fail(RS_ERR_INVALID_ARG, "tensor-core plan: the input must be 16-byte aligned");
+        if (p->use_stream && fp.use_tma) return stream::launch(p, d_in, d_out, stream);
         size_t smem = p->smem;
         if (fp.use_tma) {
             rs_status s = encode_map(p, d_in);
@@ -899,13 +923,19 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     std::vector<Candidate> cands = enumerate_candidates(p, tma, tc);
     if (cands.empty()) return RS_OK;
     const std::string key = tune_key(p);
-    int G, th, tw, st, n1;
-    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1)) {
+    // the tile configurations are timed on the tile kernel; the streaming
+    // kernel (if any) is compared with the winner at the end
+    const int stream_ok = p->stream_ok;
+    p->use_stream = 0;
+    int G, th, tw, st, n1, us_cached = 0;
+    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1, &us_cached)) {
         for (const Candidate &c : cands)
             if (c.G == G && c.tile_h == th && c.tile_w == tw && c.stages == st) {
                 Candidate k = c;
                 k.n1 = n1;
-                return apply_fused(p, stream, k, tma);
+                const rs_status s2 = apply_fused(p, stream, k, tma);
+                p->use_stream = (s2 == RS_OK && stream_ok && us_cached) ? 1 : 0;
+                return s2;
             }
     }
     const Candidate before = p->chosen;
@@ -956,7 +986,18 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     }
     rs_status s = apply_fused(p, stream, best, tma);
     if (s != RS_OK) return s;
-    if (best_us < 1e299) cache_store(cache_path, key, best, best_us);
+    if (stream_ok) {
+        // tile winner against the streaming kernel
+        double us_tile = 0, us_stream = 0;
+        s = time_plan(p, d_in, d_out, stream, &us_tile);
+        if (s != RS_OK) return s;
+        p->use_stream = 1;
+        s = time_plan(p, d_in, d_out, stream, &us_stream);
+        if (s != RS_OK) return s;
+        p->use_stream = us_stream < us_tile ? 1 : 0;
+        best_us = std::min(us_tile, us_stream);
+    }
+    if (best_us < 1e299) cache_store(cache_path, key, best, best_us, p->use_stream);
     return RS_OK;
 }
 
@@ -967,6 +1008,7 @@ rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
     cudaError_t e = launch_weights(weight_args(p, 0), weight_args(p, 1), stream);
     if (e == cudaSuccess && p->path == 0) e = launch_band(weight_args(p, 0), weight_args(p, 1), stream);
     if (e != cudaSuccess) return cuda_fail(e, "weight kernel launch");
+    if (p->stream_ok) return stream::rebuild(p, stream);
     return RS_OK;
 }
 
@@ -990,7 +1032,19 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
     info->table_h = p->gy.t_eff;
     info->table_w = p->gx.t_eff;
     info->path = (p->path == 0 && p->chosen.tc) ? 2 : p->path;
-    if (p->path == 0) {
+    if (p->path == 0 && p->use_stream) {
+        info->path = 3;
+        info->tile_h = stream::kRB;
+        info->tile_w = p->sp.SW;
+        info->group_h = stream::kGV;
+        info->group_w = stream::kG;
+        info->span_h = p->sp.JV;
+        info->span_w = p->sp.JH;
+        info->warps_pass1 = 0;
+        info->stages = p->sp.NI;
+        info->smem_bytes = int32_t(p->s_smem);
+        info->ctas_per_sm = p->s_ctas;
+    } else if (p->path == 0) {
         info->tile_h = p->fp.tile_h;
         info->tile_w = p->fp.tile_w;
         info->group_h = info->group_w = p->G;

@@ -46,6 +46,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kErrBounds = 201;  // a band would read outside the staged tile
 constexpr int kErrTimeout = 202; // an mbarrier wait ran out
 constexpr int kOffCache = 2048;  // batch tile prefix sums kept in shared memory
+constexpr int kPrefetch = 2;     // tiles ahead whose input is prefetched into L2
 
 template <typename A, typename T> __device__ __forceinline__ A to_acc(T v);
 template <> __device__ __forceinline__ float to_acc<float, float>(float v) { return v; }
@@ -142,6 +143,23 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// L2 prefetch of a 2-D / 3-D tile (no shared memory, no completion): warms
+// L2 for a later tile copy so that its latency is an L2 hit, not DRAM.
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
 // 1-D bulk copy global -> shared (16-byte aligned addresses, size multiple of 16).
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
@@ -165,9 +183,10 @@ struct Params {
     const int32_t *base_y, *base_x;
     const void *band_y, *band_x; // [groups][js] accumulation type
     int32_t J;                   // band width (inputs per group)
-    int32_t js_y, js_x;          // group strides (elements) of the two bands; the
+    int32_t js_y, js_x;          // slot strides (elements) of the two bands: the
                                  // vertical band of the FP32 path stores every
-                                 // weight twice (packed-pair FMAs)
+                                 // weight twice, the horizontal band interleaves
+                                 // group pairs (both for packed-pair FMAs)
     int32_t tile_h, tile_w;      // output tile (multiples of G)
     int32_t box_h, box_w;        // staged rows, staged samples (pitch of tin)
     int32_t sub_h, n_sub;        // TMA box height and copies per tile
@@ -242,9 +261,12 @@ struct Rec2 {
     int32_t cb[32];
 };
 
+// Horizontal band slots of a tile of ngx groups (groups run in pairs).
+__host__ __device__ inline int pair_slots(int ngx) { return (ngx + 1) / 2; }
+
 __host__ __device__ inline size_t rec2_bytes(int ngx, int js, size_t acc)
 {
-    return align_up(sizeof(Rec2) + size_t(ngx) * js * acc, 128);
+    return align_up(sizeof(Rec2) + size_t(pair_slots(ngx)) * js * acc, 128);
 }
 
 // Shared-memory layout: stages x (tin, wy, wx) | 2 x tt | 2 x (Rec2 + wx copy)
@@ -282,7 +304,7 @@ __host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int
     Layout L;
     L.tin = align_up(size_t(box_h) * box_w * elem, 128);
     L.wy = align_up(size_t(ngy) * js_y * acc, 128);
-    L.wx = align_up(size_t(ngx) * js_x * acc, 128);
+    L.wx = align_up(size_t(pair_slots(ngx)) * js_x * acc, 128);
     L.stage = L.tin + L.wy + L.wx;
     L.tt = align_up(size_t(tile_h) * pitch_t * acc, 128);
     L.rec2 = rec2_bytes(ngx, js_x, acc);
@@ -343,6 +365,28 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+// Two consecutive staged samples as a packed FP32 pair (one 8-byte load for
+// FP32, one 4-byte load converted for the 16-bit types).
+template <typename T> __device__ __forceinline__ uint64_t load_pair(const T *p);
+template <> __device__ __forceinline__ uint64_t load_pair<float>(const float *p)
+{
+    return *reinterpret_cast<const uint64_t *>(p);
+}
+template <> __device__ __forceinline__ uint64_t load_pair<__half>(const __half *p)
+{
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(p));
+    return pack2(f.x, f.y);
+}
+template <> __device__ __forceinline__ uint64_t load_pair<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    return pack2(f.x, f.y);
+}
+template <> __device__ __forceinline__ uint64_t load_pair<double>(const double *p)
+{
+    return 0ull; // unused: the FP64 path is not packed
+}
+
 // N consecutive 8-byte pairs from shared memory (16-byte loads when N is even).
 template <int N> __device__ __forceinline__ void load_pairs(uint64_t (&w)[N], const uint64_t *p)
 {
@@ -503,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             const int ngy = P.tile_h / G, ngx = P.tile_w / G;
             const int ty = ti.t / P.tiles_x, tx = ti.t % P.tiles_x;
             const uint32_t by = uint32_t(ti.nvy) * P.js_y * sizeof(A);
-            const uint32_t bx = uint32_t(ti.nvx) * P.js_x * sizeof(A);
+            const uint32_t bx = uint32_t(pair_slots(ti.nvx)) * P.js_x * sizeof(A);
             const uint32_t bt = uint32_t(P.n_sub) * P.sub_h * P.box_w * sizeof(T);
             mbar_arrive_expect_tx(&full[s], bt + by + bx);
             const CUtensorMap *map = batch ? w.maps + ti.img : &tmap;
@@ -515,7 +559,24 @@ __global__ void __launch_bounds__(kThreads, 3)
                     tma_load_2d(dst + size_t(q) * P.sub_h * P.box_w, map, &full[s], ti.xs, ti.ry0 + q * P.sub_h);
             }
             bulk_load(stage_wy(s), static_cast<const A *>(P.band_y) + size_t(ty) * ngy * P.js_y, by, &full[s]);
-            bulk_load(stage_wx(s), static_cast<const A *>(P.band_x) + size_t(tx) * ngx * P.js_x, bx, &full[s]);
+            // warm L2 with the input of this CTA's tile kPrefetch further on
+            // (single image: the tile's first groups carry its smallest bases)
+            for (int a = (k == 0 ? 1 : kPrefetch); a <= kPrefetch && !batch; ++a) {
+                const int tn = int(blockIdx.x) + (k + a) * int(gridDim.x);
+                if (tn < P.tiles_y * P.tiles_x) {
+                    const int nty = tn / P.tiles_x, ntx = tn % P.tiles_x;
+                    const int ry = __ldg(P.base_y + nty * ngy);
+                    const int s0 = __ldg(P.base_x + ntx * ngx) * C;
+                    const int nxs = s0 - (s0 % kVec);
+                    if constexpr (TC) {
+                        tma_prefetch_3d(map, 0, ry, nxs / 8);
+                    } else {
+                        for (int q = 0; q < P.n_sub; ++q) tma_prefetch_2d(map, nxs, ry + q * P.sub_h);
+                    }
+                }
+            }
+            bulk_load(stage_wx(s), static_cast<const A *>(P.band_x) + size_t(tx) * pair_slots(ngx) * P.js_x, bx,
+                      &full[s]);
         }
     };
 
@@ -554,9 +615,9 @@ __global__ void __launch_bounds__(kThreads, 3)
                     }
                     A *wy = stage_wy(0), *wx = stage_wx(0);
                     const A *sy = static_cast<const A *>(P.band_y) + size_t(ty) * ngy * P.js_y;
-                    const A *sx = static_cast<const A *>(P.band_x) + size_t(tx) * ngx * P.js_x;
+                    const A *sx = static_cast<const A *>(P.band_x) + size_t(tx) * pair_slots(ngx) * P.js_x;
                     for (int e = threadIdx.x; e < ti.nvy * P.js_y; e += t1n) wy[e] = __ldg(sy + e);
-                    for (int e = threadIdx.x; e < ti.nvx * P.js_x; e += t1n) wx[e] = __ldg(sx + e);
+                    for (int e = threadIdx.x; e < pair_slots(ti.nvx) * P.js_x; e += t1n) wx[e] = __ldg(sx + e);
                 }
                 named_sync(1, t1n);
             }
@@ -652,12 +713,14 @@ __global__ void __launch_bounds__(kThreads, 3)
                         if (lane == 0) flag(err, kErrBounds);
                         continue;
                     }
-                    const int c0 = k * 32 * V + lane;
-                    const T *col = tin + rb * box_w + c0;
-                    A *dst = tt + q * G * pitch_t + c0;
                     if constexpr (kPacked) {
-                        // column pairs (v, v+1) share one packed FMA; the vertical
-                        // band holds every weight twice, so pairs load as they are
+                        // lane owns the column pairs (2 lane, 2 lane + 1) + 64 u: one
+                        // 8-byte (FP32) or 4-byte (16-bit) load gives a pair ready
+                        // for the packed FMA; the vertical band holds every
+                        // weight twice, so weight pairs load as they are
+                        const int c0 = k * 32 * V + 2 * lane;
+                        const T *col = tin + rb * box_w + c0;
+                        A *dst = tt + q * G * pitch_t + c0;
                         uint64_t acc2[G][V / 2];
     #pragma unroll
                         for (int g = 0; g < G; ++g)
@@ -669,15 +732,13 @@ __global__ void __launch_bounds__(kThreads, 3)
                             uint64_t w2[G];
                             load_pairs<G>(w2, wq);
                             wq += G;
-                            float d[V];
+                            uint64_t dd[V / 2];
     #pragma unroll
-                            for (int v = 0; v < V; ++v) d[v] = to_acc<A, T>(col[32 * v]);
+                            for (int u = 0; u < V / 2; ++u) dd[u] = load_pair<T>(col + 64 * u);
     #pragma unroll
-                            for (int u = 0; u < V / 2; ++u) {
-                                const uint64_t dd = pack2(d[2 * u], d[2 * u + 1]);
+                            for (int u = 0; u < V / 2; ++u)
     #pragma unroll
-                                for (int g = 0; g < G; ++g) acc2[g][u] = fma2(w2[g], dd, acc2[g][u]);
-                            }
+                                for (int g = 0; g < G; ++g) acc2[g][u] = fma2(w2[g], dd[u], acc2[g][u]);
                             col += box_w;
                         }
     #pragma unroll
@@ -686,10 +747,13 @@ __global__ void __launch_bounds__(kThreads, 3)
                             for (int u = 0; u < V / 2; ++u) {
                                 float lo, hi;
                                 unpack2(acc2[g][u], lo, hi);
-                                dst[g * pitch_t + 32 * (2 * u)] = lo;
-                                dst[g * pitch_t + 32 * (2 * u + 1)] = hi;
+                                dst[g * pitch_t + 64 * u] = lo;
+                                dst[g * pitch_t + 64 * u + 1] = hi;
                             }
                     } else {
+                        const int c0 = k * 32 * V + lane;
+                        const T *col = tin + rb * box_w + c0;
+                        A *dst = tt + q * G * pitch_t + c0;
                         A acc[G][V];
     #pragma unroll
                         for (int g = 0; g < G; ++g)
@@ -734,7 +798,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             {
                 const A *src = stage_wx(s);
                 A *dstw = rec2_w(b);
-                for (int e = threadIdx.x; e < ti.nvx * P.js_x; e += t1n) dstw[e] = src[e];
+                for (int e = threadIdx.x; e < pair_slots(ti.nvx) * P.js_x; e += t1n) dstw[e] = src[e];
             }
             mbar_arrive(&ttfull[b]);
             // every pass-1 warp is done with stage s before it is refilled
@@ -762,103 +826,122 @@ __global__ void __launch_bounds__(kThreads, 3)
             const A *tt = tt_buf(b);
             const A *wxs = rec2_w(b);
             const int J = P.J;
-            const int pitch_t = P.pitch_t;
+            const int pitch_t = P.pitch_t, js_x = P.js_x, box_w = P.box_w, tile_h = P.tile_h;
             const int ngx = P.tile_w / G;
             const int ty = r2->ty, tx = r2->tx, nvx = r2->nvx;
-            const int RB = P.tile_h < 32 ? P.tile_h : 32; // rows per warp task
-            const int GPW = 32 / RB;                      // groups per warp task
+            const int64_t out_h = P.out_h, out_w = P.out_w, out_stride = P.out_stride;
+            T *out = static_cast<T *>(P.out);
+            // Lanes run along output rows; each lane takes the pair of groups
+            // (2 pq, 2 pq + 1) of its row, whose weights the band interleaves,
+            // so one packed FMA advances both groups.
+            const int RB = tile_h < 32 ? tile_h : 32; // rows per warp task
+            const int GPW = 32 / RB;                  // group pairs per warp task
             const int rsub = lane % RB, gsub = lane / RB;
-            const int nrb = (P.tile_h + RB - 1) / RB;
-            const int npg = (nvx + GPW - 1) / GPW;
+            const int nrb = (tile_h + RB - 1) / RB;
+            const int npairs = pair_slots(nvx);
+            const int npg = (npairs + GPW - 1) / GPW;
             const int ntask = nrb * npg;
             const int per = (ntask + n2 - 1) / n2;
             const int k0 = w2 * per, k1 = min(ntask, k0 + per);
-            T *out = static_cast<T *>(P.out);
             for (int task = k0; task < k1; ++task) {
                 const int rbk = task / npg, pg = task - rbk * npg;
-                const int q = pg * GPW + gsub;
+                const int pq = pg * GPW + gsub;
                 const int row = rbk * RB + rsub;
-                const int64_t yo = int64_t(ty) * P.tile_h + row;
-                const int gx = tx * ngx + q;
-                if (q >= nvx || row >= P.tile_h || yo >= P.out_h) continue;
-                const int cb = r2->cb[q];
-                if (cb < 0 || cb + J * C > P.box_w) {
+                const int64_t yo = int64_t(ty) * tile_h + row;
+                if (pq >= npairs || row >= tile_h || yo >= out_h) continue;
+                const int q0 = 2 * pq;
+                const bool has1 = q0 + 1 < nvx;
+                const int cb0 = r2->cb[q0];
+                const int cb1 = has1 ? r2->cb[q0 + 1] : cb0;
+                if (cb0 < 0 || cb0 + J * C > box_w || cb1 < 0 || cb1 + J * C > box_w) {
                     flag(err, kErrBounds);
                     continue;
                 }
-                A acc[G][C];
-                const A *rowp = tt + row * pitch_t + cb;
-                const A *wq = wxs + q * P.js_x;
-                if constexpr (kPacked && G % 2 == 0) {
-                    // member pairs (g, g+1) share one packed FMA; their weights
-                    // are adjacent in the band
-                    uint64_t acc2[G / 2][C];
-#pragma unroll
-                    for (int h = 0; h < G / 2; ++h)
-#pragma unroll
-                        for (int c = 0; c < C; ++c) acc2[h][c] = 0ull;
-                    const uint64_t *wq2 = reinterpret_cast<const uint64_t *>(wq);
-#pragma unroll 4
-                    for (int j = 0; j < J; ++j) {
-                        uint64_t wp[G / 2];
-                        load_pairs<G / 2>(wp, wq2);
-                        wq2 += G / 2;
-#pragma unroll
-                        for (int c = 0; c < C; ++c) {
-                            const float dv = rowp[c];
-                            const uint64_t dd = pack2(dv, dv);
-#pragma unroll
-                            for (int h = 0; h < G / 2; ++h) acc2[h][c] = fma2(wp[h], dd, acc2[h][c]);
-                        }
-                        rowp += C;
-                    }
-#pragma unroll
-                    for (int h = 0; h < G / 2; ++h)
-#pragma unroll
-                        for (int c = 0; c < C; ++c) unpack2(acc2[h][c], acc[2 * h][c], acc[2 * h + 1][c]);
-                } else {
+                A acc[2][G][C];
+                const A *rp0 = tt + row * pitch_t + cb0;
+                const A *rp1 = tt + row * pitch_t + cb1;
+                if constexpr (sizeof(A) == 4) {
+                    uint64_t acc2[G][C];
 #pragma unroll
                     for (int g = 0; g < G; ++g)
 #pragma unroll
-                        for (int c = 0; c < C; ++c) acc[g][c] = A(0);
+                        for (int c = 0; c < C; ++c) acc2[g][c] = 0ull;
+                    const uint64_t *wq2 = reinterpret_cast<const uint64_t *>(wxs + pq * js_x);
 #pragma unroll 4
                     for (int j = 0; j < J; ++j) {
-                        A wv[G];
-                        load_w<A, G>(wv, wq);
-                        wq += G;
+                        uint64_t wp[G];
+                        load_pairs<G>(wp, wq2);
+                        wq2 += G;
 #pragma unroll
                         for (int c = 0; c < C; ++c) {
-                            const A d = rowp[c];
+                            const uint64_t dd = pack2(rp0[c], rp1[c]);
 #pragma unroll
-                            for (int g = 0; g < G; ++g) acc[g][c] = fma(wv[g], d, acc[g][c]);
+                            for (int g = 0; g < G; ++g) acc2[g][c] = fma2(wp[g], dd, acc2[g][c]);
                         }
-                        rowp += C;
+                        rp0 += C;
+                        rp1 += C;
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+#pragma unroll
+                        for (int c = 0; c < C; ++c) {
+                            float lo, hi;
+                            unpack2(acc2[g][c], lo, hi);
+                            acc[0][g][c] = lo;
+                            acc[1][g][c] = hi;
+                        }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+#pragma unroll
+                            for (int c = 0; c < C; ++c) acc[h][g][c] = A(0);
+                    const A *wq = wxs + pq * js_x;
+#pragma unroll 2
+                    for (int j = 0; j < J; ++j) {
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            const A w0 = wq[2 * g], w1 = wq[2 * g + 1];
+#pragma unroll
+                            for (int c = 0; c < C; ++c) {
+                                acc[0][g][c] = fma(w0, rp0[c], acc[0][g][c]);
+                                acc[1][g][c] = fma(w1, rp1[c], acc[1][g][c]);
+                            }
+                        }
+                        wq += 2 * G;
+                        rp0 += C;
+                        rp1 += C;
                     }
                 }
-                // Store G*C contiguous samples of this row (clipped at the right edge).
-                const int64_t x0 = int64_t(gx) * G;
-                T *o = out + yo * P.out_stride + x0 * C;
-                const int nvalid = P.out_w - x0 < G ? int(P.out_w - x0) : G;
-                constexpr int kRun = G * C;
-                constexpr int kRunBytes = kRun * int(sizeof(T));
-                if (nvalid == G && (kRunBytes % 16) == 0 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
-                    union {
-                        T e[kRun];
-                        uint4 v[kRunBytes / 16 > 0 ? kRunBytes / 16 : 1];
-                    } u;
+                // Store G*C contiguous samples of each group's row (clipped at the right edge).
 #pragma unroll
-                    for (int g = 0; g < G; ++g)
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !has1) break;
+                    const int64_t x0 = (int64_t(tx) * ngx + q0 + h) * G;
+                    T *o = out + yo * out_stride + x0 * C;
+                    const int nvalid = out_w - x0 < G ? int(out_w - x0) : G;
+                    constexpr int kRun = G * C;
+                    constexpr int kRunBytes = kRun * int(sizeof(T));
+                    if (nvalid == G && (kRunBytes % 16) == 0 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+                        union {
+                            T e[kRun];
+                            uint4 v[kRunBytes / 16 > 0 ? kRunBytes / 16 : 1];
+                        } u;
 #pragma unroll
-                        for (int c = 0; c < C; ++c) u.e[g * C + c] = from_acc<T, A>(acc[g][c]);
-                    uint4 *ov = reinterpret_cast<uint4 *>(o);
+                        for (int g = 0; g < G; ++g)
 #pragma unroll
-                    for (int v = 0; v < kRunBytes / 16; ++v) ov[v] = u.v[v];
-                } else {
+                            for (int c = 0; c < C; ++c) u.e[g * C + c] = from_acc<T, A>(acc[h][g][c]);
+                        uint4 *ov = reinterpret_cast<uint4 *>(o);
 #pragma unroll
-                    for (int g = 0; g < G; ++g)
-                        if (g < nvalid)
+                        for (int v = 0; v < kRunBytes / 16; ++v) ov[v] = u.v[v];
+                    } else {
 #pragma unroll
-                            for (int c = 0; c < C; ++c) o[g * C + c] = from_acc<T, A>(acc[g][c]);
+                        for (int g = 0; g < G; ++g)
+                            if (g < nvalid)
+#pragma unroll
+                                for (int c = 0; c < C; ++c) o[g * C + c] = from_acc<T, A>(acc[h][g][c]);
+                    }
                 }
             }
             mbar_arrive(&ttempty[b]);

@@ -43,14 +43,34 @@ struct AxisTables {
     // group g reads inputs [base[g], base[g] + J) with the weight of member r
     // and input j stored `dup` times (1, or 2 for packed-pair FMAs) at
     // band_w[g * band_stride(G * dup, J) + (j * G + r) * dup + d].
+    // With pair_ngx > 0 (the horizontal band of the fused kernel) the groups
+    // of every tile of pair_ngx groups are taken two at a time: slot s holds
+    // tile s / P, pair p = s % P (P = ceil(pair_ngx / 2)), and the weights of
+    // its groups q0 = tile * pair_ngx + 2p and q0 + 1 interleaved at
+    // band_w[s * band_stride(2 G, J) + (j * G + r) * 2 + d] (d selects the
+    // group; zeros for a group past the tile or the axis), so that one lane
+    // runs both groups with packed-pair FMAs.
     int32_t *band_base = nullptr; // [groups]
-    void *band_w = nullptr;       // [groups][band_stride(G * dup, J)] working precision
+    void *band_w = nullptr;       // [band_slots][band_slot_stride] working precision
     int32_t G = 0, J = 0, groups = 0, dup = 1;
+    int32_t pair_ngx = 0;
 };
 
 // Floats per band group: J * G rounded up to a multiple of 4, so that every
 // group starts on a 16-byte boundary (TMA bulk copies need that).
 __host__ __device__ inline int band_stride(int G, int J) { return (J * G + 3) / 4 * 4; }
+
+// Slots of a band (groups, or tile-local group pairs) and floats per slot.
+__host__ __device__ inline int64_t band_slots(const AxisTables &t)
+{
+    if (t.pair_ngx <= 0) return t.groups;
+    const int64_t tiles = (int64_t(t.groups) + t.pair_ngx - 1) / t.pair_ngx;
+    return tiles * ((t.pair_ngx + 1) / 2);
+}
+__host__ __device__ inline int band_slot_stride(const AxisTables &t)
+{
+    return band_stride(t.G * (t.pair_ngx > 0 ? 2 : t.dup), t.J);
+}
 
 // Parameters of the weight-table kernel for one axis (passed by value).
 struct WeightArgs {

@@ -9,6 +9,7 @@
 
 #include "rs_fused.cuh"
 #include "rs_internal.h"
+#include "rs_stream.cuh"
 
 namespace rs {
 
@@ -67,6 +68,16 @@ struct rs_plan {
     int64_t scratch_bytes = 0;
     std::vector<int32_t> host_start_y, host_start_x; // for re-planning and tuning
     rs::Candidate chosen;                            // fused configuration in use
+    // row-streaming kernel (FP32 upscales and mild downscales)
+    int stream_ok = 0;  // a streaming configuration exists
+    int use_stream = 0; // rs_resample runs it (else the tile kernel above)
+    rs::stream::Params sp{};
+    rs::DeviceBuf sbufs;
+    CUtensorMap stmap;
+    const void *stmap_ptr = nullptr;
+    const void *s_fn = nullptr;
+    size_t s_smem = 0;
+    int s_grid = 0, s_ctas = 0;
 };
 
 namespace rs {
@@ -97,5 +108,14 @@ void work_regions(const rs_plan *p, fused::Work *w);
 fused::Work single_work(const rs_plan *p, int use_tma);
 // Cost of a candidate in modelled SM cycles per output pixel (also sets n1).
 double model_cost(Candidate &c, int C, size_t esz, size_t asz, int V);
+
+namespace stream {
+// Configures the row-streaming kernel for a plan (needs the host start tables);
+// RS_ERR_UNSUPPORTED when the plan is not eligible.
+rs_status setup(rs_plan *p, cudaStream_t s);
+// Rebuilds its band tables from the plan's weight tables (after a recompute).
+rs_status rebuild(rs_plan *p, cudaStream_t s);
+rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
+} // namespace stream
 
 } // namespace rs

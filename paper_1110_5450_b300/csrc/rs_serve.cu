@@ -239,7 +239,8 @@ FastPlan fast_plan(rs_server *S, Req *q)
         const int V = var->V;
         const int64_t J = std::max(span(q->gy, G - 1) + q->gy.t_eff, span(q->gx, G - 1) + q->gx.t_eff);
         if (J > 256) continue;
-        const int js_y = band_stride(G * dup, int(J)), js_x = band_stride(G, int(J));
+        // the horizontal band interleaves group pairs
+        const int js_y = band_stride(G * dup, int(J)), js_x = band_stride(2 * G, int(J));
         for (int tile_h : {32, 16, 8}) {
             if (tile_h % G) continue;
             const int ngy = tile_h / G;
@@ -294,9 +295,11 @@ FastPlan fast_plan(rs_server *S, Req *q)
                     const AxisGeom &g = *gs[a];
                     const int64_t groups = (g.n_out + G - 1) / G;
                     const int js = a == 0 ? js_y : js_x;
+                    const int64_t slots =
+                        a == 0 ? groups : (groups + ngx - 1) / ngx * fused::pair_slots(ngx);
                     tb += 3 * up256(size_t(g.n_out) * 4) + up256(size_t(g.n_out) * g.t_eff * 8) +
                           up256(size_t(g.n_out) * g.t_eff * asz) + up256(size_t(groups) * 4) +
-                          up256(size_t(groups) * js * asz);
+                          up256(size_t(slots) * js * asz);
                 }
                 q->tab_bytes = tb;
                 q->own_out = q->r.d_out == nullptr;
@@ -331,6 +334,7 @@ void place_tables(rs_server *S, Req *q)
         t.J = q->P.J;
         t.groups = int32_t(groups);
         t.dup = (a == 0 && asz == 4) ? 2 : 1;
+        t.pair_ngx = a == 1 ? q->P.tile_w / q->G : 0;
         const int js = a == 0 ? q->P.js_y : q->P.js_x;
         t.jlo = reinterpret_cast<int32_t *>(take(size_t(g.n_out) * 4));
         t.cnt = reinterpret_cast<int32_t *>(take(size_t(g.n_out) * 4));
@@ -338,7 +342,7 @@ void place_tables(rs_server *S, Req *q)
         t.w64 = reinterpret_cast<double *>(take(size_t(g.n_out) * g.t_eff * 8));
         t.wwork = take(size_t(g.n_out) * g.t_eff * asz);
         t.band_base = reinterpret_cast<int32_t *>(take(size_t(groups) * 4));
-        t.band_w = take(size_t(groups) * js * asz);
+        t.band_w = take(size_t(band_slots(t)) * js * asz);
     }
     q->P.base_y = q->ty.band_base;
     q->P.base_x = q->tx.band_base;

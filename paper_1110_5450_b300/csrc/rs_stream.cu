@@ -1,0 +1,276 @@
+// rs_stream.cu -- host side of the row-streaming kernel (rs_stream.cuh): its
+// band tables, configuration, tensor map and launch.  Used by FP32 plans of 1
+// or 3 channels whose horizontal band is narrow (upscales and mild
+// downscales); every other plan runs the tile kernel.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rs_plan.h"
+#include "rs_stream.cuh"
+
+namespace rs {
+namespace stream {
+namespace {
+
+// Horizontal band of groups of 4 outputs with a 4-pixel aligned start:
+// hbase[q] = (smallest window start of the group) rounded down to a multiple
+// of 4, hband[q][j][g] = weight of output 4q + g at input hbase[q] + j.  The
+// window may run past the input's end (the staged copy reads zeros there).
+__global__ void hband_kernel(AxisGeom g, const int32_t *start, const float *w, int32_t *hbase, float *hband,
+                             int groups, int JH)
+{
+    const int64_t n = int64_t(groups) * JH * kG;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t q = e / (JH * kG);
+        const int j = int((e / kG) % JH), r = int(e % kG);
+        int64_t lo = g.n_in;
+        for (int m = 0; m < kG; ++m) {
+            const int64_t i = q * kG + m;
+            if (i < g.n_out) lo = min(lo, int64_t(start[i]));
+        }
+        const int64_t b = lo & ~int64_t(3);
+        if (j == 0 && r == 0) hbase[q] = int32_t(b);
+        const int64_t i = q * kG + r;
+        float v = 0.f;
+        if (i < g.n_out) {
+            const int64_t off = start[i] - b;
+            if (j >= off && j < off + g.t_eff) v = w[i * g.t_eff + (j - off)];
+        }
+        hband[e] = v;
+    }
+}
+
+const void *kernel_for(int C)
+{
+    if (C == 1) return reinterpret_cast<const void *>(&stream_kernel<1>);
+    if (C == 3) return reinterpret_cast<const void *>(&stream_kernel<3>);
+    return nullptr;
+}
+
+int pad_pitch(int n) // multiple of 4 with n / 4 odd, >= n
+{
+    int p = (n + 3) / 4 * 4;
+    if ((p / 4) % 2 == 0) p += 4;
+    return p;
+}
+
+} // namespace
+
+rs_status setup(rs_plan *p, cudaStream_t s)
+{
+    p->stream_ok = 0;
+    const rs_plan_desc &d = p->desc;
+    const int C = d.channels;
+    if (d.in_dtype != RS_F32 || (C != 1 && C != 3) || (d.flags & RS_NO_STREAM)) return RS_ERR_UNSUPPORTED;
+    if (!tma_layout_ok(p)) return RS_ERR_UNSUPPORTED;
+    const std::vector<int32_t> &sx = p->host_start_x, &sy = p->host_start_y;
+    const AxisGeom &gx = p->gx, &gy = p->gy;
+    // horizontal band: 4-pixel aligned group bases
+    const int groups_x = int((gx.n_out + kG - 1) / kG);
+    std::vector<int32_t> hb(groups_x);
+    int JH = 0;
+    for (int q = 0; q < groups_x; ++q) {
+        int lo = int(gx.n_in), hi = 0;
+        for (int m = 0; m < kG && q * kG + m < gx.n_out; ++m) {
+            lo = std::min(lo, int(sx[q * kG + m]));
+            hi = std::max(hi, int(sx[q * kG + m]) + gx.t_eff);
+        }
+        hb[q] = lo & ~3;
+        JH = std::max(JH, hi - hb[q]);
+    }
+    JH = (JH + 3) / 4 * 4;
+    // vertical band of groups of 4 output rows (the tile kernel's band code, G = 4)
+    int JV = 0;
+    for (size_t i = 0; i < sy.size(); i += kGV) {
+        int lo = sy[i], hi = sy[i] + gy.t_eff;
+        for (size_t r = 1; r < size_t(kGV) && i + r < sy.size(); ++r) {
+            lo = std::min(lo, int(sy[i + r]));
+            hi = std::max(hi, int(sy[i + r]) + gy.t_eff);
+        }
+        JV = std::max(JV, hi - lo);
+    }
+    JV = (JV + 1) / 2 * 2;
+    if (JH > 16 || JV > 64 || JV > gy.n_in) return RS_ERR_UNSUPPORTED;
+    // row bases of the groups (as the band kernel computes them) and the most
+    // groups whose last row falls in one 32-row block
+    const int pairs = int((gy.n_out + kGV - 1) / kGV);
+    std::vector<int32_t> vb(pairs);
+    for (int q = 0; q < pairs; ++q) {
+        int lo = sy[kGV * q];
+        for (int r = 1; r < kGV && kGV * q + r < int(sy.size()); ++r) lo = std::min(lo, int(sy[kGV * q + r]));
+        vb[q] = gy.n_in >= JV ? std::min<int64_t>(lo, gy.n_in - JV) : 0;
+    }
+    int WP = 0;
+    for (int a = 0, b = 0; a < pairs; ++a) {
+        while (b < pairs && vb[b] + JV <= vb[a] + JV + kRB - 1) ++b;
+        WP = std::max(WP, b - a);
+    }
+    WP = std::max(WP, 1);
+    // the widest strip (multiple of 4 outputs, at most 128) whose staged width
+    // fits one TMA box and whose CTA (3 staged blocks) keeps two CTAs per SM
+    const int HR = kRB + JV, M = JV - 1;
+    int SW = 0, P = 0, Q = 0, NI = 0;
+    size_t smem = 0;
+    for (int sw = 128; sw >= 16 && SW == 0; sw -= 4) {
+        const int ngx = sw / kG;
+        int need = 0;
+        for (int g0 = 0; g0 < groups_x; g0 += ngx) {
+            const int gl = std::min(groups_x, g0 + ngx) - 1;
+            need = std::max(need, (hb[gl] + JH - hb[g0]) * C);
+        }
+        const int pp = pad_pitch(need);
+        if (pp > 256) continue;
+        const int qq = pad_pitch(sw * C);
+        for (int ni = kMaxNI; ni >= 3; --ni) {
+            const size_t t = layout(ni, pp, HR, M, qq, ngx, JH, WP, JV).total;
+            if (t <= 113 * 1024) {
+                SW = sw;
+                P = pp;
+                Q = qq;
+                NI = ni;
+                smem = t;
+                break;
+            }
+        }
+    }
+    if (SW == 0) return RS_ERR_UNSUPPORTED;
+    const int ngx = SW / kG;
+    const void *fn = kernel_for(C);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return cuda_fail(e, "setting shared memory size");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (occ < 1) return RS_ERR_UNSUPPORTED;
+    // row ranges: enough CTAs for whole waves (>= 90% of the last wave busy),
+    // each range within the kernel's per-CTA block budget
+    const int n_strips = (groups_x + ngx - 1) / ngx;
+    const int slots = occ * p->num_sms;
+    auto blocks_ok = [&](int ppr) {
+        for (int q0 = 0; q0 < pairs; q0 += ppr) {
+            const int q1 = std::min(pairs, q0 + ppr) - 1;
+            if ((vb[q1] + JV - vb[q0] + kRB - 1) / kRB > kMaxBlk) return false;
+        }
+        return true;
+    };
+    int ppr = 0;
+    for (int nr = 1; nr <= 1024; ++nr) {
+        const int cand = (pairs + nr - 1) / nr;
+        if (cand < 8 && nr > 1 && ppr) break;
+        if (!blocks_ok(cand)) continue;
+        const int64_t grid = int64_t(n_strips) * ((pairs + cand - 1) / cand);
+        const int64_t waves = (grid + slots - 1) / slots;
+        ppr = cand;
+        if (grid >= slots && double(grid) / double(waves * slots) >= 0.9) break;
+    }
+    if (ppr == 0) return RS_ERR_UNSUPPORTED;
+
+    // device tables: horizontal base + band, vertical base + band
+    Carver cv;
+    const size_t o_hb = cv.take(size_t(groups_x) * 4);
+    const size_t o_hw = cv.take(size_t(groups_x) * JH * kG * 4);
+    const size_t o_vb = cv.take(size_t((pairs + 3) & ~3) * 4); // the kernel copies whole 16-byte words
+    const size_t o_vw = cv.take(size_t(pairs) * JV * 8 * 4);
+    if (p->sbufs.p) {
+        cudaFree(p->sbufs.p);
+        p->sbufs.p = nullptr;
+    }
+    e = cudaMalloc(&p->sbufs.p, cv.off);
+    if (e != cudaSuccess) return cuda_fail(e, "allocating stream tables");
+    p->sbufs.n = cv.off;
+    char *base = static_cast<char *>(p->sbufs.p);
+    Params &sp = p->sp;
+    std::memset(&sp, 0, sizeof sp);
+    sp.in_h = gy.n_in;
+    sp.in_w = gx.n_in;
+    sp.out_h = gy.n_out;
+    sp.out_w = gx.n_out;
+    sp.in_stride = d.in_row_stride;
+    sp.out_stride = d.out_row_stride;
+    sp.hbase = reinterpret_cast<const int32_t *>(base + o_hb);
+    sp.hband = reinterpret_cast<const float *>(base + o_hw);
+    sp.vbase = reinterpret_cast<const int32_t *>(base + o_vb);
+    sp.vband = reinterpret_cast<const float *>(base + o_vw);
+    sp.JH = JH;
+    sp.JV = JV;
+    sp.SW = SW;
+    sp.n_strips = n_strips;
+    sp.pairs = pairs;
+    sp.pairs_per_range = ppr;
+    sp.groups_x = groups_x;
+    sp.P = P;
+    sp.Q = Q;
+    sp.NI = NI;
+    sp.HR = HR;
+    sp.M = M;
+    sp.WP = WP;
+    sp.err = p->d_err;
+    rs_status st = rebuild(p, s);
+    if (st != RS_OK) return st;
+    p->s_fn = fn;
+    p->s_smem = smem;
+    p->s_grid = n_strips * ((pairs + ppr - 1) / ppr);
+    p->s_ctas = occ;
+    p->stmap_ptr = nullptr;
+    p->stream_ok = 1;
+    p->scratch_bytes = int64_t(p->tables.n + p->bands.n + p->tmp.n + p->sbufs.n);
+    return RS_OK;
+}
+
+rs_status rebuild(rs_plan *p, cudaStream_t s)
+{
+    const Params &sp = p->sp;
+    const int64_t n = int64_t(sp.groups_x) * sp.JH * kG;
+    const int blocks = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+    hband_kernel<<<std::max(1, blocks), 256, 0, s>>>(p->gx, p->tx.start, static_cast<const float *>(p->tx.wwork),
+                                                     const_cast<int32_t *>(sp.hbase), const_cast<float *>(sp.hband),
+                                                     sp.groups_x, sp.JH);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "horizontal band launch");
+    // vertical band: groups of 4 rows, every weight twice -> per tap (w0, w0, .., w3, w3)
+    AxisTables vt = p->ty;
+    vt.G = kGV;
+    vt.J = sp.JV;
+    vt.groups = sp.pairs;
+    vt.dup = 2;
+    vt.pair_ngx = 0;
+    vt.band_base = const_cast<int32_t *>(sp.vbase);
+    vt.band_w = const_cast<float *>(sp.vband);
+    WeightArgs a0;
+    a0.g = p->gy;
+    a0.t = vt;
+    a0.work_is_double = 0;
+    a0.err = p->d_err;
+    WeightArgs a1 = a0;
+    a1.t.groups = 0; // second axis unused
+    e = launch_band(a0, a1, s);
+    if (e != cudaSuccess) return cuda_fail(e, "vertical band launch");
+    return RS_OK;
+}
+
+rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s)
+{
+    const rs_plan_desc &d = p->desc;
+    if (p->stmap_ptr != d_in) {
+        cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};
+        cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * 4)};
+        cuuint32_t box[2] = {cuuint32_t(p->sp.P), cuuint32_t(kRB)};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode_fn()(&p->stmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(d_in), dims,
+                                 strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(RS_ERR_CUDA, "stream tensor map encoding failed");
+        p->stmap_ptr = d_in;
+    }
+    Params sp = p->sp;
+    sp.in = static_cast<const float *>(d_in);
+    sp.out = static_cast<float *>(d_out);
+    void *args[2] = {&p->stmap, &sp};
+    cudaError_t e = cudaLaunchKernel(p->s_fn, dim3(p->s_grid), dim3(kThreads), args, p->s_smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream kernel launch");
+    return RS_OK;
+}
+
+} // namespace stream
+} // namespace rs

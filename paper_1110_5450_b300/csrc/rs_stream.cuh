@@ -1,0 +1,299 @@
+// rs_stream.cuh -- the row-streaming resample kernel (horizontal pass first).
+//
+// A CTA owns a strip of SW output columns and a range of output-row pairs.  It
+// walks down the input rows the range needs in blocks of 32 rows:
+//   * a ring of NI staged input blocks is kept filled by TMA copies (thread 0
+//     re-issues a slot as soon as its block has been consumed, so NI - 1
+//     copies are in flight while one block is processed);
+//   * the horizontal pass turns each staged input row into the strip's SW
+//     output columns (lanes run along the 32 rows of a block, every lane holds
+//     the 4-pixel chunks of its row in registers and applies the band of G = 4
+//     outputs; the band's start is 4-pixel aligned, so chunks load as 16-byte
+//     words) and appends the results to a ring of horizontally filtered rows;
+//   * the vertical pass turns every group of 4 output rows whose taps are all
+//     in that ring into its rows (lanes along 4-sample chunks of the strip,
+//     packed FP32 FMAs, each loaded sample used by the 4 rows) and writes them
+//     with coalesced 16-byte stores.
+// The ring of filtered rows repeats its first M slots after its end, so the
+// J_v rows of a row group are always linear in shared memory.  Every wait is
+// bounded (2 s); a timeout sets the plan's error word and stops the CTA.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rs_fused.cuh"
+
+namespace rs {
+namespace stream {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRB = 32; // input rows per staged block (one per lane of a horizontal task)
+constexpr int kG = 4;   // outputs per horizontal band group
+constexpr int kGV = 4;  // output rows per vertical band group
+constexpr int kMaxNI = 4;
+
+struct Params {
+    const float *in;
+    float *out;
+    int64_t in_h, in_w, out_h, out_w;
+    int64_t in_stride, out_stride;
+    const int32_t *hbase; // [groups_x] first input pixel of each horizontal group (multiple of 4)
+    const float *hband;   // [groups_x][JH][4] weights of the group's 4 outputs per input pixel
+    const int32_t *vbase; // [pairs] first input row of each group of 4 output rows ("pair" below)
+    const float *vband;   // [pairs][JV][8] per tap: each of the group's 4 row weights twice
+    int32_t JH, JV;       // horizontal taps (multiple of 4), vertical taps (multiple of 2)
+    int32_t SW;           // output pixels per strip (multiple of 4)
+    int32_t n_strips, pairs, pairs_per_range, groups_x;
+    int32_t P;            // staged input pitch in samples (P / 4 odd)
+    int32_t Q;            // filtered-row pitch in floats (Q / 4 odd)
+    int32_t NI;           // staged input blocks (ring slots)
+    int32_t HR, M;        // filtered-row ring rows, mirrored rows
+    int32_t WP;           // most row groups that become ready after one block
+    int *err;
+};
+
+constexpr int kMaxBlk = 512; // staged blocks per CTA (row range) at most
+
+// Shared memory: NI slots of (staged input block | the vertical weights and
+// row bases of the pairs that block completes) | filtered-row ring |
+// horizontal band | group offsets | per-block pair ends | barriers.
+struct Layout {
+    size_t in_blk, wv, vb, slot, hring, hb, cb, pe, total;
+};
+
+__host__ __device__ inline Layout layout(int NI, int P, int HR, int M, int Q, int ngx, int JH, int WP, int JV)
+{
+    Layout L;
+    L.in_blk = size_t(kRB) * P * 4;
+    L.wv = size_t(WP) * JV * 32;
+    L.vb = fused::align_up(size_t(WP + 8) * 4, 16);
+    L.slot = fused::align_up(L.in_blk + L.wv + L.vb, 128);
+    L.hring = fused::align_up(size_t(HR + M) * Q * 4, 128);
+    L.hb = fused::align_up(size_t(ngx) * JH * kG * 4, 128);
+    L.cb = fused::align_up(size_t(ngx) * 4, 128);
+    L.pe = fused::align_up(size_t(kMaxBlk) * 4, 128);
+    L.total = 128 + size_t(NI) * L.slot + L.hring + L.hb + L.cb + L.pe + 128;
+    return L;
+}
+
+template <int C>
+__global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (fused::smem_addr(smem_raw) & 127u)) & 127u);
+    const int ngx = p.SW / kG;
+    const int JH = p.JH, JV = p.JV, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, WP = p.WP;
+    const Layout L = layout(NI, P, HR, M, Q, ngx, JH, WP, JV);
+    unsigned char *slots = smem;
+    float *hring = reinterpret_cast<float *>(smem + NI * L.slot);
+    float *hb = reinterpret_cast<float *>(smem + NI * L.slot + L.hring);
+    int32_t *cb = reinterpret_cast<int32_t *>(smem + NI * L.slot + L.hring + L.hb);
+    int32_t *pe_s = reinterpret_cast<int32_t *>(smem + NI * L.slot + L.hring + L.hb + L.cb);
+    unsigned char *ctl = smem + NI * L.slot + L.hring + L.hb + L.cb + L.pe;
+    uint64_t *full = reinterpret_cast<uint64_t *>(ctl); // [kMaxNI]
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(ctl + 8 * kMaxNI);
+    auto slot_in = [&](int s) { return reinterpret_cast<float *>(slots + s * L.slot); };
+    auto slot_wv = [&](int s) { return reinterpret_cast<const ulonglong2 *>(slots + s * L.slot + L.in_blk); };
+    auto slot_vb = [&](int s) { return reinterpret_cast<const int32_t *>(slots + s * L.slot + L.in_blk + L.wv); };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int strip = int(blockIdx.x) % p.n_strips, range = int(blockIdx.x) / p.n_strips;
+    const int p0 = range * p.pairs_per_range;
+    const int p1 = min(p.pairs, p0 + p.pairs_per_range);
+    if (p0 >= p1) return;
+    const int g0 = strip * ngx;
+    const int ngv = min(ngx, p.groups_x - g0); // groups of the strip inside the image
+    const int xs = __ldg(p.hbase + g0) * C;    // first staged sample (multiple of 4)
+    const int r_lo = __ldg(p.vbase + p0);
+    const int r_hi = __ldg(p.vbase + p1 - 1) + JV;
+    const int nblk = min((r_hi - r_lo + kRB - 1) / kRB, kMaxBlk);
+    const uint32_t blk_bytes = uint32_t(L.in_blk);
+
+    if (tid == 0) {
+        for (int s = 0; s < NI; ++s) fused::mbar_init(&full[s], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the strip's horizontal band and group offsets (groups past the image: zeros)
+    for (int e = tid; e < ngx * JH * kG; e += kThreads) {
+        const int q = e / (JH * kG);
+        hb[e] = q < ngv ? __ldg(p.hband + size_t(g0) * JH * kG + e) : 0.f;
+    }
+    for (int q = tid; q < ngx; q += kThreads) cb[q] = q < ngv ? __ldg(p.hbase + g0 + q) * C - xs : 0;
+    // pair p is complete after block kb(p) (its last row is filtered then);
+    // pe_s[k] = first pair not complete after block k
+    auto kb = [&](int vb) {
+        const int k = (vb + JV - r_lo + kRB - 1) / kRB - 1;
+        return k < 0 ? 0 : (k > nblk - 1 ? nblk - 1 : k);
+    };
+    for (int q = p0 + tid; q < p1; q += kThreads) {
+        const int kp = kb(__ldg(p.vbase + q));
+        const int kn = q + 1 < p1 ? kb(__ldg(p.vbase + q + 1)) : nblk;
+        for (int k = kp; k < kn; ++k) pe_s[k] = q + 1;
+        if (q == p0)
+            for (int k = 0; k < kp; ++k) pe_s[k] = p0;
+    }
+    __syncthreads();
+
+    // thread 0: block k's input rows plus the weights and bases of its pairs
+    auto issue = [&](int k) {
+        const int s = k % NI;
+        const int ps = k ? pe_s[k - 1] : p0, pe = pe_s[k];
+        int n = pe - ps;
+        if (n > WP) {
+            fused::flag(p.err, fused::kErrBounds);
+            n = 0;
+        }
+        const int pa = ps & ~3, pb = (pe + 3) & ~3;
+        const uint32_t wbytes = uint32_t(n) * JV * 32, vbytes = n ? uint32_t(pb - pa) * 4 : 0u;
+        fused::mbar_arrive_expect_tx(&full[s], blk_bytes + wbytes + vbytes);
+        fused::tma_load_2d(slot_in(s), &tmap, &full[s], xs, r_lo + k * kRB);
+        if (n) {
+            fused::bulk_load(const_cast<ulonglong2 *>(slot_wv(s)), p.vband + size_t(ps) * JV * 8, wbytes, &full[s]);
+            fused::bulk_load(const_cast<int32_t *>(slot_vb(s)), p.vbase + pa, vbytes, &full[s]);
+        }
+    };
+    if (tid == 0)
+        for (int k = 0; k < NI && k < nblk; ++k) issue(k);
+
+    const int nch = (p.SW * C) / 4; // 4-sample chunks of a filtered row
+    const int64_t row_samples = p.out_w * C;
+    const int64_t x0s = int64_t(strip) * p.SW * C; // first output sample of the strip
+    int k = 0;
+    for (; k < nblk; ++k) {
+        const int slot = k % NI;
+        const bool landed = fused::wait_or_abort(&full[slot], uint32_t((k / NI) & 1), abort_flag, p.err);
+        const int base_k = (k * kRB) % HR; // ring slot of the block's first row
+        // ---------------- horizontal pass: 32 rows x the strip's groups ----------------
+        if (landed) {
+            int hs = base_k + lane;
+            if (hs >= HR) hs -= HR;
+            const float *rowp = slot_in(slot) + size_t(lane) * P;
+            for (int q = warp; q < ngv; q += kWarps) {
+                const float4 *src = reinterpret_cast<const float4 *>(rowp + cb[q]);
+                const float4 *wq = reinterpret_cast<const float4 *>(hb + q * JH * kG);
+                float acc[kG][C];
+#pragma unroll
+                for (int g = 0; g < kG; ++g)
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[g][c] = 0.f;
+                for (int t0 = 0; t0 < JH; t0 += 4) {
+                    // 4 input pixels of this lane's row (C 16-byte words) ...
+                    float d[4 * C];
+#pragma unroll
+                    for (int v = 0; v < C; ++v) {
+                        const float4 x = src[v];
+                        d[4 * v] = x.x;
+                        d[4 * v + 1] = x.y;
+                        d[4 * v + 2] = x.z;
+                        d[4 * v + 3] = x.w;
+                    }
+                    src += C;
+                    // ... times the 4 outputs' weights at those pixels (warp-uniform)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float4 w = wq[t];
+#pragma unroll
+                        for (int c = 0; c < C; ++c) {
+                            const float x = d[t * C + c];
+                            acc[0][c] = fmaf(w.x, x, acc[0][c]);
+                            acc[1][c] = fmaf(w.y, x, acc[1][c]);
+                            acc[2][c] = fmaf(w.z, x, acc[2][c]);
+                            acc[3][c] = fmaf(w.w, x, acc[3][c]);
+                        }
+                    }
+                    wq += 4;
+                }
+                // the group's 4 x C filtered samples, contiguous in the ring row
+                float4 o[C];
+                float *of = reinterpret_cast<float *>(o);
+#pragma unroll
+                for (int g = 0; g < kG; ++g)
+#pragma unroll
+                    for (int c = 0; c < C; ++c) of[g * C + c] = acc[g][c];
+                float4 *dst = reinterpret_cast<float4 *>(hring + size_t(hs) * Q + q * kG * C);
+#pragma unroll
+                for (int v = 0; v < C; ++v) dst[v] = o[v];
+                if (hs < M) {
+                    float4 *dm = reinterpret_cast<float4 *>(hring + size_t(hs + HR) * Q + q * kG * C);
+#pragma unroll
+                    for (int v = 0; v < C; ++v) dm[v] = o[v];
+                }
+            }
+        }
+        // every thread agrees on whether the block landed (a timeout stops all)
+        if (!__syncthreads_and(landed ? 1 : 0)) break;
+        // ---------------- vertical pass: completed pairs x 4-sample chunks ----------------
+        {
+            const int ps = k ? pe_s[k - 1] : p0, pe = pe_s[k];
+            const int n = pe - ps <= WP ? pe - ps : 0;
+            const ulonglong2 *wvs = slot_wv(slot);
+            const int32_t *vbs = slot_vb(slot) - (ps & ~3); // indexed by pair
+            const int ntask = n * nch;
+            int po = tid / nch, ch = tid - (tid / nch) * nch;
+            const int dpo = kThreads / nch, dch = kThreads - dpo * nch;
+            for (int t = tid; t < ntask; t += kThreads) {
+                const int pr = ps + po;
+                // first row of the pair: within (32k - JV, 32k + 32 - JV] of r_lo
+                int hs0 = base_k + (vbs[pr] - r_lo - k * kRB);
+                if (hs0 < 0) hs0 += HR;
+                if (hs0 >= HR) hs0 -= HR;
+                const float *src = hring + size_t(hs0) * Q + ch * 4;
+                const ulonglong2 *wv = wvs + po * JV * 2;
+                // 4 rows x 2 sample pairs of packed accumulators
+                uint64_t a[kGV][2];
+#pragma unroll
+                for (int r = 0; r < kGV; ++r) a[r][0] = a[r][1] = 0ull;
+#pragma unroll 2
+                for (int j = 0; j < JV; ++j) {
+                    const ulonglong2 dd = *reinterpret_cast<const ulonglong2 *>(src);
+                    const ulonglong2 w01 = wv[2 * j], w23 = wv[2 * j + 1];
+                    const uint64_t w[kGV] = {w01.x, w01.y, w23.x, w23.y};
+#pragma unroll
+                    for (int r = 0; r < kGV; ++r) {
+                        a[r][0] = fused::fma2(w[r], dd.x, a[r][0]);
+                        a[r][1] = fused::fma2(w[r], dd.y, a[r][1]);
+                    }
+                    src += Q;
+                }
+                const int64_t sx = x0s + int64_t(ch) * 4;
+#pragma unroll
+                for (int h = 0; h < kGV; ++h) {
+                    const int64_t y = int64_t(kGV) * pr + h;
+                    if (y >= p.out_h || sx >= row_samples) continue;
+                    float4 v;
+                    fused::unpack2(a[h][0], v.x, v.y);
+                    fused::unpack2(a[h][1], v.z, v.w);
+                    float *o = p.out + y * p.out_stride + sx;
+                    if (sx + 4 <= row_samples && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+                        *reinterpret_cast<float4 *>(o) = v;
+                    } else {
+                        const float e[4] = {v.x, v.y, v.z, v.w};
+                        for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[i] = e[i];
+                    }
+                }
+                po += dpo;
+                ch += dch;
+                if (ch >= nch) {
+                    ch -= nch;
+                    ++po;
+                }
+            }
+        }
+        __syncthreads();
+        // the slot is consumed (input by the horizontal pass, weights by the
+        // vertical pass): refill it with block k + NI
+        if (tid == 0 && k + NI < nblk) issue(k + NI);
+    }
+    // On a timeout, let the copies still in flight (blocks k .. k + NI - 1)
+    // land (bounded) before the CTA's shared memory is released.
+    if (k < nblk && tid == 0) {
+        for (int b = k; b < nblk && b < k + NI; ++b) fused::mbar_wait_bounded(&full[b % NI], uint32_t((b / NI) & 1));
+    }
+}
+
+} // namespace stream
+} // namespace rs

@@ -234,14 +234,13 @@ __global__ void __launch_bounds__(kThreadsW) weights_kernel(WeightArgs a0, Weigh
     if (nb > 0) axis_block(A, o0, nb, jlo_s, cnt_s, slot_s, val_s, sum_s, start_s);
 }
 
-// Band element e of group grp of one axis.  Layout:
-// band_w[grp * JS + (j * G + r) * dup + d], JS = band_stride(G * dup, J).
-template <typename W>
-__device__ void band_element(const WeightArgs &A, int64_t grp, int e)
+// Base of band group grp (the smallest window start of its members, kept
+// inside the axis) and whether the members' windows fit J inputs from it.
+__device__ int64_t band_group_base(const WeightArgs &A, int64_t grp, bool *fits)
 {
     const AxisGeom &g = A.g;
     const AxisTables &T = A.t;
-    const int G = T.G, J = T.J, te = g.t_eff, dup = T.dup;
+    const int G = T.G, J = T.J, te = g.t_eff;
     int64_t b0 = g.n_in, hi = 0;
     for (int r = 0; r < G; ++r) {
         const int64_t i = grp * G + r;
@@ -251,26 +250,71 @@ __device__ void band_element(const WeightArgs &A, int64_t grp, int e)
         hi = s + te > hi ? s + te : hi;
     }
     const int64_t b = g.n_in >= J ? (b0 < g.n_in - J ? b0 : g.n_in - J) : 0;
-    const bool fits = (hi - b) <= J;
-    if (e == 0) {
-        T.band_base[grp] = int32_t(b);
-        if (!fits) flag_error(A.err, kErrBand);
+    *fits = (hi - b) <= J;
+    return b;
+}
+
+// Weight of member r of group grp at band input j (0 outside its window).
+template <typename W>
+__device__ W band_weight(const WeightArgs &A, int64_t grp, int64_t b, bool fits, int j, int r)
+{
+    const AxisGeom &g = A.g;
+    const AxisTables &T = A.t;
+    const int64_t i = grp * T.G + r;
+    if (j >= T.J || i >= g.n_out || !fits) return W(0);
+    const int64_t off = T.start[i] - b;
+    if (j >= off && j < off + g.t_eff) return static_cast<const W *>(T.wwork)[i * g.t_eff + (j - off)];
+    return W(0);
+}
+
+// Band element e of slot `slot` of one axis (layouts in rs_internal.h):
+// band_w[slot * JS + (j * G + r) * dup + d] with d a duplicate, or with
+// pairing band_w[slot * JS + (j * G + r) * 2 + d] with d the group of the pair.
+template <typename W>
+__device__ void band_element(const WeightArgs &A, int64_t slot, int e)
+{
+    const AxisTables &T = A.t;
+    const int G = T.G, JS = band_slot_stride(T);
+    int64_t grp;
+    int idx;
+    bool real = true;
+    if (T.pair_ngx > 0) {
+        const int ppt = (T.pair_ngx + 1) / 2;
+        const int64_t tile = slot / ppt;
+        const int pq = int(slot % ppt), d = e & 1;
+        const int local = 2 * pq + d;
+        grp = tile * T.pair_ngx + local;
+        real = local < T.pair_ngx && grp < T.groups;
+        idx = e >> 1;
+        if (real && e == d) {
+            bool fits;
+            const int64_t b = band_group_base(A, grp, &fits);
+            T.band_base[grp] = int32_t(b);
+            if (!fits) flag_error(A.err, kErrBand);
+        }
+    } else {
+        grp = slot;
+        idx = e / T.dup;
+        if (e == 0) {
+            bool fits;
+            const int64_t b = band_group_base(A, grp, &fits);
+            T.band_base[grp] = int32_t(b);
+            if (!fits) flag_error(A.err, kErrBand);
+        }
     }
     W v = W(0);
-    const int idx = e / dup;
-    const int j = idx / G, r = idx % G;
-    const int64_t i = grp * G + r;
-    if (j < J && i < g.n_out && fits) {
-        const int64_t off = T.start[i] - b;
-        if (j >= off && j < off + te) v = static_cast<const W *>(T.wwork)[i * te + (j - off)];
+    if (real) {
+        bool fits;
+        const int64_t b = band_group_base(A, grp, &fits);
+        v = band_weight<W>(A, grp, b, fits, idx / G, idx % G);
     }
-    static_cast<W *>(T.band_w)[grp * band_stride(G * dup, J) + e] = v;
+    static_cast<W *>(T.band_w)[slot * JS + e] = v;
 }
 
 __global__ void band_kernel(WeightArgs a0, WeightArgs a1)
 {
-    const int64_t js0 = band_stride(a0.t.G * a0.t.dup, a0.t.J), js1 = band_stride(a1.t.G * a1.t.dup, a1.t.J);
-    const int64_t n0 = int64_t(a0.t.groups) * js0, n1 = int64_t(a1.t.groups) * js1;
+    const int64_t js0 = band_slot_stride(a0.t), js1 = band_slot_stride(a1.t);
+    const int64_t n0 = band_slots(a0.t) * js0, n1 = band_slots(a1.t) * js1;
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n0 + n1;
          t += int64_t(gridDim.x) * blockDim.x) {
         const bool first = t < n0;
@@ -309,8 +353,7 @@ cudaError_t launch_weights(const WeightArgs &a0, const WeightArgs &a1, cudaStrea
 
 cudaError_t launch_band(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s)
 {
-    const int64_t n = int64_t(a0.t.groups) * band_stride(a0.t.G * a0.t.dup, a0.t.J) +
-                      int64_t(a1.t.groups) * band_stride(a1.t.G * a1.t.dup, a1.t.J);
+    const int64_t n = band_slots(a0.t) * band_slot_stride(a0.t) + band_slots(a1.t) * band_slot_stride(a1.t);
     const int threads = 256;
     int64_t blocks = (n + threads - 1) / threads;
     if (blocks > 148 * 16) blocks = 148 * 16;

@@ -77,7 +77,7 @@ def test_batch_matches_oracle_and_single_path(rs, dt, C, aligned):
         # alone, through the plan path (on the SIMT kernel, as batches), with the same pitch
         d = rs.make_desc(sp["in_h"], sp["in_w"], C, got.shape[0], got.shape[1], kernel=sp["kernel"],
                          param=sp["param"], boundary=sp["boundary"], dtype=ins[i].dtype,
-                         in_row_stride=pitches[i], flags=rs.RS_FORCE_SIMT)
+                         in_row_stride=pitches[i], flags=rs.RS_FORCE_SIMT | rs.RS_NO_STREAM)
         h = rs.rs_plan_create(d, 0)
         alone = torch.empty_like(outs[i])
         rs.rs_resample(h, ins[i].data_ptr(), alone.data_ptr(), 0)

@@ -121,7 +121,7 @@ def test_server_results_match_oracle_and_alone(rs):
         assert np.abs(got.double().cpu().numpy() - want).max() <= TOL[dt], (tk, key, scale)
         # the server runs the SIMT kernel: compare with a plan kept off the tensor cores
         desc = rs.make_desc(key[0], key[0], C, st.out_h, st.out_w, kernel=kern, param=par, boundary="mirror",
-                            dtype=tdts[dt], in_row_stride=pitch, flags=rs.RS_FORCE_SIMT)
+                            dtype=tdts[dt], in_row_stride=pitch, flags=rs.RS_FORCE_SIMT | rs.RS_NO_STREAM)
         alone = _alone(rs, desc, buf.data_ptr(), (st.out_h, st.out_w, C), tdts[dt])
         assert torch.equal(alone, got), (tk, key, scale)
         rs.rs_server_release(srv, tk)
