@@ -41,10 +41,28 @@ __global__ void hband_kernel(AxisGeom g, const int32_t *start, const float *w, i
     }
 }
 
-const void *kernel_for(int C)
+// Instantiated kernels: channels x vertical taps (a plan's band is padded
+// with zero weights to the next instantiated width).
+constexpr int kJV[] = {4, 6, 8, 10, 12, 14, 16};
+
+template <int C> const void *kernel_jv(int jv)
 {
-    if (C == 1) return reinterpret_cast<const void *>(&stream_kernel<1>);
-    if (C == 3) return reinterpret_cast<const void *>(&stream_kernel<3>);
+    switch (jv) {
+    case 4: return reinterpret_cast<const void *>(&stream_kernel<C, 4>);
+    case 6: return reinterpret_cast<const void *>(&stream_kernel<C, 6>);
+    case 8: return reinterpret_cast<const void *>(&stream_kernel<C, 8>);
+    case 10: return reinterpret_cast<const void *>(&stream_kernel<C, 10>);
+    case 12: return reinterpret_cast<const void *>(&stream_kernel<C, 12>);
+    case 14: return reinterpret_cast<const void *>(&stream_kernel<C, 14>);
+    case 16: return reinterpret_cast<const void *>(&stream_kernel<C, 16>);
+    }
+    return nullptr;
+}
+
+const void *kernel_for(int C, int jv)
+{
+    if (C == 1) return kernel_jv<1>(jv);
+    if (C == 3) return kernel_jv<3>(jv);
     return nullptr;
 }
 
@@ -90,8 +108,16 @@ rs_status setup(rs_plan *p, cudaStream_t s)
         }
         JV = std::max(JV, hi - lo);
     }
-    JV = (JV + 1) / 2 * 2;
-    if (JH > 16 || JV > 64 || JV > gy.n_in) return RS_ERR_UNSUPPORTED;
+    {
+        int jv = 0;
+        for (int c : kJV)
+            if (c >= JV) {
+                jv = c;
+                break;
+            }
+        JV = jv;
+    }
+    if (JH > 16 || JV == 0 || JV > gy.n_in) return RS_ERR_UNSUPPORTED;
     // row bases of the groups (as the band kernel computes them) and the most
     // groups whose last row falls in one 32-row block
     const int pairs = int((gy.n_out + kGV - 1) / kGV);
@@ -121,9 +147,9 @@ rs_status setup(rs_plan *p, cudaStream_t s)
         }
         const int pp = pad_pitch(need);
         if (pp > 256) continue;
-        const int qq = pad_pitch(sw * C);
+        const int qq = (HR + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
         for (int ni = kMaxNI; ni >= 3; --ni) {
-            const size_t t = layout(ni, pp, HR, M, qq, ngx, JH, WP, JV).total;
+            const size_t t = layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV).total;
             if (t <= 113 * 1024) {
                 SW = sw;
                 P = pp;
@@ -136,7 +162,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     }
     if (SW == 0) return RS_ERR_UNSUPPORTED;
     const int ngx = SW / kG;
-    const void *fn = kernel_for(C);
+    const void *fn = kernel_for(C, JV);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "setting shared memory size");
     int occ = 0;
@@ -171,7 +197,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     const size_t o_hb = cv.take(size_t(groups_x) * 4);
     const size_t o_hw = cv.take(size_t(groups_x) * JH * kG * 4);
     const size_t o_vb = cv.take(size_t((pairs + 3) & ~3) * 4); // the kernel copies whole 16-byte words
-    const size_t o_vw = cv.take(size_t(pairs) * JV * 8 * 4);
+    const size_t o_vw = cv.take(size_t(pairs) * JV * kGV * 2 * 4);
     if (p->sbufs.p) {
         cudaFree(p->sbufs.p);
         p->sbufs.p = nullptr;

@@ -11,9 +11,9 @@
 //     outputs; the band's start is 4-pixel aligned, so chunks load as 16-byte
 //     words) and appends the results to a ring of horizontally filtered rows;
 //   * the vertical pass turns every group of 4 output rows whose taps are all
-//     in that ring into its rows (lanes along 4-sample chunks of the strip,
+//     in that ring into its rows (lanes along 4-sample columns of the strip,
 //     packed FP32 FMAs, each loaded sample used by the 4 rows) and writes them
-//     with coalesced 16-byte stores.
+//     with 16-byte stores.
 // The ring of filtered rows repeats its first M slots after its end, so the
 // J_v rows of a row group are always linear in shared memory.  Every wait is
 // bounded (2 s); a timeout sets the plan's error word and stops the CTA.
@@ -48,7 +48,7 @@ struct Params {
     int32_t SW;           // output pixels per strip (multiple of 4)
     int32_t n_strips, pairs, pairs_per_range, groups_x;
     int32_t P;            // staged input pitch in samples (P / 4 odd)
-    int32_t Q;            // filtered-row pitch in floats (Q / 4 odd)
+    int32_t Q;            // rows per 4-sample column of the filtered-row ring (>= HR + M, odd)
     int32_t NI;           // staged input blocks (ring slots)
     int32_t HR, M;        // filtered-row ring rows, mirrored rows
     int32_t WP;           // most row groups that become ready after one block
@@ -64,14 +64,14 @@ struct Layout {
     size_t in_blk, wv, vb, slot, hring, hb, cb, pe, total;
 };
 
-__host__ __device__ inline Layout layout(int NI, int P, int HR, int M, int Q, int ngx, int JH, int WP, int JV)
+__host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx, int JH, int WP, int JV)
 {
     Layout L;
     L.in_blk = size_t(kRB) * P * 4;
-    L.wv = size_t(WP) * JV * 32;
+    L.wv = size_t(WP) * JV * kGV * 8;
     L.vb = fused::align_up(size_t(WP + 8) * 4, 16);
     L.slot = fused::align_up(L.in_blk + L.wv + L.vb, 128);
-    L.hring = fused::align_up(size_t(HR + M) * Q * 4, 128);
+    L.hring = fused::align_up(size_t(nch) * Q * 16, 128);
     L.hb = fused::align_up(size_t(ngx) * JH * kG * 4, 128);
     L.cb = fused::align_up(size_t(ngx) * 4, 128);
     L.pe = fused::align_up(size_t(kMaxBlk) * 4, 128);
@@ -79,16 +79,19 @@ __host__ __device__ inline Layout layout(int NI, int P, int HR, int M, int Q, in
     return L;
 }
 
-template <int C>
+template <int C, int JV>
 __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (fused::smem_addr(smem_raw) & 127u)) & 127u);
     const int ngx = p.SW / kG;
-    const int JH = p.JH, JV = p.JV, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, WP = p.WP;
-    const Layout L = layout(NI, P, HR, M, Q, ngx, JH, WP, JV);
+    const int JH = p.JH, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, WP = p.WP;
+    const int nch = (p.SW * C) / 4; // 4-sample columns of a filtered row
+    const Layout L = layout(NI, P, Q, nch, ngx, JH, WP, JV);
     unsigned char *slots = smem;
-    float *hring = reinterpret_cast<float *>(smem + NI * L.slot);
+    // filtered rows, column-major in 4-sample columns: [nch][Q] float4, so the
+    // vertical taps of a column are consecutive 16-byte words
+    float4 *hring = reinterpret_cast<float4 *>(smem + NI * L.slot);
     float *hb = reinterpret_cast<float *>(smem + NI * L.slot + L.hring);
     int32_t *cb = reinterpret_cast<int32_t *>(smem + NI * L.slot + L.hring + L.hb);
     int32_t *pe_s = reinterpret_cast<int32_t *>(smem + NI * L.slot + L.hring + L.hb + L.cb);
@@ -148,20 +151,22 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
             n = 0;
         }
         const int pa = ps & ~3, pb = (pe + 3) & ~3;
-        const uint32_t wbytes = uint32_t(n) * JV * 32, vbytes = n ? uint32_t(pb - pa) * 4 : 0u;
+        const uint32_t wbytes = uint32_t(n) * JV * kGV * 8, vbytes = n ? uint32_t(pb - pa) * 4 : 0u;
         fused::mbar_arrive_expect_tx(&full[s], blk_bytes + wbytes + vbytes);
         fused::tma_load_2d(slot_in(s), &tmap, &full[s], xs, r_lo + k * kRB);
         if (n) {
-            fused::bulk_load(const_cast<ulonglong2 *>(slot_wv(s)), p.vband + size_t(ps) * JV * 8, wbytes, &full[s]);
+            fused::bulk_load(const_cast<ulonglong2 *>(slot_wv(s)), p.vband + size_t(ps) * JV * kGV * 2, wbytes,
+                             &full[s]);
             fused::bulk_load(const_cast<int32_t *>(slot_vb(s)), p.vbase + pa, vbytes, &full[s]);
         }
     };
     if (tid == 0)
         for (int k = 0; k < NI && k < nblk; ++k) issue(k);
 
-    const int nch = (p.SW * C) / 4; // 4-sample chunks of a filtered row
     const int64_t row_samples = p.out_w * C;
     const int64_t x0s = int64_t(strip) * p.SW * C; // first output sample of the strip
+    // 16-byte stores need a 16-byte aligned output and row pitch (chunks are 4 samples)
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(p.out) | uintptr_t(p.out_stride * 4)) & 15u) == 0;
     int k = 0;
     for (; k < nblk; ++k) {
         const int slot = k % NI;
@@ -214,13 +219,12 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
                 for (int g = 0; g < kG; ++g)
 #pragma unroll
                     for (int c = 0; c < C; ++c) of[g * C + c] = acc[g][c];
-                float4 *dst = reinterpret_cast<float4 *>(hring + size_t(hs) * Q + q * kG * C);
+                float4 *dst = hring + (q * C) * Q + hs;
 #pragma unroll
-                for (int v = 0; v < C; ++v) dst[v] = o[v];
+                for (int v = 0; v < C; ++v) dst[v * Q] = o[v];
                 if (hs < M) {
-                    float4 *dm = reinterpret_cast<float4 *>(hring + size_t(hs + HR) * Q + q * kG * C);
 #pragma unroll
-                    for (int v = 0; v < C; ++v) dm[v] = o[v];
+                    for (int v = 0; v < C; ++v) dst[v * Q + HR] = o[v];
                 }
             }
         }
@@ -237,42 +241,48 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
             const int dpo = kThreads / nch, dch = kThreads - dpo * nch;
             for (int t = tid; t < ntask; t += kThreads) {
                 const int pr = ps + po;
-                // first row of the pair: within (32k - JV, 32k + 32 - JV] of r_lo
+                // first row of the group: within (32k - JV, 32k + 32 - JV] of r_lo
                 int hs0 = base_k + (vbs[pr] - r_lo - k * kRB);
                 if (hs0 < 0) hs0 += HR;
                 if (hs0 >= HR) hs0 -= HR;
-                const float *src = hring + size_t(hs0) * Q + ch * 4;
-                const ulonglong2 *wv = wvs + po * JV * 2;
+                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(hring + ch * Q + hs0);
+                const ulonglong2 *wv = wvs + po * JV * (kGV / 2);
                 // 4 rows x 2 sample pairs of packed accumulators
                 uint64_t a[kGV][2];
 #pragma unroll
                 for (int r = 0; r < kGV; ++r) a[r][0] = a[r][1] = 0ull;
-#pragma unroll 2
-                for (int j = 0; j < JV; ++j) {
-                    const ulonglong2 dd = *reinterpret_cast<const ulonglong2 *>(src);
-                    const ulonglong2 w01 = wv[2 * j], w23 = wv[2 * j + 1];
-                    const uint64_t w[kGV] = {w01.x, w01.y, w23.x, w23.y};
 #pragma unroll
-                    for (int r = 0; r < kGV; ++r) {
-                        a[r][0] = fused::fma2(w[r], dd.x, a[r][0]);
-                        a[r][1] = fused::fma2(w[r], dd.y, a[r][1]);
+                for (int j = 0; j < JV; ++j) {
+                    const ulonglong2 dd = src[j];
+#pragma unroll
+                    for (int r2 = 0; r2 < kGV / 2; ++r2) {
+                        const ulonglong2 w = wv[(kGV / 2) * j + r2]; // rows 2 r2, 2 r2 + 1 (each twice)
+                        a[2 * r2][0] = fused::fma2(w.x, dd.x, a[2 * r2][0]);
+                        a[2 * r2][1] = fused::fma2(w.x, dd.y, a[2 * r2][1]);
+                        a[2 * r2 + 1][0] = fused::fma2(w.y, dd.x, a[2 * r2 + 1][0]);
+                        a[2 * r2 + 1][1] = fused::fma2(w.y, dd.y, a[2 * r2 + 1][1]);
                     }
-                    src += Q;
                 }
                 const int64_t sx = x0s + int64_t(ch) * 4;
+                const int64_t y0 = int64_t(kGV) * pr;
+                float *o = p.out + y0 * p.out_stride + sx;
+                if (y0 + kGV <= p.out_h && sx + 4 <= row_samples && vec_ok) {
+                    // whole rows of 4 samples: 16-byte stores
 #pragma unroll
-                for (int h = 0; h < kGV; ++h) {
-                    const int64_t y = int64_t(kGV) * pr + h;
-                    if (y >= p.out_h || sx >= row_samples) continue;
-                    float4 v;
-                    fused::unpack2(a[h][0], v.x, v.y);
-                    fused::unpack2(a[h][1], v.z, v.w);
-                    float *o = p.out + y * p.out_stride + sx;
-                    if (sx + 4 <= row_samples && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
-                        *reinterpret_cast<float4 *>(o) = v;
-                    } else {
-                        const float e[4] = {v.x, v.y, v.z, v.w};
-                        for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[i] = e[i];
+                    for (int h = 0; h < kGV; ++h) {
+                        float4 v;
+                        fused::unpack2(a[h][0], v.x, v.y);
+                        fused::unpack2(a[h][1], v.z, v.w);
+                        *reinterpret_cast<float4 *>(o + h * p.out_stride) = v;
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < kGV; ++h) {
+                        if (y0 + h >= p.out_h) break;
+                        float e[4];
+                        fused::unpack2(a[h][0], e[0], e[1]);
+                        fused::unpack2(a[h][1], e[2], e[3]);
+                        for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[h * p.out_stride + i] = e[i];
                     }
                 }
                 po += dpo;
