@@ -278,6 +278,7 @@ rs_status apply_fused(rs_plan *p, cudaStream_t stream, const Candidate &c, bool 
     p->tx.band_w = base + o_wx;
     e = launch_band(weight_args(p, 0), weight_args(p, 1), stream);
     if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
+    p->tile_bands_stale = 0;
     std::vector<int32_t> by(p->ty.groups), bx(p->tx.groups);
     e = cudaMemcpyAsync(by.data(), p->ty.band_base, by.size() * 4, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
@@ -877,6 +878,11 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
         if (p->chosen.tc && !fp.use_tma)
             return fail(RS_ERR_INVALID_ARG, "tensor-core plan: the input must be 16-byte aligned");
         if (p->use_stream && fp.use_tma) return stream::launch(p, d_in, d_out, stream);
+        if (p->tile_bands_stale) {
+            e = launch_band(weight_args(p, 0), weight_args(p, 1), stream);
+            if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
+            p->tile_bands_stale = 0;
+        }
         size_t smem = p->smem;
         if (fp.use_tma) {
             rs_status s = encode_map(p, d_in);
@@ -1006,8 +1012,14 @@ rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
     if (!p) return fail(RS_ERR_INVALID_ARG, "NULL plan");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     cudaError_t e = launch_weights(weight_args(p, 0), weight_args(p, 1), stream);
-    if (e == cudaSuccess && p->path == 0) e = launch_band(weight_args(p, 0), weight_args(p, 1), stream);
     if (e != cudaSuccess) return cuda_fail(e, "weight kernel launch");
+    if (p->path == 0 && p->use_stream) {
+        // the tile kernel's bands are rebuilt only if a tile launch needs them
+        p->tile_bands_stale = 1;
+        return stream::rebuild(p, stream);
+    }
+    if (p->path == 0) e = launch_band(weight_args(p, 0), weight_args(p, 1), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
     if (p->stream_ok) return stream::rebuild(p, stream);
     return RS_OK;
 }

@@ -54,6 +54,10 @@ struct AxisTables {
     void *band_w = nullptr;       // [band_slots][band_slot_stride] working precision
     int32_t G = 0, J = 0, groups = 0, dup = 1;
     int32_t pair_ngx = 0;
+    // align > 1: group bases are the members' smallest start rounded down to a
+    // multiple of align, not kept inside the axis (the row-streaming kernel's
+    // horizontal band; its staged copy reads zeros past the input's end)
+    int32_t align = 0;
 };
 
 // Floats per band group: J * G rounded up to a multiple of 4, so that every

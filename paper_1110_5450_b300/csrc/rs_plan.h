@@ -69,6 +69,7 @@ struct rs_plan {
     std::vector<int32_t> host_start_y, host_start_x; // for re-planning and tuning
     rs::Candidate chosen;                            // fused configuration in use
     // row-streaming kernel (FP32 upscales and mild downscales)
+    int tile_bands_stale = 0; // recomputed weights not yet in the tile kernel's bands
     int stream_ok = 0;  // a streaming configuration exists
     int use_stream = 0; // rs_resample runs it (else the tile kernel above)
     rs::stream::Params sp{};

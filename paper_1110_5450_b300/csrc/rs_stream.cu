@@ -13,34 +13,6 @@ namespace rs {
 namespace stream {
 namespace {
 
-// Horizontal band of groups of 4 outputs with a 4-pixel aligned start:
-// hbase[q] = (smallest window start of the group) rounded down to a multiple
-// of 4, hband[q][j][g] = weight of output 4q + g at input hbase[q] + j.  The
-// window may run past the input's end (the staged copy reads zeros there).
-__global__ void hband_kernel(AxisGeom g, const int32_t *start, const float *w, int32_t *hbase, float *hband,
-                             int groups, int JH)
-{
-    const int64_t n = int64_t(groups) * JH * kG;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t q = e / (JH * kG);
-        const int j = int((e / kG) % JH), r = int(e % kG);
-        int64_t lo = g.n_in;
-        for (int m = 0; m < kG; ++m) {
-            const int64_t i = q * kG + m;
-            if (i < g.n_out) lo = min(lo, int64_t(start[i]));
-        }
-        const int64_t b = lo & ~int64_t(3);
-        if (j == 0 && r == 0) hbase[q] = int32_t(b);
-        const int64_t i = q * kG + r;
-        float v = 0.f;
-        if (i < g.n_out) {
-            const int64_t off = start[i] - b;
-            if (j >= off && j < off + g.t_eff) v = w[i * g.t_eff + (j - off)];
-        }
-        hband[e] = v;
-    }
-}
-
 // Instantiated kernels: channels x vertical taps (a plan's band is padded
 // with zero weights to the next instantiated width).
 constexpr int kJV[] = {4, 6, 8, 10, 12, 14, 16};
@@ -246,32 +218,37 @@ rs_status setup(rs_plan *p, cudaStream_t s)
 
 rs_status rebuild(rs_plan *p, cudaStream_t s)
 {
+    // both bands in one launch of the band kernel:
+    //  * vertical: groups of 4 rows, every weight twice -> per tap (w0, w0, .., w3, w3);
+    //  * horizontal: groups of 4 outputs, 4-pixel aligned bases, per pixel (w0, .., w3)
     const Params &sp = p->sp;
-    const int64_t n = int64_t(sp.groups_x) * sp.JH * kG;
-    const int blocks = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
-    hband_kernel<<<std::max(1, blocks), 256, 0, s>>>(p->gx, p->tx.start, static_cast<const float *>(p->tx.wwork),
-                                                     const_cast<int32_t *>(sp.hbase), const_cast<float *>(sp.hband),
-                                                     sp.groups_x, sp.JH);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "horizontal band launch");
-    // vertical band: groups of 4 rows, every weight twice -> per tap (w0, w0, .., w3, w3)
     AxisTables vt = p->ty;
     vt.G = kGV;
     vt.J = sp.JV;
     vt.groups = sp.pairs;
     vt.dup = 2;
     vt.pair_ngx = 0;
+    vt.align = 0;
     vt.band_base = const_cast<int32_t *>(sp.vbase);
     vt.band_w = const_cast<float *>(sp.vband);
-    WeightArgs a0;
+    AxisTables ht = p->tx;
+    ht.G = kG;
+    ht.J = sp.JH;
+    ht.groups = sp.groups_x;
+    ht.dup = 1;
+    ht.pair_ngx = 0;
+    ht.align = 4;
+    ht.band_base = const_cast<int32_t *>(sp.hbase);
+    ht.band_w = const_cast<float *>(sp.hband);
+    WeightArgs a0, a1;
     a0.g = p->gy;
     a0.t = vt;
-    a0.work_is_double = 0;
-    a0.err = p->d_err;
-    WeightArgs a1 = a0;
-    a1.t.groups = 0; // second axis unused
-    e = launch_band(a0, a1, s);
-    if (e != cudaSuccess) return cuda_fail(e, "vertical band launch");
+    a1.g = p->gx;
+    a1.t = ht;
+    a0.work_is_double = a1.work_is_double = 0;
+    a0.err = a1.err = p->d_err;
+    const cudaError_t e = launch_band(a0, a1, s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream band launch");
     return RS_OK;
 }
 

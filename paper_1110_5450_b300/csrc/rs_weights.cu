@@ -249,7 +249,7 @@ __device__ int64_t band_group_base(const WeightArgs &A, int64_t grp, bool *fits)
         b0 = s < b0 ? s : b0;
         hi = s + te > hi ? s + te : hi;
     }
-    const int64_t b = g.n_in >= J ? (b0 < g.n_in - J ? b0 : g.n_in - J) : 0;
+    const int64_t b = T.align > 1 ? b0 - b0 % T.align : (g.n_in >= J ? (b0 < g.n_in - J ? b0 : g.n_in - J) : 0);
     *fits = (hi - b) <= J;
     return b;
 }
