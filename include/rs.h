@@ -113,15 +113,15 @@ typedef enum {
 #define RS_TWO_PASS 0x08u     /* separate H-then-V kernels through an HBM buffer  */
 #define RS_CHECK 0x10u        /* device bounds checks that set an error word      */
 #define RS_NO_STREAM 0x20u    /* never pick the row-streaming kernel              */
-#define RS_FORCE_STREAM 0x40u /* pick the row-streaming kernel (FP32, 1 or 3 channels,
-                                 horizontal band <= 16 taps); RS_ERR_UNSUPPORTED where
-                                 it cannot apply                                  */
+#define RS_FORCE_STREAM 0x40u /* pick the row-streaming kernel (FP32, 1 or 3 channels;
+                                 bands of 4 outputs of at most 40 / 32 inputs across /
+                                 down); RS_ERR_UNSUPPORTED where it cannot apply  */
 /* The row-streaming kernel runs the horizontal pass first on staged input rows
  * and the vertical pass on a ring of filtered rows, with deep TMA prefetch and
  * coalesced output rows.  It is chosen for FP32 plans of 1 or 3 channels whose
- * horizontal band (groups of 4 outputs) needs at most 16 input pixels, with a
- * 16-byte row pitch; an input pointer that is not 16-byte aligned at
- * rs_resample falls back to the tile kernel of the same plan. */
+ * bands of 4 outputs need at most 40 input pixels across and 32 input rows
+ * down, with a 16-byte row pitch; an input pointer that is not 16-byte aligned
+ * at rs_resample falls back to the tile kernel of the same plan. */
 
 /* Plan descriptor.  Sizes are in samples/elements, not bytes. */
 typedef struct {

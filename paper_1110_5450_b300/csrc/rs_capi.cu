@@ -125,6 +125,10 @@ int64_t derive_out(int32_t given, int64_t n, double scale)
     return std::max<int64_t>(1, int64_t(v));
 }
 
+// Weight-table launch for both axes; when the axes are identical the column
+// tables alias the row tables and only the rows are computed.
+cudaError_t launch_plan_weights(rs_plan *p, cudaStream_t s);
+
 WeightArgs weight_args(rs_plan *p, int axis)
 {
     WeightArgs a;
@@ -133,6 +137,13 @@ WeightArgs weight_args(rs_plan *p, int axis)
     a.work_is_double = p->work_double;
     a.err = p->d_err;
     return a;
+}
+
+cudaError_t launch_plan_weights(rs_plan *p, cudaStream_t s)
+{
+    WeightArgs a1 = weight_args(p, 1);
+    if (p->axes_alias) a1.g.n_out = 0; // the column tables are the row tables
+    return launch_weights(weight_args(p, 0), a1, s);
 }
 
 // Largest band span (max start - min start within a group) + t_eff.
@@ -770,11 +781,18 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     p->work_double = d.in_dtype == RS_F64 ? 1 : 0;
     const size_t wsz = p->work_double ? 8 : 4;
 
-    // weight tables of both axes and the error word, one allocation
+    // weight tables of both axes and the error word, one allocation; identical
+    // axes (same sizes, kernel, boundary) share one set of tables
+    const AxisGeom &ga = p->gy, &gb = p->gx;
+    p->axes_alias = (ga.n_in == gb.n_in && ga.n_out == gb.n_out && ga.D == gb.D && ga.R == gb.R &&
+                     ga.t_raw == gb.t_raw && ga.t_eff == gb.t_eff && ga.kernel == gb.kernel &&
+                     ga.boundary == gb.boundary && ga.param == gb.param)
+                        ? 1
+                        : 0;
     Carver cv;
     const size_t o_err = cv.take(16);
     size_t o[2][5];
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < 2 - p->axes_alias; ++a) {
         const AxisGeom &g = a == 0 ? p->gy : p->gx;
         o[a][0] = cv.take(size_t(g.n_out) * 4);
         o[a][1] = cv.take(size_t(g.n_out) * 4);
@@ -792,14 +810,15 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     p->d_err = reinterpret_cast<int *>(base + o_err);
     for (int a = 0; a < 2; ++a) {
         AxisTables &t = a == 0 ? p->ty : p->tx;
-        t.jlo = reinterpret_cast<int32_t *>(base + o[a][0]);
-        t.cnt = reinterpret_cast<int32_t *>(base + o[a][1]);
-        t.start = reinterpret_cast<int32_t *>(base + o[a][2]);
-        t.w64 = reinterpret_cast<double *>(base + o[a][3]);
-        t.wwork = base + o[a][4];
+        const int b = p->axes_alias ? 0 : a;
+        t.jlo = reinterpret_cast<int32_t *>(base + o[b][0]);
+        t.cnt = reinterpret_cast<int32_t *>(base + o[b][1]);
+        t.start = reinterpret_cast<int32_t *>(base + o[b][2]);
+        t.w64 = reinterpret_cast<double *>(base + o[b][3]);
+        t.wwork = base + o[b][4];
     }
     e = cudaMemsetAsync(p->d_err, 0, 16, stream);
-    if (e == cudaSuccess) e = launch_weights(weight_args(p, 0), weight_args(p, 1), stream);
+    if (e == cudaSuccess) e = launch_plan_weights(p, stream);
     if (e != cudaSuccess) {
         delete p;
         return cuda_fail(e, "weight kernel launch");
@@ -832,8 +851,8 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     }
     if ((d.flags & RS_FORCE_STREAM) && !p->stream_ok) {
         delete p;
-        return fail(RS_ERR_UNSUPPORTED, "row-streaming kernel needs FP32, 1 or 3 channels, a 16-byte row pitch "
-                                        "and a horizontal band of at most 16 input pixels");
+        return fail(RS_ERR_UNSUPPORTED, "row-streaming kernel needs FP32, 1 or 3 channels, a 16-byte row pitch, "
+                                        "a horizontal band of at most 40 and a vertical band of at most 32 inputs");
     }
     if (st != RS_OK) {
         p->path = 1;
@@ -1011,7 +1030,7 @@ rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
 {
     if (!p) return fail(RS_ERR_INVALID_ARG, "NULL plan");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-    cudaError_t e = launch_weights(weight_args(p, 0), weight_args(p, 1), stream);
+    cudaError_t e = launch_plan_weights(p, stream);
     if (e != cudaSuccess) return cuda_fail(e, "weight kernel launch");
     if (p->path == 0 && p->use_stream) {
         // the tile kernel's bands are rebuilt only if a tile launch needs them

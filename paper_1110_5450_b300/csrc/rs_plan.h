@@ -51,6 +51,7 @@ struct rs_plan {
     rs::AxisGeom gy, gx;
     rs::AxisTables ty, tx;
     int work_double = 0;
+    int axes_alias = 0; // identical axes: the column tables are the row tables
     int path = 1; // 0 fused, 1 two-pass
     rs::DeviceBuf tables, bands, tmp, errbuf;
     int *d_err = nullptr;

@@ -15,7 +15,7 @@ namespace {
 
 // Instantiated kernels: channels x vertical taps (a plan's band is padded
 // with zero weights to the next instantiated width).
-constexpr int kJV[] = {4, 6, 8, 10, 12, 14, 16};
+constexpr int kJV[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
 
 template <int C> const void *kernel_jv(int jv)
 {
@@ -27,6 +27,10 @@ template <int C> const void *kernel_jv(int jv)
     case 12: return reinterpret_cast<const void *>(&stream_kernel<C, 12>);
     case 14: return reinterpret_cast<const void *>(&stream_kernel<C, 14>);
     case 16: return reinterpret_cast<const void *>(&stream_kernel<C, 16>);
+    case 20: return reinterpret_cast<const void *>(&stream_kernel<C, 20>);
+    case 24: return reinterpret_cast<const void *>(&stream_kernel<C, 24>);
+    case 28: return reinterpret_cast<const void *>(&stream_kernel<C, 28>);
+    case 32: return reinterpret_cast<const void *>(&stream_kernel<C, 32>);
     }
     return nullptr;
 }
@@ -89,7 +93,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
             }
         JV = jv;
     }
-    if (JH > 16 || JV == 0 || JV > gy.n_in) return RS_ERR_UNSUPPORTED;
+    if (JH > 40 || JV == 0 || JV > gy.n_in) return RS_ERR_UNSUPPORTED;
     // row bases of the groups (as the band kernel computes them) and the most
     // groups whose last row falls in one 32-row block
     const int pairs = int((gy.n_out + kGV - 1) / kGV);
@@ -108,8 +112,13 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     // the widest strip (multiple of 4 outputs, at most 128) whose staged width
     // fits one TMA box and whose CTA (3 staged blocks) keeps two CTAs per SM
     const int HR = kRB + JV, M = JV - 1;
-    int SW = 0, P = 0, Q = 0, NI = 0;
+    int SW = 0, P = 0, offB = 0, Q = 0, NI = 0;
     size_t smem = 0;
+    // narrow strips (one box per block, three staged blocks) where one fits;
+    // else wide strips (two boxes per block: the second starts early enough
+    // that every group's band fits one of them)
+    // (passes: narrow with >= 3 staged blocks, wide, narrow with 2 blocks)
+    for (int pass = 0; pass < 3 && SW == 0; ++pass)
     for (int sw = 128; sw >= 16 && SW == 0; sw -= 4) {
         const int ngx = sw / kG;
         int need = 0;
@@ -117,14 +126,29 @@ rs_status setup(rs_plan *p, cudaStream_t s)
             const int gl = std::min(groups_x, g0 + ngx) - 1;
             need = std::max(need, (hb[gl] + JH - hb[g0]) * C);
         }
-        const int pp = pad_pitch(need);
-        if (pp > 256) continue;
+        int pp = 0, ob = 0;
+        if (pass != 1) {
+            pp = pad_pitch(need);
+            if (pp > 256) pp = 0;
+        } else {
+            // boxes A = [0, P) and B = [ob, ob + P) of the strip's samples:
+            // ob <= P - JH C (overlap of a band) and ob + P >= need
+            for (int cand = pad_pitch((need + JH * C + 1) / 2); cand <= 256 && !pp; cand += 8) {
+                const int o = (cand - JH * C) / 4 * 4;
+                if (o > 0 && o + cand >= need) {
+                    pp = cand;
+                    ob = o;
+                }
+            }
+        }
+        if (pp == 0) continue;
         const int qq = (HR + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
-        for (int ni = kMaxNI; ni >= 3; --ni) {
-            const size_t t = layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV).total;
-            if (t <= 113 * 1024) {
+        for (int ni = kMaxNI; ni >= 2; --ni) {
+            const size_t t = layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0).total;
+            if (t <= 113 * 1024 && (ni >= 3 || pass > 0)) {
                 SW = sw;
                 P = pp;
+                offB = ob;
                 Q = qq;
                 NI = ni;
                 smem = t;
@@ -198,6 +222,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     sp.pairs_per_range = ppr;
     sp.groups_x = groups_x;
     sp.P = P;
+    sp.offB = offB;
     sp.Q = Q;
     sp.NI = NI;
     sp.HR = HR;

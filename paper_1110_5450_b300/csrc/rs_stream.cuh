@@ -48,6 +48,9 @@ struct Params {
     int32_t SW;           // output pixels per strip (multiple of 4)
     int32_t n_strips, pairs, pairs_per_range, groups_x;
     int32_t P;            // staged input pitch in samples (P / 4 odd)
+    int32_t offB;         // 0: one staged box of P x 32 samples per block; else a second box
+                          //    P x 32 starting offB samples further (rows wider than one
+                          //    256-element box), in its own 128-byte aligned sub-buffer
     int32_t Q;            // rows per 4-sample column of the filtered-row ring (>= HR + M, odd)
     int32_t NI;           // staged input blocks (ring slots)
     int32_t HR, M;        // filtered-row ring rows, mirrored rows
@@ -64,10 +67,11 @@ struct Layout {
     size_t in_blk, wv, vb, slot, hring, hb, cb, pe, total;
 };
 
-__host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx, int JH, int WP, int JV)
+__host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx, int JH, int WP, int JV,
+                                         bool two_boxes)
 {
     Layout L;
-    L.in_blk = size_t(kRB) * P * 4;
+    L.in_blk = size_t(kRB) * P * 4 * (two_boxes ? 2 : 1);
     L.wv = size_t(WP) * JV * kGV * 8;
     L.vb = fused::align_up(size_t(WP + 8) * 4, 16);
     L.slot = fused::align_up(L.in_blk + L.wv + L.vb, 128);
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     const int ngx = p.SW / kG;
     const int JH = p.JH, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, WP = p.WP;
     const int nch = (p.SW * C) / 4; // 4-sample columns of a filtered row
-    const Layout L = layout(NI, P, Q, nch, ngx, JH, WP, JV);
+    const Layout L = layout(NI, P, Q, nch, ngx, JH, WP, JV, p.offB != 0);
     unsigned char *slots = smem;
     // filtered rows, column-major in 4-sample columns: [nch][Q] float4, so the
     // vertical taps of a column are consecutive 16-byte words
@@ -125,7 +129,13 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
         const int q = e / (JH * kG);
         hb[e] = q < ngv ? __ldg(p.hband + size_t(g0) * JH * kG + e) : 0.f;
     }
-    for (int q = tid; q < ngx; q += kThreads) cb[q] = q < ngv ? __ldg(p.hbase + g0 + q) * C - xs : 0;
+    // per group: offset of its band window in the staged block (the second
+    // box's sub-buffer when the window does not fit the first box)
+    for (int q = tid; q < ngx; q += kThreads) {
+        int o = q < ngv ? __ldg(p.hbase + g0 + q) * C - xs : 0;
+        if (p.offB && o + JH * C > P) o += kRB * P - p.offB;
+        cb[q] = o;
+    }
     // pair p is complete after block kb(p) (its last row is filtered then);
     // pe_s[k] = first pair not complete after block k
     auto kb = [&](int vb) {
@@ -154,6 +164,8 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
         const uint32_t wbytes = uint32_t(n) * JV * kGV * 8, vbytes = n ? uint32_t(pb - pa) * 4 : 0u;
         fused::mbar_arrive_expect_tx(&full[s], blk_bytes + wbytes + vbytes);
         fused::tma_load_2d(slot_in(s), &tmap, &full[s], xs, r_lo + k * kRB);
+        if (p.offB) // second box: its own sub-buffer right after the first (128-byte aligned)
+            fused::tma_load_2d(slot_in(s) + kRB * P, &tmap, &full[s], xs + p.offB, r_lo + k * kRB);
         if (n) {
             fused::bulk_load(const_cast<ulonglong2 *>(slot_wv(s)), p.vband + size_t(ps) * JV * kGV * 2, wbytes,
                              &full[s]);

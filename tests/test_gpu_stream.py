@@ -34,7 +34,9 @@ SHAPES = [((67, 92), (150, 203)),     # x2.2, ragged strips
           ((64, 100), (50, 77)),      # mild downscale (~x0.78)
           ((40, 400), (90, 999)),     # wide, many strips
           ((200, 20), (401, 37)),     # tall, one strip
-          ((32, 32), (5, 3)) ]         # tiny output
+          ((32, 32), (5, 3)),         # tiny output
+          ((300, 400), (90, 120)),    # x0.3: wide strips (two boxes per staged row)
+          ((257, 611), (77, 183))]    # ~x0.3, ragged
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=[f"{a[0]}x{a[1]}-{b[0]}x{b[1]}" for a, b in SHAPES])
@@ -147,6 +149,20 @@ def test_stream_full_size_sampled_rows(rs):
     err = 0.0
     for r in rows:
         want = oracle.resample(exact, 5612, 5612, "lanczos", "mirror", param=3.0, rows=(r, r + 1))
+        err = max(err, float(np.abs(got[r] - want[0]).max()))
+    assert err <= TOL["f32"], err
+
+
+def test_stream_full_size_x03_sampled_rows(rs):
+    """4096x4096x3 x0.3 (antialiased, 20 taps) on the streaming kernel's wide strips."""
+    t, exact = quantise(synth.sinusoids(4096, 4096, 3, seed=synth.SEED_C2), "f32")
+    got, info = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_STREAM, scale=0.3)
+    assert info.path == 3 and (info.out_h, info.out_w) == (1229, 1229)
+    g = np.random.default_rng(5)
+    rows = sorted(set([0, 1, 614, 1227, 1228]) | set(int(r) for r in g.integers(0, 1229, 8)))
+    err = 0.0
+    for r in rows:
+        want = oracle.resample(exact, 1229, 1229, "lanczos", "mirror", param=3.0, rows=(r, r + 1))
         err = max(err, float(np.abs(got[r] - want[0]).max()))
     assert err <= TOL["f32"], err
 
