@@ -546,9 +546,17 @@ def main():
     # launch; both bands of a streaming plan) and the resample
     launches_per_step = 3 * len(plans)
 
+    side = torch.cuda.Stream()
+
     def step():
+        # the plans' tables are independent: both at once on two streams,
+        # then the resamples (each fills the GPU) one after the other
+        side.wait_stream(stream)
+        for p in plans[1:]:
+            p.recompute(side)
+        plans[0].recompute(stream)
+        stream.wait_stream(side)
         for p, y in zip(plans, ys):
-            p.recompute(stream)
             p(x, out=y, stream=stream)
 
     for _ in range(2):

@@ -1067,7 +1067,7 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
         info->path = 3;
         info->tile_h = stream::kRB;
         info->tile_w = p->sp.SW;
-        info->group_h = stream::kGV;
+        info->group_h = p->sp.GV;
         info->group_w = stream::kG;
         info->span_h = p->sp.JV;
         info->span_w = p->sp.JH;

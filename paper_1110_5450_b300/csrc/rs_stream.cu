@@ -13,33 +13,58 @@ namespace rs {
 namespace stream {
 namespace {
 
-// Instantiated kernels: channels x vertical taps (a plan's band is padded
-// with zero weights to the next instantiated width).
-constexpr int kJV[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
+// Instantiated kernels: channels x vertical taps x rows per vertical group (a
+// plan's band is padded with zero weights to the next instantiated width):
+// groups of 8 rows up to 16 taps, groups of 4 rows up to 32.
+constexpr int kJV8[] = {8, 10, 12, 14, 16};
+constexpr int kJV4[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
 
-template <int C> const void *kernel_jv(int jv)
+template <int C, int GV> const void *kernel_jv(int jv)
 {
     switch (jv) {
-    case 4: return reinterpret_cast<const void *>(&stream_kernel<C, 4>);
-    case 6: return reinterpret_cast<const void *>(&stream_kernel<C, 6>);
-    case 8: return reinterpret_cast<const void *>(&stream_kernel<C, 8>);
-    case 10: return reinterpret_cast<const void *>(&stream_kernel<C, 10>);
-    case 12: return reinterpret_cast<const void *>(&stream_kernel<C, 12>);
-    case 14: return reinterpret_cast<const void *>(&stream_kernel<C, 14>);
-    case 16: return reinterpret_cast<const void *>(&stream_kernel<C, 16>);
-    case 20: return reinterpret_cast<const void *>(&stream_kernel<C, 20>);
-    case 24: return reinterpret_cast<const void *>(&stream_kernel<C, 24>);
-    case 28: return reinterpret_cast<const void *>(&stream_kernel<C, 28>);
-    case 32: return reinterpret_cast<const void *>(&stream_kernel<C, 32>);
+    case 4: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 4, 4>) : nullptr;
+    case 6: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 6, 4>) : nullptr;
+    case 8: return reinterpret_cast<const void *>(&stream_kernel<C, 8, GV>);
+    case 10: return reinterpret_cast<const void *>(&stream_kernel<C, 10, GV>);
+    case 12: return reinterpret_cast<const void *>(&stream_kernel<C, 12, GV>);
+    case 14: return reinterpret_cast<const void *>(&stream_kernel<C, 14, GV>);
+    case 16: return reinterpret_cast<const void *>(&stream_kernel<C, 16, GV>);
+    case 20: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 20, 4>) : nullptr;
+    case 24: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 24, 4>) : nullptr;
+    case 28: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 28, 4>) : nullptr;
+    case 32: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 32, 4>) : nullptr;
     }
     return nullptr;
 }
 
-const void *kernel_for(int C, int jv)
+const void *kernel_for(int C, int jv, int gv)
 {
-    if (C == 1) return kernel_jv<1>(jv);
-    if (C == 3) return kernel_jv<3>(jv);
+    if (C == 1) return gv == 8 ? kernel_jv<1, 8>(jv) : kernel_jv<1, 4>(jv);
+    if (C == 3) return gv == 8 ? kernel_jv<3, 8>(jv) : kernel_jv<3, 4>(jv);
     return nullptr;
+}
+
+// Vertical taps of groups of GV output rows, rounded up to an instantiated
+// width (0 if none is wide enough).
+int vertical_taps(const std::vector<int32_t> &sy, int t_eff, int GV)
+{
+    int J = 0;
+    for (size_t i = 0; i < sy.size(); i += GV) {
+        int lo = sy[i], hi = sy[i] + t_eff;
+        for (size_t r = 1; r < size_t(GV) && i + r < sy.size(); ++r) {
+            lo = std::min(lo, int(sy[i + r]));
+            hi = std::max(hi, int(sy[i + r]) + t_eff);
+        }
+        J = std::max(J, hi - lo);
+    }
+    if (GV == 8) {
+        for (int c : kJV8)
+            if (c >= J) return c;
+    } else {
+        for (int c : kJV4)
+            if (c >= J) return c;
+    }
+    return 0;
 }
 
 int pad_pitch(int n) // multiple of 4 with n / 4 odd, >= n
@@ -74,33 +99,21 @@ rs_status setup(rs_plan *p, cudaStream_t s)
         JH = std::max(JH, hi - hb[q]);
     }
     JH = (JH + 3) / 4 * 4;
-    // vertical band of groups of 4 output rows (the tile kernel's band code, G = 4)
-    int JV = 0;
-    for (size_t i = 0; i < sy.size(); i += kGV) {
-        int lo = sy[i], hi = sy[i] + gy.t_eff;
-        for (size_t r = 1; r < size_t(kGV) && i + r < sy.size(); ++r) {
-            lo = std::min(lo, int(sy[i + r]));
-            hi = std::max(hi, int(sy[i + r]) + gy.t_eff);
-        }
-        JV = std::max(JV, hi - lo);
-    }
-    {
-        int jv = 0;
-        for (int c : kJV)
-            if (c >= JV) {
-                jv = c;
-                break;
-            }
-        JV = jv;
+    // vertical band (the tile kernel's band code): groups of 8 rows while the
+    // band stays within 16 taps, else groups of 4
+    int GV = 8, JV = vertical_taps(sy, gy.t_eff, 8);
+    if (JV == 0) {
+        GV = 4;
+        JV = vertical_taps(sy, gy.t_eff, 4);
     }
     if (JH > 40 || JV == 0 || JV > gy.n_in) return RS_ERR_UNSUPPORTED;
     // row bases of the groups (as the band kernel computes them) and the most
     // groups whose last row falls in one 32-row block
-    const int pairs = int((gy.n_out + kGV - 1) / kGV);
+    const int pairs = int((gy.n_out + GV - 1) / GV);
     std::vector<int32_t> vb(pairs);
     for (int q = 0; q < pairs; ++q) {
-        int lo = sy[kGV * q];
-        for (int r = 1; r < kGV && kGV * q + r < int(sy.size()); ++r) lo = std::min(lo, int(sy[kGV * q + r]));
+        int lo = sy[GV * q];
+        for (int r = 1; r < GV && GV * q + r < int(sy.size()); ++r) lo = std::min(lo, int(sy[GV * q + r]));
         vb[q] = gy.n_in >= JV ? std::min<int64_t>(lo, gy.n_in - JV) : 0;
     }
     int WP = 0;
@@ -144,7 +157,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
         if (pp == 0) continue;
         const int qq = (HR + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
         for (int ni = kMaxNI; ni >= 2; --ni) {
-            const size_t t = layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0).total;
+            const size_t t = layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total;
             if (t <= 113 * 1024 && (ni >= 3 || pass > 0)) {
                 SW = sw;
                 P = pp;
@@ -158,7 +171,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     }
     if (SW == 0) return RS_ERR_UNSUPPORTED;
     const int ngx = SW / kG;
-    const void *fn = kernel_for(C, JV);
+    const void *fn = kernel_for(C, JV, GV);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "setting shared memory size");
     int occ = 0;
@@ -193,7 +206,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     const size_t o_hb = cv.take(size_t(groups_x) * 4);
     const size_t o_hw = cv.take(size_t(groups_x) * JH * kG * 4);
     const size_t o_vb = cv.take(size_t((pairs + 3) & ~3) * 4); // the kernel copies whole 16-byte words
-    const size_t o_vw = cv.take(size_t(pairs) * JV * kGV * 2 * 4);
+    const size_t o_vw = cv.take(size_t(pairs) * JV * vtap_floats(GV) * 4);
     if (p->sbufs.p) {
         cudaFree(p->sbufs.p);
         p->sbufs.p = nullptr;
@@ -228,6 +241,7 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     sp.HR = HR;
     sp.M = M;
     sp.WP = WP;
+    sp.GV = GV;
     sp.err = p->d_err;
     rs_status st = rebuild(p, s);
     if (st != RS_OK) return st;
@@ -248,10 +262,10 @@ rs_status rebuild(rs_plan *p, cudaStream_t s)
     //  * horizontal: groups of 4 outputs, 4-pixel aligned bases, per pixel (w0, .., w3)
     const Params &sp = p->sp;
     AxisTables vt = p->ty;
-    vt.G = kGV;
+    vt.G = sp.GV;
     vt.J = sp.JV;
     vt.groups = sp.pairs;
-    vt.dup = 2;
+    vt.dup = sp.GV == 4 ? 2 : 1; // groups of 4 rows: every weight twice (packed FMAs)
     vt.pair_ngx = 0;
     vt.align = 0;
     vt.band_base = const_cast<int32_t *>(sp.vbase);

@@ -32,7 +32,12 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRB = 32; // input rows per staged block (one per lane of a horizontal task)
 constexpr int kG = 4;   // outputs per horizontal band group
-constexpr int kGV = 4;  // output rows per vertical band group
+// Output rows per vertical band group: 8 (scalar FMAs, each loaded sample
+// feeds 8 rows) where the band stays narrow, else 4 (packed FMAs on pairs of
+// samples with every weight stored twice).
+constexpr int kGV8 = 8, kGV4 = 4;
+// floats per vertical tap of a group in the band
+__host__ __device__ constexpr int vtap_floats(int GV) { return GV == 4 ? 8 : GV; }
 constexpr int kMaxNI = 4;
 
 struct Params {
@@ -42,8 +47,8 @@ struct Params {
     int64_t in_stride, out_stride;
     const int32_t *hbase; // [groups_x] first input pixel of each horizontal group (multiple of 4)
     const float *hband;   // [groups_x][JH][4] weights of the group's 4 outputs per input pixel
-    const int32_t *vbase; // [pairs] first input row of each group of 4 output rows ("pair" below)
-    const float *vband;   // [pairs][JV][8] per tap: each of the group's 4 row weights twice
+    const int32_t *vbase; // [pairs] first input row of each group of 8 output rows ("pair" below)
+    const float *vband;   // [pairs][JV][8] per tap: the weights of the group's 8 rows
     int32_t JH, JV;       // horizontal taps (multiple of 4), vertical taps (multiple of 2)
     int32_t SW;           // output pixels per strip (multiple of 4)
     int32_t n_strips, pairs, pairs_per_range, groups_x;
@@ -55,6 +60,7 @@ struct Params {
     int32_t NI;           // staged input blocks (ring slots)
     int32_t HR, M;        // filtered-row ring rows, mirrored rows
     int32_t WP;           // most row groups that become ready after one block
+    int32_t GV;           // rows per vertical group (the kernel's template argument)
     int *err;
 };
 
@@ -68,11 +74,11 @@ struct Layout {
 };
 
 __host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx, int JH, int WP, int JV,
-                                         bool two_boxes)
+                                         bool two_boxes, int GV)
 {
     Layout L;
     L.in_blk = size_t(kRB) * P * 4 * (two_boxes ? 2 : 1);
-    L.wv = size_t(WP) * JV * kGV * 8;
+    L.wv = size_t(WP) * JV * vtap_floats(GV) * 4;
     L.vb = fused::align_up(size_t(WP + 8) * 4, 16);
     L.slot = fused::align_up(L.in_blk + L.wv + L.vb, 128);
     L.hring = fused::align_up(size_t(nch) * Q * 16, 128);
@@ -83,7 +89,7 @@ __host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx,
     return L;
 }
 
-template <int C, int JV>
+template <int C, int JV, int GV>
 __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -91,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     const int ngx = p.SW / kG;
     const int JH = p.JH, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, WP = p.WP;
     const int nch = (p.SW * C) / 4; // 4-sample columns of a filtered row
-    const Layout L = layout(NI, P, Q, nch, ngx, JH, WP, JV, p.offB != 0);
+    const Layout L = layout(NI, P, Q, nch, ngx, JH, WP, JV, p.offB != 0, GV);
     unsigned char *slots = smem;
     // filtered rows, column-major in 4-sample columns: [nch][Q] float4, so the
     // vertical taps of a column are consecutive 16-byte words
@@ -161,13 +167,13 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
             n = 0;
         }
         const int pa = ps & ~3, pb = (pe + 3) & ~3;
-        const uint32_t wbytes = uint32_t(n) * JV * kGV * 8, vbytes = n ? uint32_t(pb - pa) * 4 : 0u;
+        const uint32_t wbytes = uint32_t(n) * JV * vtap_floats(GV) * 4, vbytes = n ? uint32_t(pb - pa) * 4 : 0u;
         fused::mbar_arrive_expect_tx(&full[s], blk_bytes + wbytes + vbytes);
         fused::tma_load_2d(slot_in(s), &tmap, &full[s], xs, r_lo + k * kRB);
         if (p.offB) // second box: its own sub-buffer right after the first (128-byte aligned)
             fused::tma_load_2d(slot_in(s) + kRB * P, &tmap, &full[s], xs + p.offB, r_lo + k * kRB);
         if (n) {
-            fused::bulk_load(const_cast<ulonglong2 *>(slot_wv(s)), p.vband + size_t(ps) * JV * kGV * 2, wbytes,
+            fused::bulk_load(const_cast<ulonglong2 *>(slot_wv(s)), p.vband + size_t(ps) * JV * vtap_floats(GV), wbytes,
                              &full[s]);
             fused::bulk_load(const_cast<int32_t *>(slot_vb(s)), p.vbase + pa, vbytes, &full[s]);
         }
@@ -257,44 +263,72 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
                 int hs0 = base_k + (vbs[pr] - r_lo - k * kRB);
                 if (hs0 < 0) hs0 += HR;
                 if (hs0 >= HR) hs0 -= HR;
-                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(hring + ch * Q + hs0);
-                const ulonglong2 *wv = wvs + po * JV * (kGV / 2);
-                // 4 rows x 2 sample pairs of packed accumulators
-                uint64_t a[kGV][2];
+                const float4 *src4 = hring + ch * Q + hs0;
+                const float4 *wv = reinterpret_cast<const float4 *>(wvs) + po * JV * (vtap_floats(GV) / 4);
+                float a[GV][4];
+                if constexpr (GV == 4) {
+                    // 4 rows x 2 sample pairs of packed accumulators; the band
+                    // stores every weight twice, so pairs load as they are
+                    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(src4);
+                    const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(wv);
+                    uint64_t acc[GV][2];
 #pragma unroll
-                for (int r = 0; r < kGV; ++r) a[r][0] = a[r][1] = 0ull;
+                    for (int r = 0; r < GV; ++r) acc[r][0] = acc[r][1] = 0ull;
 #pragma unroll
-                for (int j = 0; j < JV; ++j) {
-                    const ulonglong2 dd = src[j];
+                    for (int j = 0; j < JV; ++j) {
+                        const ulonglong2 dd = src[j];
 #pragma unroll
-                    for (int r2 = 0; r2 < kGV / 2; ++r2) {
-                        const ulonglong2 w = wv[(kGV / 2) * j + r2]; // rows 2 r2, 2 r2 + 1 (each twice)
-                        a[2 * r2][0] = fused::fma2(w.x, dd.x, a[2 * r2][0]);
-                        a[2 * r2][1] = fused::fma2(w.x, dd.y, a[2 * r2][1]);
-                        a[2 * r2 + 1][0] = fused::fma2(w.y, dd.x, a[2 * r2 + 1][0]);
-                        a[2 * r2 + 1][1] = fused::fma2(w.y, dd.y, a[2 * r2 + 1][1]);
+                        for (int r2 = 0; r2 < GV / 2; ++r2) {
+                            const ulonglong2 w = w2[(GV / 2) * j + r2]; // rows 2 r2, 2 r2 + 1
+                            acc[2 * r2][0] = fused::fma2(w.x, dd.x, acc[2 * r2][0]);
+                            acc[2 * r2][1] = fused::fma2(w.x, dd.y, acc[2 * r2][1]);
+                            acc[2 * r2 + 1][0] = fused::fma2(w.y, dd.x, acc[2 * r2 + 1][0]);
+                            acc[2 * r2 + 1][1] = fused::fma2(w.y, dd.y, acc[2 * r2 + 1][1]);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < GV; ++r) {
+                        fused::unpack2(acc[r][0], a[r][0], a[r][1]);
+                        fused::unpack2(acc[r][1], a[r][2], a[r][3]);
+                    }
+                } else {
+                    // 8 rows x 4 samples; each loaded sample feeds the 8 rows
+#pragma unroll
+                    for (int r = 0; r < GV; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < JV; ++j) {
+                        const float4 d = src4[j];
+                        float w[GV];
+#pragma unroll
+                        for (int v = 0; v < GV / 4; ++v) {
+                            const float4 q = wv[(GV / 4) * j + v];
+                            w[4 * v] = q.x;
+                            w[4 * v + 1] = q.y;
+                            w[4 * v + 2] = q.z;
+                            w[4 * v + 3] = q.w;
+                        }
+#pragma unroll
+                        for (int r = 0; r < GV; ++r) {
+                            a[r][0] = fmaf(w[r], d.x, a[r][0]);
+                            a[r][1] = fmaf(w[r], d.y, a[r][1]);
+                            a[r][2] = fmaf(w[r], d.z, a[r][2]);
+                            a[r][3] = fmaf(w[r], d.w, a[r][3]);
+                        }
                     }
                 }
                 const int64_t sx = x0s + int64_t(ch) * 4;
-                const int64_t y0 = int64_t(kGV) * pr;
+                const int64_t y0 = int64_t(GV) * pr;
                 float *o = p.out + y0 * p.out_stride + sx;
-                if (y0 + kGV <= p.out_h && sx + 4 <= row_samples && vec_ok) {
+                if (y0 + GV <= p.out_h && sx + 4 <= row_samples && vec_ok) {
                     // whole rows of 4 samples: 16-byte stores
 #pragma unroll
-                    for (int h = 0; h < kGV; ++h) {
-                        float4 v;
-                        fused::unpack2(a[h][0], v.x, v.y);
-                        fused::unpack2(a[h][1], v.z, v.w);
-                        *reinterpret_cast<float4 *>(o + h * p.out_stride) = v;
-                    }
+                    for (int h = 0; h < GV; ++h)
+                        *reinterpret_cast<float4 *>(o + h * p.out_stride) = make_float4(a[h][0], a[h][1], a[h][2], a[h][3]);
                 } else {
 #pragma unroll
-                    for (int h = 0; h < kGV; ++h) {
+                    for (int h = 0; h < GV; ++h) {
                         if (y0 + h >= p.out_h) break;
-                        float e[4];
-                        fused::unpack2(a[h][0], e[0], e[1]);
-                        fused::unpack2(a[h][1], e[2], e[3]);
-                        for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[h * p.out_stride + i] = e[i];
+                        for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[h * p.out_stride + i] = a[h][i];
                     }
                 }
                 po += dpo;
