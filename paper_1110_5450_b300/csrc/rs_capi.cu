@@ -959,8 +959,14 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
                 Candidate k = c;
                 k.n1 = n1;
                 const rs_status s2 = apply_fused(p, stream, k, tma);
-                p->use_stream = (s2 == RS_OK && stream_ok && us_cached) ? 1 : 0;
-                return s2;
+                if (s2 != RS_OK) return s2;
+                if (stream_ok && us_cached) {
+                    // the cached streaming configuration
+                    const rs_status s3 = stream::setup(p, stream, stream::Opts::decode(us_cached));
+                    if (s3 != RS_OK && s3 != RS_ERR_UNSUPPORTED) return s3;
+                    p->use_stream = s3 == RS_OK ? 1 : 0;
+                }
+                return RS_OK;
             }
     }
     const Candidate before = p->chosen;
@@ -1011,18 +1017,45 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     }
     rs_status s = apply_fused(p, stream, best, tma);
     if (s != RS_OK) return s;
+    int stream_choice = 0;
     if (stream_ok) {
-        // tile winner against the streaming kernel
-        double us_tile = 0, us_stream = 0;
+        // tile winner against the streaming configurations
+        double us_tile = 0;
         s = time_plan(p, d_in, d_out, stream, &us_tile);
         if (s != RS_OK) return s;
-        p->use_stream = 1;
-        s = time_plan(p, d_in, d_out, stream, &us_stream);
-        if (s != RS_OK) return s;
-        p->use_stream = us_stream < us_tile ? 1 : 0;
-        best_us = std::min(us_tile, us_stream);
+        const int cands_s[][3] = {{0, 0, 3}, {0, 0, 2}, {1, 4, 3}, {1, 4, 2}, {1, 3, 3}, {1, 5, 3}, {1, 5, 2}};
+        double best_s = 1e300;
+        int best_code = 0;
+        for (const auto &c : cands_s) {
+            stream::Opts o;
+            o.ws = c[0];
+            o.hw = c[1];
+            o.ni_min = c[2];
+            const rs_status ss = stream::setup(p, stream, o);
+            if (ss == RS_ERR_UNSUPPORTED) continue;
+            if (ss != RS_OK) return ss;
+            p->use_stream = 1;
+            double us = 0;
+            s = time_plan(p, d_in, d_out, stream, &us);
+            if (s != RS_OK) return s;
+            if (us < best_s) {
+                best_s = us;
+                best_code = p->stream_code;
+            }
+        }
+        p->use_stream = 0;
+        if (best_code && (best_s < us_tile || (p->desc.flags & RS_FORCE_STREAM))) {
+            s = stream::setup(p, stream, stream::Opts::decode(best_code));
+            if (s != RS_OK) return s;
+            p->use_stream = 1;
+            stream_choice = best_code;
+        } else if (best_code) {
+            // keep a streaming configuration for an explicit switch back
+            stream::setup(p, stream, stream::Opts::decode(best_code));
+        }
+        best_us = std::min(us_tile, best_s);
     }
-    if (best_us < 1e299) cache_store(cache_path, key, best, best_us, p->use_stream);
+    if (best_us < 1e299) cache_store(cache_path, key, best, best_us, stream_choice);
     return RS_OK;
 }
 

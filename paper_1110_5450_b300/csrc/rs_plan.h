@@ -72,6 +72,7 @@ struct rs_plan {
     // row-streaming kernel (FP32 upscales and mild downscales)
     int tile_bands_stale = 0; // recomputed weights not yet in the tile kernel's bands
     int stream_ok = 0;  // a streaming configuration exists
+    int stream_code = 0; // its choices (stream::Opts::code)
     int use_stream = 0; // rs_resample runs it (else the tile kernel above)
     rs::stream::Params sp{};
     rs::DeviceBuf sbufs;
@@ -112,9 +113,24 @@ fused::Work single_work(const rs_plan *p, int use_tma);
 double model_cost(Candidate &c, int C, size_t esz, size_t asz, int V);
 
 namespace stream {
+// Choices of a streaming configuration: ws = 1 warp-specialised kernel, 0
+// phase-alternating, -1 either (warp-specialised first); hw = warps on the
+// horizontal pass (0: 4); ni_min = fewest staged input blocks of a narrow strip.
+struct Opts {
+    int ws = -1, hw = 0, ni_min = 3;
+    int code() const { return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min; }
+    static Opts decode(int c)
+    {
+        Opts o;
+        o.ws = (c & 2) ? 1 : 0;
+        o.hw = (c >> 2) & 15;
+        o.ni_min = (c >> 6) & 7;
+        return o;
+    }
+};
 // Configures the row-streaming kernel for a plan (needs the host start tables);
 // RS_ERR_UNSUPPORTED when the plan is not eligible.
-rs_status setup(rs_plan *p, cudaStream_t s);
+rs_status setup(rs_plan *p, cudaStream_t s, const Opts &o = Opts());
 // Rebuilds its band tables from the plan's weight tables (after a recompute).
 rs_status rebuild(rs_plan *p, cudaStream_t s);
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);

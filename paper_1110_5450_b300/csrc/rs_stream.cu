@@ -19,28 +19,34 @@ namespace {
 constexpr int kJV8[] = {8, 10, 12, 14, 16};
 constexpr int kJV4[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
 
-template <int C, int GV> const void *kernel_jv(int jv)
+template <int C, int JV, int GV> const void *kernel_of(bool ws)
+{
+    return ws ? reinterpret_cast<const void *>(&stream_ws_kernel<C, JV, GV>)
+              : reinterpret_cast<const void *>(&stream_kernel<C, JV, GV>);
+}
+
+template <int C, int GV> const void *kernel_jv(int jv, bool ws)
 {
     switch (jv) {
-    case 4: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 4, 4>) : nullptr;
-    case 6: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 6, 4>) : nullptr;
-    case 8: return reinterpret_cast<const void *>(&stream_kernel<C, 8, GV>);
-    case 10: return reinterpret_cast<const void *>(&stream_kernel<C, 10, GV>);
-    case 12: return reinterpret_cast<const void *>(&stream_kernel<C, 12, GV>);
-    case 14: return reinterpret_cast<const void *>(&stream_kernel<C, 14, GV>);
-    case 16: return reinterpret_cast<const void *>(&stream_kernel<C, 16, GV>);
-    case 20: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 20, 4>) : nullptr;
-    case 24: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 24, 4>) : nullptr;
-    case 28: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 28, 4>) : nullptr;
-    case 32: return GV == 4 ? reinterpret_cast<const void *>(&stream_kernel<C, 32, 4>) : nullptr;
+    case 4: return GV == 4 ? kernel_of<C, 4, 4>(ws) : nullptr;
+    case 6: return GV == 4 ? kernel_of<C, 6, 4>(ws) : nullptr;
+    case 8: return kernel_of<C, 8, GV>(ws);
+    case 10: return kernel_of<C, 10, GV>(ws);
+    case 12: return kernel_of<C, 12, GV>(ws);
+    case 14: return kernel_of<C, 14, GV>(ws);
+    case 16: return kernel_of<C, 16, GV>(ws);
+    case 20: return GV == 4 ? kernel_of<C, 20, 4>(ws) : nullptr;
+    case 24: return GV == 4 ? kernel_of<C, 24, 4>(ws) : nullptr;
+    case 28: return GV == 4 ? kernel_of<C, 28, 4>(ws) : nullptr;
+    case 32: return GV == 4 ? kernel_of<C, 32, 4>(ws) : nullptr;
     }
     return nullptr;
 }
 
-const void *kernel_for(int C, int jv, int gv)
+const void *kernel_for(int C, int jv, int gv, bool ws)
 {
-    if (C == 1) return gv == 8 ? kernel_jv<1, 8>(jv) : kernel_jv<1, 4>(jv);
-    if (C == 3) return gv == 8 ? kernel_jv<3, 8>(jv) : kernel_jv<3, 4>(jv);
+    if (C == 1) return gv == 8 ? kernel_jv<1, 8>(jv, ws) : kernel_jv<1, 4>(jv, ws);
+    if (C == 3) return gv == 8 ? kernel_jv<3, 8>(jv, ws) : kernel_jv<3, 4>(jv, ws);
     return nullptr;
 }
 
@@ -76,7 +82,7 @@ int pad_pitch(int n) // multiple of 4 with n / 4 odd, >= n
 
 } // namespace
 
-rs_status setup(rs_plan *p, cudaStream_t s)
+rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
 {
     p->stream_ok = 0;
     const rs_plan_desc &d = p->desc;
@@ -123,10 +129,13 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     }
     WP = std::max(WP, 1);
     // the widest strip (multiple of 4 outputs, at most 128) whose staged width
-    // fits one TMA box and whose CTA (3 staged blocks) keeps two CTAs per SM
-    const int HR = kRB + JV, M = JV - 1;
-    int SW = 0, P = 0, offB = 0, Q = 0, NI = 0;
+    // fits the TMA boxes and whose CTA keeps two CTAs per SM; the warp-
+    // specialised kernel first (its filtered-row ring holds two blocks)
+    int SW = 0, P = 0, offB = 0, Q = 0, NI = 0, NW = 0, HR = 0, M = JV - 1;
     size_t smem = 0;
+    for (int ws = 1; ws >= 0 && SW == 0; --ws) {
+    if (opts.ws >= 0 && ws != opts.ws) continue;
+    const int hr = (ws ? 2 : 1) * kRB + JV;
     // narrow strips (one box per block, three staged blocks) where one fits;
     // else wide strips (two boxes per block: the second starts early enough
     // that every group's band fits one of them)
@@ -155,23 +164,27 @@ rs_status setup(rs_plan *p, cudaStream_t s)
             }
         }
         if (pp == 0) continue;
-        const int qq = (HR + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
+        const int qq = (hr + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
         for (int ni = kMaxNI; ni >= 2; --ni) {
-            const size_t t = layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total;
-            if (t <= 113 * 1024 && (ni >= 3 || pass > 0)) {
+            const size_t t = ws ? layout_ws(ni, 2, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total
+                                : layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total;
+            if (t <= 113 * 1024 && (ni >= opts.ni_min || pass > 0)) {
                 SW = sw;
                 P = pp;
                 offB = ob;
                 Q = qq;
                 NI = ni;
+                NW = ws ? 2 : 0;
+                HR = hr;
                 smem = t;
                 break;
             }
         }
     }
+    }
     if (SW == 0) return RS_ERR_UNSUPPORTED;
     const int ngx = SW / kG;
-    const void *fn = kernel_for(C, JV, GV);
+    const void *fn = kernel_for(C, JV, GV, NW != 0);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "setting shared memory size");
     int occ = 0;
@@ -238,6 +251,14 @@ rs_status setup(rs_plan *p, cudaStream_t s)
     sp.offB = offB;
     sp.Q = Q;
     sp.NI = NI;
+    sp.NW = NW;
+    sp.HW = opts.hw > 0 ? std::min(6, std::max(2, opts.hw)) : 4;
+    {
+        Opts used = opts;
+        used.ws = NW ? 1 : 0;
+        used.hw = NW ? sp.HW : 0;
+        p->stream_code = used.code();
+    }
     sp.HR = HR;
     sp.M = M;
     sp.WP = WP;

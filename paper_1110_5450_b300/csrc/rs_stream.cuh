@@ -58,6 +58,8 @@ struct Params {
                           //    256-element box), in its own 128-byte aligned sub-buffer
     int32_t Q;            // rows per 4-sample column of the filtered-row ring (>= HR + M, odd)
     int32_t NI;           // staged input blocks (ring slots)
+    int32_t NW;           // warp-specialised kernel: vertical weight slots (0: phase-alternating kernel)
+    int32_t HW;           // warp-specialised kernel: warps on the horizontal pass
     int32_t HR, M;        // filtered-row ring rows, mirrored rows
     int32_t WP;           // most row groups that become ready after one block
     int32_t GV;           // rows per vertical group (the kernel's template argument)
@@ -87,6 +89,134 @@ __host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx,
     L.pe = fused::align_up(size_t(kMaxBlk) * 4, 128);
     L.total = 128 + size_t(NI) * L.slot + L.hring + L.hb + L.cb + L.pe + 128;
     return L;
+}
+
+// Horizontal pass of one 4-output group for the 32 rows of a staged block:
+// lane = row; rowp = the lane's staged row, hs = its ring slot.
+template <int C>
+__device__ __forceinline__ void h_group(const float *rowp, int cbq, const float *hbq, int JH, float4 *hring, int q,
+                                        int Q, int HR, int M, int hs)
+{
+    const float4 *src = reinterpret_cast<const float4 *>(rowp + cbq);
+    const float4 *wq = reinterpret_cast<const float4 *>(hbq);
+    float acc[kG][C];
+#pragma unroll
+    for (int g = 0; g < kG; ++g)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[g][c] = 0.f;
+    for (int t0 = 0; t0 < JH; t0 += 4) {
+        // 4 input pixels of this lane's row (C 16-byte words) ...
+        float d[4 * C];
+#pragma unroll
+        for (int v = 0; v < C; ++v) {
+            const float4 x = src[v];
+            d[4 * v] = x.x;
+            d[4 * v + 1] = x.y;
+            d[4 * v + 2] = x.z;
+            d[4 * v + 3] = x.w;
+        }
+        src += C;
+        // ... times the 4 outputs' weights at those pixels (warp-uniform)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float4 w = wq[t];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float x = d[t * C + c];
+                acc[0][c] = fmaf(w.x, x, acc[0][c]);
+                acc[1][c] = fmaf(w.y, x, acc[1][c]);
+                acc[2][c] = fmaf(w.z, x, acc[2][c]);
+                acc[3][c] = fmaf(w.w, x, acc[3][c]);
+            }
+        }
+        wq += 4;
+    }
+    // the group's 4 x C filtered samples, contiguous in the ring row
+    float4 o[C];
+    float *of = reinterpret_cast<float *>(o);
+#pragma unroll
+    for (int g = 0; g < kG; ++g)
+#pragma unroll
+        for (int c = 0; c < C; ++c) of[g * C + c] = acc[g][c];
+    float4 *dst = hring + (q * C) * Q + hs;
+#pragma unroll
+    for (int v = 0; v < C; ++v) dst[v * Q] = o[v];
+    if (hs < M) {
+#pragma unroll
+        for (int v = 0; v < C; ++v) dst[v * Q + HR] = o[v];
+    }
+}
+
+// Vertical pass of one row group (GV output rows) for one 4-sample column:
+// src4 = the column's first tap row in the ring, wv = the group's weights.
+template <int JV, int GV>
+__device__ __forceinline__ void v_task(const float4 *src4, const float4 *wv, float *out, int64_t out_stride,
+                                       int64_t y0, int64_t out_h, int64_t sx, int64_t row_samples, bool vec_ok)
+{
+    float a[GV][4];
+    if constexpr (GV == 4) {
+        // 4 rows x 2 sample pairs of packed accumulators; the band stores
+        // every weight twice, so pairs load as they are
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(src4);
+        const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(wv);
+        uint64_t acc[GV][2];
+#pragma unroll
+        for (int r = 0; r < GV; ++r) acc[r][0] = acc[r][1] = 0ull;
+#pragma unroll
+        for (int j = 0; j < JV; ++j) {
+            const ulonglong2 dd = src[j];
+#pragma unroll
+            for (int r2 = 0; r2 < GV / 2; ++r2) {
+                const ulonglong2 w = w2[(GV / 2) * j + r2]; // rows 2 r2, 2 r2 + 1
+                acc[2 * r2][0] = fused::fma2(w.x, dd.x, acc[2 * r2][0]);
+                acc[2 * r2][1] = fused::fma2(w.x, dd.y, acc[2 * r2][1]);
+                acc[2 * r2 + 1][0] = fused::fma2(w.y, dd.x, acc[2 * r2 + 1][0]);
+                acc[2 * r2 + 1][1] = fused::fma2(w.y, dd.y, acc[2 * r2 + 1][1]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < GV; ++r) {
+            fused::unpack2(acc[r][0], a[r][0], a[r][1]);
+            fused::unpack2(acc[r][1], a[r][2], a[r][3]);
+        }
+    } else {
+        // 8 rows x 4 samples; each loaded sample feeds the 8 rows
+#pragma unroll
+        for (int r = 0; r < GV; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
+#pragma unroll
+        for (int j = 0; j < JV; ++j) {
+            const float4 d = src4[j];
+            float w[GV];
+#pragma unroll
+            for (int v = 0; v < GV / 4; ++v) {
+                const float4 q = wv[(GV / 4) * j + v];
+                w[4 * v] = q.x;
+                w[4 * v + 1] = q.y;
+                w[4 * v + 2] = q.z;
+                w[4 * v + 3] = q.w;
+            }
+#pragma unroll
+            for (int r = 0; r < GV; ++r) {
+                a[r][0] = fmaf(w[r], d.x, a[r][0]);
+                a[r][1] = fmaf(w[r], d.y, a[r][1]);
+                a[r][2] = fmaf(w[r], d.z, a[r][2]);
+                a[r][3] = fmaf(w[r], d.w, a[r][3]);
+            }
+        }
+    }
+    float *o = out + y0 * out_stride + sx;
+    if (y0 + GV <= out_h && sx + 4 <= row_samples && vec_ok) {
+        // whole rows of 4 samples: 16-byte stores
+#pragma unroll
+        for (int h = 0; h < GV; ++h)
+            *reinterpret_cast<float4 *>(o + h * out_stride) = make_float4(a[h][0], a[h][1], a[h][2], a[h][3]);
+    } else {
+#pragma unroll
+        for (int h = 0; h < GV; ++h) {
+            if (y0 + h >= out_h) break;
+            for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[h * out_stride + i] = a[h][i];
+        }
+    }
 }
 
 template <int C, int JV, int GV>
@@ -195,56 +325,8 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
             int hs = base_k + lane;
             if (hs >= HR) hs -= HR;
             const float *rowp = slot_in(slot) + size_t(lane) * P;
-            for (int q = warp; q < ngv; q += kWarps) {
-                const float4 *src = reinterpret_cast<const float4 *>(rowp + cb[q]);
-                const float4 *wq = reinterpret_cast<const float4 *>(hb + q * JH * kG);
-                float acc[kG][C];
-#pragma unroll
-                for (int g = 0; g < kG; ++g)
-#pragma unroll
-                    for (int c = 0; c < C; ++c) acc[g][c] = 0.f;
-                for (int t0 = 0; t0 < JH; t0 += 4) {
-                    // 4 input pixels of this lane's row (C 16-byte words) ...
-                    float d[4 * C];
-#pragma unroll
-                    for (int v = 0; v < C; ++v) {
-                        const float4 x = src[v];
-                        d[4 * v] = x.x;
-                        d[4 * v + 1] = x.y;
-                        d[4 * v + 2] = x.z;
-                        d[4 * v + 3] = x.w;
-                    }
-                    src += C;
-                    // ... times the 4 outputs' weights at those pixels (warp-uniform)
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const float4 w = wq[t];
-#pragma unroll
-                        for (int c = 0; c < C; ++c) {
-                            const float x = d[t * C + c];
-                            acc[0][c] = fmaf(w.x, x, acc[0][c]);
-                            acc[1][c] = fmaf(w.y, x, acc[1][c]);
-                            acc[2][c] = fmaf(w.z, x, acc[2][c]);
-                            acc[3][c] = fmaf(w.w, x, acc[3][c]);
-                        }
-                    }
-                    wq += 4;
-                }
-                // the group's 4 x C filtered samples, contiguous in the ring row
-                float4 o[C];
-                float *of = reinterpret_cast<float *>(o);
-#pragma unroll
-                for (int g = 0; g < kG; ++g)
-#pragma unroll
-                    for (int c = 0; c < C; ++c) of[g * C + c] = acc[g][c];
-                float4 *dst = hring + (q * C) * Q + hs;
-#pragma unroll
-                for (int v = 0; v < C; ++v) dst[v * Q] = o[v];
-                if (hs < M) {
-#pragma unroll
-                    for (int v = 0; v < C; ++v) dst[v * Q + HR] = o[v];
-                }
-            }
+            for (int q = warp; q < ngv; q += kWarps)
+                h_group<C>(rowp, cb[q], hb + q * JH * kG, JH, hring, q, Q, HR, M, hs);
         }
         // every thread agrees on whether the block landed (a timeout stops all)
         if (!__syncthreads_and(landed ? 1 : 0)) break;
@@ -263,74 +345,9 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
                 int hs0 = base_k + (vbs[pr] - r_lo - k * kRB);
                 if (hs0 < 0) hs0 += HR;
                 if (hs0 >= HR) hs0 -= HR;
-                const float4 *src4 = hring + ch * Q + hs0;
-                const float4 *wv = reinterpret_cast<const float4 *>(wvs) + po * JV * (vtap_floats(GV) / 4);
-                float a[GV][4];
-                if constexpr (GV == 4) {
-                    // 4 rows x 2 sample pairs of packed accumulators; the band
-                    // stores every weight twice, so pairs load as they are
-                    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(src4);
-                    const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(wv);
-                    uint64_t acc[GV][2];
-#pragma unroll
-                    for (int r = 0; r < GV; ++r) acc[r][0] = acc[r][1] = 0ull;
-#pragma unroll
-                    for (int j = 0; j < JV; ++j) {
-                        const ulonglong2 dd = src[j];
-#pragma unroll
-                        for (int r2 = 0; r2 < GV / 2; ++r2) {
-                            const ulonglong2 w = w2[(GV / 2) * j + r2]; // rows 2 r2, 2 r2 + 1
-                            acc[2 * r2][0] = fused::fma2(w.x, dd.x, acc[2 * r2][0]);
-                            acc[2 * r2][1] = fused::fma2(w.x, dd.y, acc[2 * r2][1]);
-                            acc[2 * r2 + 1][0] = fused::fma2(w.y, dd.x, acc[2 * r2 + 1][0]);
-                            acc[2 * r2 + 1][1] = fused::fma2(w.y, dd.y, acc[2 * r2 + 1][1]);
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < GV; ++r) {
-                        fused::unpack2(acc[r][0], a[r][0], a[r][1]);
-                        fused::unpack2(acc[r][1], a[r][2], a[r][3]);
-                    }
-                } else {
-                    // 8 rows x 4 samples; each loaded sample feeds the 8 rows
-#pragma unroll
-                    for (int r = 0; r < GV; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
-#pragma unroll
-                    for (int j = 0; j < JV; ++j) {
-                        const float4 d = src4[j];
-                        float w[GV];
-#pragma unroll
-                        for (int v = 0; v < GV / 4; ++v) {
-                            const float4 q = wv[(GV / 4) * j + v];
-                            w[4 * v] = q.x;
-                            w[4 * v + 1] = q.y;
-                            w[4 * v + 2] = q.z;
-                            w[4 * v + 3] = q.w;
-                        }
-#pragma unroll
-                        for (int r = 0; r < GV; ++r) {
-                            a[r][0] = fmaf(w[r], d.x, a[r][0]);
-                            a[r][1] = fmaf(w[r], d.y, a[r][1]);
-                            a[r][2] = fmaf(w[r], d.z, a[r][2]);
-                            a[r][3] = fmaf(w[r], d.w, a[r][3]);
-                        }
-                    }
-                }
-                const int64_t sx = x0s + int64_t(ch) * 4;
-                const int64_t y0 = int64_t(GV) * pr;
-                float *o = p.out + y0 * p.out_stride + sx;
-                if (y0 + GV <= p.out_h && sx + 4 <= row_samples && vec_ok) {
-                    // whole rows of 4 samples: 16-byte stores
-#pragma unroll
-                    for (int h = 0; h < GV; ++h)
-                        *reinterpret_cast<float4 *>(o + h * p.out_stride) = make_float4(a[h][0], a[h][1], a[h][2], a[h][3]);
-                } else {
-#pragma unroll
-                    for (int h = 0; h < GV; ++h) {
-                        if (y0 + h >= p.out_h) break;
-                        for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[h * p.out_stride + i] = a[h][i];
-                    }
-                }
+                v_task<JV, GV>(hring + ch * Q + hs0,
+                               reinterpret_cast<const float4 *>(wvs) + po * JV * (vtap_floats(GV) / 4), p.out,
+                               p.out_stride, int64_t(GV) * pr, p.out_h, x0s + int64_t(ch) * 4, row_samples, vec_ok);
                 po += dpo;
                 ch += dch;
                 if (ch >= nch) {
@@ -348,6 +365,223 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     // land (bounded) before the CTA's shared memory is released.
     if (k < nblk && tid == 0) {
         for (int b = k; b < nblk && b < k + NI; ++b) fused::mbar_wait_bounded(&full[b % NI], uint32_t((b / NI) & 1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised variant: the first HW warps run the horizontal pass on
+// block k while the others run the vertical pass on block k - 1 (or earlier),
+// so the two phases overlap instead of alternating between block barriers
+// (HW follows the two passes' work per block).  The input
+// blocks and the vertical weights live in separate rings, each refilled by
+// its own consumer; the filtered-row ring holds two blocks plus a band.
+//   hdone[k & 1]: the horizontal warps finished block k (its rows are in the ring)
+//   vdone[k & 1]: the vertical warps finished block k (the ring slots of its
+//                 rows may be overwritten by block k + 2)
+
+struct LayoutWS {
+    size_t in_blk, in_ring, wv, vb, wslot, w_ring, hring, hb, cb, pe, total;
+};
+
+__host__ __device__ inline LayoutWS layout_ws(int NI, int NW, int P, int Q, int nch, int ngx, int JH, int WP, int JV,
+                                              bool two_boxes, int GV)
+{
+    LayoutWS L;
+    L.in_blk = size_t(kRB) * P * 4 * (two_boxes ? 2 : 1);
+    L.in_ring = size_t(NI) * L.in_blk; // in_blk is a multiple of 128 bytes
+    L.wv = size_t(WP) * JV * vtap_floats(GV) * 4;
+    L.vb = fused::align_up(size_t(WP + 8) * 4, 16);
+    L.wslot = fused::align_up(L.wv + L.vb, 128);
+    L.w_ring = size_t(NW) * L.wslot;
+    L.hring = fused::align_up(size_t(nch) * Q * 16, 128);
+    L.hb = fused::align_up(size_t(ngx) * JH * kG * 4, 128);
+    L.cb = fused::align_up(size_t(ngx) * 4, 128);
+    L.pe = fused::align_up(size_t(kMaxBlk) * 4, 128);
+    L.total = 128 + L.in_ring + L.w_ring + L.hring + L.hb + L.cb + L.pe + 128;
+    return L;
+}
+
+// bar.red.and over a named barrier: every participating thread gets the AND.
+__device__ __forceinline__ bool group_and(int id, int threads, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.and.pred po, %2, %3, pi;\n\tselp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"(v ? 1u : 0u), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+template <int C, int JV, int GV>
+__global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                  const Params p)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (fused::smem_addr(smem_raw) & 127u)) & 127u);
+    const int ngx = p.SW / kG;
+    const int JH = p.JH, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, NW = p.NW, WP = p.WP;
+    const int nch = (p.SW * C) / 4;
+    const LayoutWS L = layout_ws(NI, NW, P, Q, nch, ngx, JH, WP, JV, p.offB != 0, GV);
+    unsigned char *in_ring = smem;
+    unsigned char *w_ring = smem + L.in_ring;
+    float4 *hring = reinterpret_cast<float4 *>(w_ring + L.w_ring);
+    float *hb = reinterpret_cast<float *>(w_ring + L.w_ring + L.hring);
+    int32_t *cb = reinterpret_cast<int32_t *>(w_ring + L.w_ring + L.hring + L.hb);
+    int32_t *pe_s = reinterpret_cast<int32_t *>(w_ring + L.w_ring + L.hring + L.hb + L.cb);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(w_ring + L.w_ring + L.hring + L.hb + L.cb + L.pe);
+    uint64_t *full_in = bars, *full_w = bars + kMaxNI, *hdone = bars + 2 * kMaxNI, *vdone = hdone + 2;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(vdone + 2);
+    auto slot_in = [&](int s) { return reinterpret_cast<float *>(in_ring + s * L.in_blk); };
+    auto slot_wv = [&](int s) { return reinterpret_cast<const float4 *>(w_ring + s * L.wslot); };
+    auto slot_vb = [&](int s) { return reinterpret_cast<const int32_t *>(w_ring + s * L.wslot + L.wv); };
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kHWarps = p.HW, kHThreads = 32 * p.HW, kVThreads = kThreads - kHThreads;
+    const int strip = int(blockIdx.x) % p.n_strips, range = int(blockIdx.x) / p.n_strips;
+    const int p0 = range * p.pairs_per_range;
+    const int p1 = min(p.pairs, p0 + p.pairs_per_range);
+    if (p0 >= p1) return;
+    const int g0 = strip * ngx;
+    const int ngv = min(ngx, p.groups_x - g0);
+    const int xs = __ldg(p.hbase + g0) * C;
+    const int r_lo = __ldg(p.vbase + p0);
+    const int r_hi = __ldg(p.vbase + p1 - 1) + JV;
+    const int nblk = min((r_hi - r_lo + kRB - 1) / kRB, kMaxBlk);
+
+    if (tid == 0) {
+        for (int s = 0; s < NI; ++s) fused::mbar_init(&full_in[s], 1);
+        for (int s = 0; s < NW; ++s) fused::mbar_init(&full_w[s], 1);
+        for (int b = 0; b < 2; ++b) {
+            fused::mbar_init(&hdone[b], kHThreads);
+            fused::mbar_init(&vdone[b], kVThreads);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < ngx * JH * kG; e += kThreads) {
+        const int q = e / (JH * kG);
+        hb[e] = q < ngv ? __ldg(p.hband + size_t(g0) * JH * kG + e) : 0.f;
+    }
+    for (int q = tid; q < ngx; q += kThreads) {
+        int o = q < ngv ? __ldg(p.hbase + g0 + q) * C - xs : 0;
+        if (p.offB && o + JH * C > P) o += kRB * P - p.offB;
+        cb[q] = o;
+    }
+    auto kb = [&](int vb) {
+        const int k = (vb + JV - r_lo + kRB - 1) / kRB - 1;
+        return k < 0 ? 0 : (k > nblk - 1 ? nblk - 1 : k);
+    };
+    for (int q = p0 + tid; q < p1; q += kThreads) {
+        const int kp = kb(__ldg(p.vbase + q));
+        const int kn = q + 1 < p1 ? kb(__ldg(p.vbase + q + 1)) : nblk;
+        for (int k = kp; k < kn; ++k) pe_s[k] = q + 1;
+        if (q == p0)
+            for (int k = 0; k < kp; ++k) pe_s[k] = p0;
+    }
+    __syncthreads();
+
+    const uint32_t blk_bytes = uint32_t(L.in_blk);
+    auto issue_in = [&](int k) { // input block k (first horizontal thread)
+        const int s = k % NI;
+        fused::mbar_arrive_expect_tx(&full_in[s], blk_bytes);
+        fused::tma_load_2d(slot_in(s), &tmap, &full_in[s], xs, r_lo + k * kRB);
+        if (p.offB) fused::tma_load_2d(slot_in(s) + kRB * P, &tmap, &full_in[s], xs + p.offB, r_lo + k * kRB);
+    };
+    auto issue_w = [&](int k) { // weights and bases of block k's groups (first vertical thread)
+        const int s = k % NW;
+        const int ps = k ? pe_s[k - 1] : p0, pe = pe_s[k];
+        int n = pe - ps;
+        if (n > WP) {
+            fused::flag(p.err, fused::kErrBounds);
+            n = 0;
+        }
+        const int pa = ps & ~3, pb = (pe + 3) & ~3;
+        const uint32_t wbytes = uint32_t(n) * JV * vtap_floats(GV) * 4, vbytes = n ? uint32_t(pb - pa) * 4 : 0u;
+        fused::mbar_arrive_expect_tx(&full_w[s], wbytes + vbytes);
+        if (n) {
+            fused::bulk_load(const_cast<float4 *>(slot_wv(s)), p.vband + size_t(ps) * JV * vtap_floats(GV), wbytes,
+                             &full_w[s]);
+            fused::bulk_load(const_cast<int32_t *>(slot_vb(s)), p.vbase + pa, vbytes, &full_w[s]);
+        }
+    };
+
+    int k = 0;
+    bool ok = true;
+    if (warp < kHWarps) {
+        // ================ horizontal pass: block k into the ring ================
+        if (tid == 0)
+            for (int b = 0; b < NI && b < nblk; ++b) issue_in(b);
+        for (; k < nblk; ++k) {
+            const int slot = k % NI;
+            bool good = fused::wait_or_abort(&full_in[slot], uint32_t((k / NI) & 1), abort_flag, p.err);
+            // the ring slots of block k's rows held block k - 2's rows
+            if (good && k >= 2) good = fused::wait_or_abort(&vdone[k & 1], uint32_t(((k - 2) >> 1) & 1), abort_flag, p.err);
+            if (!group_and(1, kHThreads, good)) {
+                ok = false;
+                break;
+            }
+            const int base_k = (k * kRB) % HR;
+            int hs = base_k + lane;
+            if (hs >= HR) hs -= HR;
+            const float *rowp = slot_in(slot) + size_t(lane) * P;
+            for (int q = warp; q < ngv; q += kHWarps)
+                h_group<C>(rowp, cb[q], hb + q * JH * kG, JH, hring, q, Q, HR, M, hs);
+            fused::named_sync(1, kHThreads); // the staged block is consumed
+            if (tid == 0 && k + NI < nblk) issue_in(k + NI);
+            fused::mbar_arrive(&hdone[k & 1]);
+        }
+    } else {
+        // ================ vertical pass: the groups block k completes ================
+        const int vt = tid - kHThreads;
+        if (vt == 0)
+            for (int b = 0; b < NW && b < nblk; ++b) issue_w(b);
+        const int64_t row_samples = p.out_w * C;
+        const int64_t x0s = int64_t(strip) * p.SW * C;
+        const bool vec_ok = ((reinterpret_cast<uintptr_t>(p.out) | uintptr_t(p.out_stride * 4)) & 15u) == 0;
+        for (; k < nblk; ++k) {
+            const int wslot = k % NW;
+            bool good = fused::wait_or_abort(&full_w[wslot], uint32_t((k / NW) & 1), abort_flag, p.err);
+            if (good) good = fused::wait_or_abort(&hdone[k & 1], uint32_t((k >> 1) & 1), abort_flag, p.err);
+            if (!group_and(2, kVThreads, good)) {
+                ok = false;
+                break;
+            }
+            const int base_k = (k * kRB) % HR;
+            const int ps = k ? pe_s[k - 1] : p0, pe = pe_s[k];
+            const int n = pe - ps <= WP ? pe - ps : 0;
+            const float4 *wvs = slot_wv(wslot);
+            const int32_t *vbs = slot_vb(wslot) - (ps & ~3);
+            const int ntask = n * nch;
+            int po = vt / nch, ch = vt - (vt / nch) * nch;
+            const int dpo = kVThreads / nch, dch = kVThreads - dpo * nch;
+            for (int t = vt; t < ntask; t += kVThreads) {
+                const int pr = ps + po;
+                int hs0 = base_k + (vbs[pr] - r_lo - k * kRB);
+                if (hs0 < 0) hs0 += HR;
+                if (hs0 >= HR) hs0 -= HR;
+                v_task<JV, GV>(hring + ch * Q + hs0, wvs + po * JV * (vtap_floats(GV) / 4), p.out, p.out_stride,
+                               int64_t(GV) * pr, p.out_h, x0s + int64_t(ch) * 4, row_samples, vec_ok);
+                po += dpo;
+                ch += dch;
+                if (ch >= nch) {
+                    ch -= nch;
+                    ++po;
+                }
+            }
+            fused::named_sync(2, kVThreads); // the weights slot is consumed
+            if (vt == 0 && k + NW < nblk) issue_w(k + NW);
+            fused::mbar_arrive(&vdone[k & 1]);
+        }
+    }
+    // On a timeout, let the copies still in flight land (bounded) before the
+    // CTA's shared memory is released.
+    if (!ok) {
+        if (tid == 0)
+            for (int b = k; b < nblk && b < k + NI; ++b) fused::mbar_wait_bounded(&full_in[b % NI], uint32_t((b / NI) & 1));
+        if (tid == kHThreads)
+            for (int b = k; b < nblk && b < k + NW; ++b) fused::mbar_wait_bounded(&full_w[b % NW], uint32_t((b / NW) & 1));
     }
 }
 
