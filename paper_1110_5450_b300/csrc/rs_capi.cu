@@ -1031,16 +1031,22 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
             o.ws = c[0];
             o.hw = c[1];
             o.ni_min = c[2];
-            const rs_status ss = stream::setup(p, stream, o);
-            if (ss == RS_ERR_UNSUPPORTED) continue;
-            if (ss != RS_OK) return ss;
-            p->use_stream = 1;
-            double us = 0;
-            s = time_plan(p, d_in, d_out, stream, &us);
-            if (s != RS_OK) return s;
-            if (us < best_s) {
-                best_s = us;
-                best_code = p->stream_code;
+            // the cost model's three best strip widths for this configuration
+            int w[3];
+            const int nw = stream::widths(p, o, w, 3);
+            for (int i = 0; i < nw; ++i) {
+                o.sw = w[i];
+                const rs_status ss = stream::setup(p, stream, o);
+                if (ss == RS_ERR_UNSUPPORTED) continue;
+                if (ss != RS_OK) return ss;
+                p->use_stream = 1;
+                double us = 0;
+                s = time_plan(p, d_in, d_out, stream, &us);
+                if (s != RS_OK) return s;
+                if (us < best_s) {
+                    best_s = us;
+                    best_code = p->stream_code;
+                }
             }
         }
         p->use_stream = 0;

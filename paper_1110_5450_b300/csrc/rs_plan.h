@@ -118,19 +118,24 @@ namespace stream {
 // horizontal pass (0: 4); ni_min = fewest staged input blocks of a narrow strip.
 struct Opts {
     int ws = -1, hw = 0, ni_min = 3;
-    int code() const { return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min; }
+    int sw = 0; // strip width (0: the cost model's choice)
+    int code() const { return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4); }
     static Opts decode(int c)
     {
         Opts o;
         o.ws = (c & 2) ? 1 : 0;
         o.hw = (c >> 2) & 15;
         o.ni_min = (c >> 6) & 7;
+        o.sw = ((c >> 9) & 63) * 4;
         return o;
     }
 };
 // Configures the row-streaming kernel for a plan (needs the host start tables);
 // RS_ERR_UNSUPPORTED when the plan is not eligible.
 rs_status setup(rs_plan *p, cudaStream_t s, const Opts &o = Opts());
+// Strip widths the configuration admits, best first by the cost model (at
+// most n); 0 if the plan is not eligible.
+int widths(rs_plan *p, const Opts &o, int *out, int n);
 // Rebuilds its band tables from the plan's weight tables (after a recompute).
 rs_status rebuild(rs_plan *p, cudaStream_t s);
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);

@@ -80,121 +80,72 @@ int pad_pitch(int n) // multiple of 4 with n / 4 odd, >= n
     return p;
 }
 
-} // namespace
+struct Strip {
+    int sw, P, offB, Q, NI, NW, HR, occ, ppr;
+    size_t smem;
+    double cost;
+};
 
-rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
+// Every strip width (multiple of 4 outputs, at most 128) whose staged width
+// fits the TMA boxes and whose CTA keeps two CTAs per SM, for the first
+// staging form that admits any: the warp-specialised kernel first (its
+// filtered-row ring holds two blocks), then narrow strips with >= ni_min
+// staged blocks, wide strips (two boxes per block: the second starts early
+// enough that every group's band fits one of them), narrow with 2 blocks.
+// Each gets its row ranges and a modelled time: whole waves of CTAs, each
+// CTA's work (strip width plus a fixed share, rows of its range plus the
+// band and the pipeline fill); cheapest first.
+std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, const std::vector<int32_t> &hb,
+                          int JH, int JV, int GV, int WP, const std::vector<int32_t> &vb, int pairs)
 {
-    p->stream_ok = 0;
-    const rs_plan_desc &d = p->desc;
-    const int C = d.channels;
-    if (d.in_dtype != RS_F32 || (C != 1 && C != 3) || (d.flags & RS_NO_STREAM)) return RS_ERR_UNSUPPORTED;
-    if (!tma_layout_ok(p)) return RS_ERR_UNSUPPORTED;
-    const std::vector<int32_t> &sx = p->host_start_x, &sy = p->host_start_y;
-    const AxisGeom &gx = p->gx, &gy = p->gy;
-    // horizontal band: 4-pixel aligned group bases
-    const int groups_x = int((gx.n_out + kG - 1) / kG);
-    std::vector<int32_t> hb(groups_x);
-    int JH = 0;
-    for (int q = 0; q < groups_x; ++q) {
-        int lo = int(gx.n_in), hi = 0;
-        for (int m = 0; m < kG && q * kG + m < gx.n_out; ++m) {
-            lo = std::min(lo, int(sx[q * kG + m]));
-            hi = std::max(hi, int(sx[q * kG + m]) + gx.t_eff);
-        }
-        hb[q] = lo & ~3;
-        JH = std::max(JH, hi - hb[q]);
-    }
-    JH = (JH + 3) / 4 * 4;
-    // vertical band (the tile kernel's band code): groups of 8 rows while the
-    // band stays within 16 taps, else groups of 4
-    int GV = 8, JV = vertical_taps(sy, gy.t_eff, 8);
-    if (JV == 0) {
-        GV = 4;
-        JV = vertical_taps(sy, gy.t_eff, 4);
-    }
-    if (JH > 40 || JV == 0 || JV > gy.n_in) return RS_ERR_UNSUPPORTED;
-    // row bases of the groups (as the band kernel computes them) and the most
-    // groups whose last row falls in one 32-row block
-    const int pairs = int((gy.n_out + GV - 1) / GV);
-    std::vector<int32_t> vb(pairs);
-    for (int q = 0; q < pairs; ++q) {
-        int lo = sy[GV * q];
-        for (int r = 1; r < GV && GV * q + r < int(sy.size()); ++r) lo = std::min(lo, int(sy[GV * q + r]));
-        vb[q] = gy.n_in >= JV ? std::min<int64_t>(lo, gy.n_in - JV) : 0;
-    }
-    int WP = 0;
-    for (int a = 0, b = 0; a < pairs; ++a) {
-        while (b < pairs && vb[b] + JV <= vb[a] + JV + kRB - 1) ++b;
-        WP = std::max(WP, b - a);
-    }
-    WP = std::max(WP, 1);
-    // the widest strip (multiple of 4 outputs, at most 128) whose staged width
-    // fits the TMA boxes and whose CTA keeps two CTAs per SM; the warp-
-    // specialised kernel first (its filtered-row ring holds two blocks)
-    int SW = 0, P = 0, offB = 0, Q = 0, NI = 0, NW = 0, HR = 0, M = JV - 1;
-    size_t smem = 0;
-    for (int ws = 1; ws >= 0 && SW == 0; --ws) {
-    if (opts.ws >= 0 && ws != opts.ws) continue;
-    const int hr = (ws ? 2 : 1) * kRB + JV;
-    // narrow strips (one box per block, three staged blocks) where one fits;
-    // else wide strips (two boxes per block: the second starts early enough
-    // that every group's band fits one of them)
-    // (passes: narrow with >= 3 staged blocks, wide, narrow with 2 blocks)
-    for (int pass = 0; pass < 3 && SW == 0; ++pass)
-    for (int sw = 128; sw >= 16 && SW == 0; sw -= 4) {
-        const int ngx = sw / kG;
-        int need = 0;
-        for (int g0 = 0; g0 < groups_x; g0 += ngx) {
-            const int gl = std::min(groups_x, g0 + ngx) - 1;
-            need = std::max(need, (hb[gl] + JH - hb[g0]) * C);
-        }
-        int pp = 0, ob = 0;
-        if (pass != 1) {
-            pp = pad_pitch(need);
-            if (pp > 256) pp = 0;
-        } else {
-            // boxes A = [0, P) and B = [ob, ob + P) of the strip's samples:
-            // ob <= P - JH C (overlap of a band) and ob + P >= need
-            for (int cand = pad_pitch((need + JH * C + 1) / 2); cand <= 256 && !pp; cand += 8) {
-                const int o = (cand - JH * C) / 4 * 4;
-                if (o > 0 && o + cand >= need) {
-                    pp = cand;
-                    ob = o;
+    // unless the caller fixes the form: groups of 8 rows (narrow vertical
+    // bands) run the phase-alternating kernel with 2 staged blocks, groups of
+    // 4 (wide bands) the warp-specialised one -- the faster form of each as
+    // measured on 4096x4096x3 at x1.37 and x0.3
+    Opts opts = opts_in;
+    const int first = opts.ws >= 0 ? opts.ws : (GV == 8 ? 0 : 1);
+    if (opts.ws < 0 && GV == 8) opts.ni_min = std::min(opts.ni_min, 2);
+    std::vector<Strip> out;
+    const int M = JV - 1;
+    for (int i = 0; i < 2 && out.empty(); ++i) {
+        const int ws = i == 0 ? first : 1 - first;
+        if (i == 1 && opts.ws >= 0) break; // a fixed form has no fallback
+        const int hr = (ws ? 2 : 1) * kRB + JV;
+        for (int pass = 0; pass < 3 && out.empty(); ++pass)
+            for (int sw = 128; sw >= 16; sw -= 4) {
+                const int ngx = sw / kG;
+                int need = 0;
+                for (int g0 = 0; g0 < groups_x; g0 += ngx) {
+                    const int gl = std::min(groups_x, g0 + ngx) - 1;
+                    need = std::max(need, (hb[gl] + JH - hb[g0]) * C);
+                }
+                int pp = 0, ob = 0;
+                if (pass != 1) {
+                    pp = pad_pitch(need);
+                    if (pp > 256) pp = 0;
+                } else {
+                    // boxes A = [0, P) and B = [ob, ob + P) of the strip's samples:
+                    // ob <= P - JH C (overlap of a band) and ob + P >= need
+                    for (int cand = pad_pitch((need + JH * C + 1) / 2); cand <= 256 && !pp; cand += 8) {
+                        const int o = (cand - JH * C) / 4 * 4;
+                        if (o > 0 && o + cand >= need) {
+                            pp = cand;
+                            ob = o;
+                        }
+                    }
+                }
+                if (pp == 0) continue;
+                const int qq = (hr + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
+                for (int ni = kMaxNI; ni >= 2; --ni) {
+                    const size_t t = ws ? layout_ws(ni, 2, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total
+                                        : layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total;
+                    if (t <= 113 * 1024 && (ni >= opts.ni_min || pass > 0)) {
+                        out.push_back({sw, pp, ob, qq, ni, ws ? 2 : 0, hr, 0, 0, t, 0.0});
+                        break;
+                    }
                 }
             }
-        }
-        if (pp == 0) continue;
-        const int qq = (hr + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
-        for (int ni = kMaxNI; ni >= 2; --ni) {
-            const size_t t = ws ? layout_ws(ni, 2, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total
-                                : layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total;
-            if (t <= 113 * 1024 && (ni >= opts.ni_min || pass > 0)) {
-                SW = sw;
-                P = pp;
-                offB = ob;
-                Q = qq;
-                NI = ni;
-                NW = ws ? 2 : 0;
-                HR = hr;
-                smem = t;
-                break;
-            }
-        }
     }
-    }
-    if (SW == 0) return RS_ERR_UNSUPPORTED;
-    const int ngx = SW / kG;
-    const void *fn = kernel_for(C, JV, GV, NW != 0);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return cuda_fail(e, "setting shared memory size");
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-    if (occ < 1) return RS_ERR_UNSUPPORTED;
-    // row ranges: enough CTAs for whole waves (>= 90% of the last wave busy),
-    // each range within the kernel's per-CTA block budget
-    const int n_strips = (groups_x + ngx - 1) / ngx;
-    const int slots = occ * p->num_sms;
     auto blocks_ok = [&](int ppr) {
         for (int q0 = 0; q0 < pairs; q0 += ppr) {
             const int q1 = std::min(pairs, q0 + ppr) - 1;
@@ -202,17 +153,135 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
         }
         return true;
     };
-    int ppr = 0;
-    for (int nr = 1; nr <= 1024; ++nr) {
-        const int cand = (pairs + nr - 1) / nr;
-        if (cand < 8 && nr > 1 && ppr) break;
-        if (!blocks_ok(cand)) continue;
-        const int64_t grid = int64_t(n_strips) * ((pairs + cand - 1) / cand);
-        const int64_t waves = (grid + slots - 1) / slots;
-        ppr = cand;
-        if (grid >= slots && double(grid) / double(waves * slots) >= 0.9) break;
+    std::vector<Strip> ok;
+    for (Strip c : out) {
+        const void *fn = kernel_for(C, JV, GV, c.NW != 0);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, fn, kThreads, c.smem) != cudaSuccess || c.occ < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const int n_strips = (groups_x + c.sw / kG - 1) / (c.sw / kG);
+        const int64_t slots = int64_t(c.occ) * p->num_sms;
+        c.cost = 1e300;
+        for (int nr = 1; nr <= 1024; ++nr) {
+            const int cand = (pairs + nr - 1) / nr;
+            if (cand < 8 && nr > 1) break;
+            if (!blocks_ok(cand)) continue;
+            const int ranges = (pairs + cand - 1) / cand;
+            int rows = 0;
+            for (int q0 = 0; q0 < pairs; q0 += cand) {
+                const int q1 = std::min(pairs, q0 + cand) - 1;
+                rows = std::max(rows, vb[q1] + JV - vb[q0]);
+            }
+            const int64_t grid = int64_t(n_strips) * ranges;
+            const int64_t waves = (grid + slots - 1) / slots;
+            const double cost = double(waves) * (c.sw + 8) * (rows + 2 * kRB);
+            if (cost < c.cost * 0.999) {
+                c.cost = cost;
+                c.ppr = cand;
+            }
+            if (ranges >= pairs) break;
+        }
+        if (c.ppr) ok.push_back(c);
     }
-    if (ppr == 0) return RS_ERR_UNSUPPORTED;
+    std::stable_sort(ok.begin(), ok.end(), [](const Strip &a, const Strip &b) { return a.cost < b.cost; });
+    return ok;
+}
+
+// The plan's bands for the streaming kernel: 4-pixel aligned horizontal
+// group bases and taps, the vertical group size, taps and row bases, and the
+// most groups whose last row falls in one 32-row block.
+struct Bands {
+    int C = 0, groups_x = 0, JH = 0, GV = 8, JV = 0, pairs = 0, WP = 0;
+    std::vector<int32_t> hb, vb;
+};
+
+rs_status bands_of(const rs_plan *p, Bands &b)
+{
+    const rs_plan_desc &d = p->desc;
+    b.C = d.channels;
+    if (d.in_dtype != RS_F32 || (b.C != 1 && b.C != 3) || (d.flags & RS_NO_STREAM)) return RS_ERR_UNSUPPORTED;
+    if (!tma_layout_ok(p)) return RS_ERR_UNSUPPORTED;
+    const std::vector<int32_t> &sx = p->host_start_x, &sy = p->host_start_y;
+    const AxisGeom &gx = p->gx, &gy = p->gy;
+    b.groups_x = int((gx.n_out + kG - 1) / kG);
+    b.hb.assign(b.groups_x, 0);
+    int JH = 0;
+    for (int q = 0; q < b.groups_x; ++q) {
+        int lo = int(gx.n_in), hi = 0;
+        for (int m = 0; m < kG && q * kG + m < gx.n_out; ++m) {
+            lo = std::min(lo, int(sx[q * kG + m]));
+            hi = std::max(hi, int(sx[q * kG + m]) + gx.t_eff);
+        }
+        b.hb[q] = lo & ~3;
+        JH = std::max(JH, hi - b.hb[q]);
+    }
+    b.JH = (JH + 3) / 4 * 4;
+    // vertical band (the tile kernel's band code): groups of 8 rows while the
+    // band stays within 16 taps, else groups of 4
+    b.GV = 8;
+    b.JV = vertical_taps(sy, gy.t_eff, 8);
+    if (b.JV == 0) {
+        b.GV = 4;
+        b.JV = vertical_taps(sy, gy.t_eff, 4);
+    }
+    if (b.JH > 40 || b.JV == 0 || b.JV > gy.n_in) return RS_ERR_UNSUPPORTED;
+    const int GV = b.GV, JV = b.JV;
+    b.pairs = int((gy.n_out + GV - 1) / GV);
+    b.vb.assign(b.pairs, 0);
+    for (int q = 0; q < b.pairs; ++q) {
+        int lo = sy[GV * q];
+        for (int r = 1; r < GV && GV * q + r < int(sy.size()); ++r) lo = std::min(lo, int(sy[GV * q + r]));
+        b.vb[q] = gy.n_in >= JV ? std::min<int64_t>(lo, gy.n_in - JV) : 0;
+    }
+    int WP = 0;
+    for (int a = 0, e = 0; a < b.pairs; ++a) {
+        while (e < b.pairs && b.vb[e] + JV <= b.vb[a] + JV + kRB - 1) ++e;
+        WP = std::max(WP, e - a);
+    }
+    b.WP = std::max(WP, 1);
+    return RS_OK;
+}
+
+} // namespace
+
+int widths(rs_plan *p, const Opts &opts, int *out, int n)
+{
+    Bands b;
+    if (bands_of(p, b) != RS_OK) return 0;
+    const std::vector<Strip> c = strips(p, opts, b.C, b.groups_x, b.hb, b.JH, b.JV, b.GV, b.WP, b.vb, b.pairs);
+    int k = 0;
+    for (; k < n && k < int(c.size()); ++k) out[k] = c[k].sw;
+    return k;
+}
+
+rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
+{
+    p->stream_ok = 0;
+    Bands bd;
+    const rs_status bst = bands_of(p, bd);
+    if (bst != RS_OK) return bst;
+    const rs_plan_desc &d = p->desc;
+    const AxisGeom &gx = p->gx, &gy = p->gy;
+    const int C = bd.C, groups_x = bd.groups_x, JH = bd.JH, GV = bd.GV, JV = bd.JV, pairs = bd.pairs, WP = bd.WP;
+    const std::vector<int32_t> &hb = bd.hb, &vb = bd.vb;
+    std::vector<Strip> cands = strips(p, opts, C, groups_x, hb, JH, JV, GV, WP, vb, pairs);
+    if (cands.empty()) return RS_ERR_UNSUPPORTED;
+    const Strip *pick = &cands[0];
+    if (opts.sw > 0) {
+        pick = nullptr;
+        for (const Strip &c : cands)
+            if (c.sw == opts.sw) pick = &c;
+        if (!pick) return RS_ERR_UNSUPPORTED;
+    }
+    const int SW = pick->sw, P = pick->P, offB = pick->offB, Q = pick->Q, NI = pick->NI, NW = pick->NW,
+              HR = pick->HR, M = JV - 1, occ = pick->occ, ppr = pick->ppr;
+    const size_t smem = pick->smem;
+    const int ngx = SW / kG;
+    const int n_strips = (groups_x + ngx - 1) / ngx;
+    const void *fn = kernel_for(C, JV, GV, NW != 0);
+    cudaError_t e = cudaSuccess;
 
     // device tables: horizontal base + band, vertical base + band
     Carver cv;
@@ -257,6 +326,7 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
         Opts used = opts;
         used.ws = NW ? 1 : 0;
         used.hw = NW ? sp.HW : 0;
+        used.sw = SW;
         p->stream_code = used.code();
     }
     sp.HR = HR;
