@@ -113,14 +113,18 @@ typedef enum {
 #define RS_TWO_PASS 0x08u     /* separate H-then-V kernels through an HBM buffer  */
 #define RS_CHECK 0x10u        /* device bounds checks that set an error word      */
 #define RS_NO_STREAM 0x20u    /* never pick the row-streaming kernel              */
-#define RS_FORCE_STREAM 0x40u /* pick the row-streaming kernel (FP32, 1 or 3 channels;
-                                 bands of 4 outputs of at most 40 / 32 inputs across /
-                                 down); RS_ERR_UNSUPPORTED where it cannot apply  */
+#define RS_FORCE_STREAM 0x40u /* pick the row-streaming kernel (FP32/FP16/BF16, 1 or 3
+                                 channels; bands of 4 outputs of at most 40 / 32
+                                 inputs across / down); RS_ERR_UNSUPPORTED where
+                                 it cannot apply                                   */
 /* The row-streaming kernel runs the horizontal pass first on staged input rows
- * and the vertical pass on a ring of filtered rows, with deep TMA prefetch and
- * coalesced output rows.  It is chosen for FP32 plans of 1 or 3 channels whose
- * bands of 4 outputs need at most 40 input pixels across and 32 input rows
- * down, with a 16-byte row pitch; an input pointer that is not 16-byte aligned
+ * and the vertical pass on a ring of filtered rows (FP32 whatever the storage
+ * type), with deep TMA prefetch and coalesced output rows.  It is chosen for
+ * FP32, FP16 and BF16 plans of 1 or 3 channels whose bands of 4 outputs need
+ * at most 40 input pixels across and 32 input rows down, with a 16-byte row
+ * pitch -- except 16-bit plans that take the tensor-core tiles (wide
+ * antialiasing), which keep them unless this kernel is forced or the
+ * autotuner measures it faster; an input pointer that is not 16-byte aligned
  * at rs_resample falls back to the tile kernel of the same plan. */
 
 /* Plan descriptor.  Sizes are in samples/elements, not bytes. */

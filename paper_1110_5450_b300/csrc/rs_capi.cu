@@ -841,9 +841,11 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
         p->path = 0;
         // the row-streaming kernel, where it applies, replaces the tile kernel
         // (which stays configured for inputs it cannot take)
+        // (a 16-bit wide downscale keeps its tensor-core tiles unless the
+        // streaming kernel is forced; the autotuner times both)
         const rs_status ss = stream::setup(p, stream);
         if (ss == RS_OK) {
-            p->use_stream = 1;
+            p->use_stream = (!p->chosen.tc || (d.flags & RS_FORCE_STREAM)) ? 1 : 0;
         } else if (ss != RS_ERR_UNSUPPORTED) {
             delete p;
             return ss;
@@ -851,7 +853,7 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     }
     if ((d.flags & RS_FORCE_STREAM) && !p->stream_ok) {
         delete p;
-        return fail(RS_ERR_UNSUPPORTED, "row-streaming kernel needs FP32, 1 or 3 channels, a 16-byte row pitch, "
+        return fail(RS_ERR_UNSUPPORTED, "row-streaming kernel needs FP32, FP16 or BF16, 1 or 3 channels, a 16-byte row pitch, "
                                         "a horizontal band of at most 40 and a vertical band of at most 32 inputs");
     }
     if (st != RS_OK) {

@@ -1,7 +1,7 @@
 // rs_stream.cu -- host side of the row-streaming kernel (rs_stream.cuh): its
-// band tables, configuration, tensor map and launch.  Used by FP32 plans of 1
-// or 3 channels whose horizontal band is narrow (upscales and mild
-// downscales); every other plan runs the tile kernel.
+// band tables, configuration, tensor map and launch.  Used by FP32, FP16 and
+// BF16 plans of 1 or 3 channels whose horizontal band is narrow (upscales and
+// downscales to about x0.3); every other plan runs the tile kernel.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -13,40 +13,17 @@ namespace rs {
 namespace stream {
 namespace {
 
-// Instantiated kernels: channels x vertical taps x rows per vertical group (a
-// plan's band is padded with zero weights to the next instantiated width):
-// groups of 8 rows up to 16 taps, groups of 4 rows up to 32.
+// Vertical band widths the kernels are instantiated for (rs_stream.cuh).
 constexpr int kJV8[] = {8, 10, 12, 14, 16};
 constexpr int kJV4[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
 
-template <int C, int JV, int GV> const void *kernel_of(bool ws)
+const void *kernel_for(int dtype, int C, int jv, int gv, bool ws)
 {
-    return ws ? reinterpret_cast<const void *>(&stream_ws_kernel<C, JV, GV>)
-              : reinterpret_cast<const void *>(&stream_kernel<C, JV, GV>);
-}
-
-template <int C, int GV> const void *kernel_jv(int jv, bool ws)
-{
-    switch (jv) {
-    case 4: return GV == 4 ? kernel_of<C, 4, 4>(ws) : nullptr;
-    case 6: return GV == 4 ? kernel_of<C, 6, 4>(ws) : nullptr;
-    case 8: return kernel_of<C, 8, GV>(ws);
-    case 10: return kernel_of<C, 10, GV>(ws);
-    case 12: return kernel_of<C, 12, GV>(ws);
-    case 14: return kernel_of<C, 14, GV>(ws);
-    case 16: return kernel_of<C, 16, GV>(ws);
-    case 20: return GV == 4 ? kernel_of<C, 20, 4>(ws) : nullptr;
-    case 24: return GV == 4 ? kernel_of<C, 24, 4>(ws) : nullptr;
-    case 28: return GV == 4 ? kernel_of<C, 28, 4>(ws) : nullptr;
-    case 32: return GV == 4 ? kernel_of<C, 32, 4>(ws) : nullptr;
+    switch (dtype) {
+    case RS_F32: return kernel_f32(C, jv, gv, ws);
+    case RS_F16: return kernel_f16(C, jv, gv, ws);
+    case RS_BF16: return kernel_bf16(C, jv, gv, ws);
     }
-    return nullptr;
-}
-
-const void *kernel_for(int C, int jv, int gv, bool ws)
-{
-    if (C == 1) return gv == 8 ? kernel_jv<1, 8>(jv, ws) : kernel_jv<1, 4>(jv, ws);
-    if (C == 3) return gv == 8 ? kernel_jv<3, 8>(jv, ws) : kernel_jv<3, 4>(jv, ws);
     return nullptr;
 }
 
@@ -73,10 +50,15 @@ int vertical_taps(const std::vector<int32_t> &sy, int t_eff, int GV)
     return 0;
 }
 
-int pad_pitch(int n) // multiple of 4 with n / 4 odd, >= n
+// Staged pitch >= n samples: a whole number of 16-byte words per row (TMA),
+// odd in 16-byte words so that lanes on consecutive rows reading 16 bytes
+// (FP32) hit distinct banks; 16-bit rows are read 8 bytes at a time and meet
+// 2-way conflicts at best.
+int pad_pitch(int n, int es)
 {
-    int p = (n + 3) / 4 * 4;
-    if ((p / 4) % 2 == 0) p += 4;
+    const int u = 16 / es; // samples per 16-byte word
+    int p = (n + u - 1) / u * u;
+    if ((p / u) % 2 == 0) p += u;
     return p;
 }
 
@@ -98,6 +80,7 @@ struct Strip {
 std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, const std::vector<int32_t> &hb,
                           int JH, int JV, int GV, int WP, const std::vector<int32_t> &vb, int pairs)
 {
+    const int dtype = p->desc.in_dtype, es = dt_size(dtype);
     // unless the caller fixes the form: groups of 8 rows (narrow vertical
     // bands) run the phase-alternating kernel with 2 staged blocks, groups of
     // 4 (wide bands) the warp-specialised one -- the faster form of each as
@@ -117,17 +100,19 @@ std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, 
                 int need = 0;
                 for (int g0 = 0; g0 < groups_x; g0 += ngx) {
                     const int gl = std::min(groups_x, g0 + ngx) - 1;
-                    need = std::max(need, (hb[gl] + JH - hb[g0]) * C);
+                    // (16-bit boxes start up to 4 samples before the first band)
+                    need = std::max(need, (hb[gl] + JH - hb[g0]) * C + (es == 2 ? 4 : 0));
                 }
                 int pp = 0, ob = 0;
                 if (pass != 1) {
-                    pp = pad_pitch(need);
+                    pp = pad_pitch(need, es);
                     if (pp > 256) pp = 0;
                 } else {
                     // boxes A = [0, P) and B = [ob, ob + P) of the strip's samples:
                     // ob <= P - JH C (overlap of a band) and ob + P >= need
-                    for (int cand = pad_pitch((need + JH * C + 1) / 2); cand <= 256 && !pp; cand += 8) {
-                        const int o = (cand - JH * C) / 4 * 4;
+                    const int u = 16 / es;
+                    for (int cand = pad_pitch((need + JH * C + 1) / 2, es); cand <= 256 && !pp; cand += 2 * u) {
+                        const int o = (cand - JH * C) / u * u;
                         if (o > 0 && o + cand >= need) {
                             pp = cand;
                             ob = o;
@@ -137,8 +122,8 @@ std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, 
                 if (pp == 0) continue;
                 const int qq = (hr + M) | 1; // odd: the vertical pass's 16-byte loads are conflict-free
                 for (int ni = kMaxNI; ni >= 2; --ni) {
-                    const size_t t = ws ? layout_ws(ni, 2, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total
-                                        : layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV).total;
+                    const size_t t = ws ? layout_ws(ni, 2, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV, es).total
+                                        : layout(ni, pp, qq, sw * C / 4, ngx, JH, WP, JV, ob != 0, GV, es).total;
                     if (t <= 113 * 1024 && (ni >= opts.ni_min || pass > 0)) {
                         out.push_back({sw, pp, ob, qq, ni, ws ? 2 : 0, hr, 0, 0, t, 0.0});
                         break;
@@ -155,7 +140,7 @@ std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, 
     };
     std::vector<Strip> ok;
     for (Strip c : out) {
-        const void *fn = kernel_for(C, JV, GV, c.NW != 0);
+        const void *fn = kernel_for(dtype, C, JV, GV, c.NW != 0);
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, fn, kThreads, c.smem) != cudaSuccess || c.occ < 1) {
             cudaGetLastError();
@@ -201,7 +186,9 @@ rs_status bands_of(const rs_plan *p, Bands &b)
 {
     const rs_plan_desc &d = p->desc;
     b.C = d.channels;
-    if (d.in_dtype != RS_F32 || (b.C != 1 && b.C != 3) || (d.flags & RS_NO_STREAM)) return RS_ERR_UNSUPPORTED;
+    if ((d.in_dtype != RS_F32 && d.in_dtype != RS_F16 && d.in_dtype != RS_BF16) || d.out_dtype != d.in_dtype ||
+        (b.C != 1 && b.C != 3) || (d.flags & RS_NO_STREAM))
+        return RS_ERR_UNSUPPORTED;
     if (!tma_layout_ok(p)) return RS_ERR_UNSUPPORTED;
     const std::vector<int32_t> &sx = p->host_start_x, &sy = p->host_start_y;
     const AxisGeom &gx = p->gx, &gy = p->gy;
@@ -280,7 +267,7 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
     const size_t smem = pick->smem;
     const int ngx = SW / kG;
     const int n_strips = (groups_x + ngx - 1) / ngx;
-    const void *fn = kernel_for(C, JV, GV, NW != 0);
+    const void *fn = kernel_for(d.in_dtype, C, JV, GV, NW != 0);
     cudaError_t e = cudaSuccess;
 
     // device tables: horizontal base + band, vertical base + band
@@ -387,18 +374,22 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s)
     const rs_plan_desc &d = p->desc;
     if (p->stmap_ptr != d_in) {
         cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};
-        cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * 4)};
+        const int es = dt_size(d.in_dtype);
+        cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * es)};
         cuuint32_t box[2] = {cuuint32_t(p->sp.P), cuuint32_t(kRB)};
         cuuint32_t estr[2] = {1, 1};
-        CUresult r = encode_fn()(&p->stmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(d_in), dims,
+        const CUtensorMapDataType ty = d.in_dtype == RS_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                       : d.in_dtype == RS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        CUresult r = encode_fn()(&p->stmap, ty, 2, const_cast<void *>(d_in), dims,
                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(RS_ERR_CUDA, "stream tensor map encoding failed");
         p->stmap_ptr = d_in;
     }
     Params sp = p->sp;
-    sp.in = static_cast<const float *>(d_in);
-    sp.out = static_cast<float *>(d_out);
+    sp.in = d_in;
+    sp.out = d_out;
     void *args[2] = {&p->stmap, &sp};
     cudaError_t e = cudaLaunchKernel(p->s_fn, dim3(p->s_grid), dim3(kThreads), args, p->s_smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "stream kernel launch");

@@ -23,6 +23,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "rs_fused.cuh"
 
 namespace rs {
@@ -41,8 +44,8 @@ __host__ __device__ constexpr int vtap_floats(int GV) { return GV == 4 ? 8 : GV;
 constexpr int kMaxNI = 4;
 
 struct Params {
-    const float *in;
-    float *out;
+    const void *in; // the image in its storage type (FP32, FP16 or BF16)
+    void *out;
     int64_t in_h, in_w, out_h, out_w;
     int64_t in_stride, out_stride;
     const int32_t *hbase; // [groups_x] first input pixel of each horizontal group (multiple of 4)
@@ -52,7 +55,7 @@ struct Params {
     int32_t JH, JV;       // horizontal taps (multiple of 4), vertical taps (multiple of 2)
     int32_t SW;           // output pixels per strip (multiple of 4)
     int32_t n_strips, pairs, pairs_per_range, groups_x;
-    int32_t P;            // staged input pitch in samples (P / 4 odd)
+    int32_t P;            // staged input pitch in samples (FP32: P / 4 odd; 16-bit: P / 8 odd)
     int32_t offB;         // 0: one staged box of P x 32 samples per block; else a second box
                           //    P x 32 starting offB samples further (rows wider than one
                           //    256-element box), in its own 128-byte aligned sub-buffer
@@ -76,10 +79,10 @@ struct Layout {
 };
 
 __host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx, int JH, int WP, int JV,
-                                         bool two_boxes, int GV)
+                                         bool two_boxes, int GV, int es)
 {
     Layout L;
-    L.in_blk = size_t(kRB) * P * 4 * (two_boxes ? 2 : 1);
+    L.in_blk = size_t(kRB) * P * es * (two_boxes ? 2 : 1);
     L.wv = size_t(WP) * JV * vtap_floats(GV) * 4;
     L.vb = fused::align_up(size_t(WP + 8) * 4, 16);
     L.slot = fused::align_up(L.in_blk + L.wv + L.vb, 128);
@@ -91,13 +94,67 @@ __host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx,
     return L;
 }
 
+// 4 consecutive staged samples as floats: one 16-byte load (FP32) or one
+// 8-byte load converted (FP16 / BF16).
+template <typename T> __device__ __forceinline__ float4 load4(const T *p);
+template <> __device__ __forceinline__ float4 load4<float>(const float *p)
+{
+    return *reinterpret_cast<const float4 *>(p);
+}
+template <> __device__ __forceinline__ float4 load4<__half>(const __half *p)
+{
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <> __device__ __forceinline__ float4 load4<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// 4 consecutive output samples, rounded to nearest in the storage type: one
+// 16-byte store (FP32) or one 8-byte store (FP16 / BF16).
+template <typename T> __device__ __forceinline__ void store4(T *p, float a, float b, float c, float d);
+template <> __device__ __forceinline__ void store4<float>(float *p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+template <> __device__ __forceinline__ void store4<__half>(__half *p, float a, float b, float c, float d)
+{
+    const __half2 x = __floats2half2_rn(a, b), y = __floats2half2_rn(c, d);
+    *reinterpret_cast<uint2 *>(p) = make_uint2(*reinterpret_cast<const uint32_t *>(&x),
+                                               *reinterpret_cast<const uint32_t *>(&y));
+}
+template <> __device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16 *p, float a, float b, float c, float d)
+{
+    const __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+    *reinterpret_cast<uint2 *>(p) = make_uint2(*reinterpret_cast<const uint32_t *>(&x),
+                                               *reinterpret_cast<const uint32_t *>(&y));
+}
+template <typename T> __device__ __forceinline__ T round_to(float v);
+template <> __device__ __forceinline__ float round_to<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half round_to<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 round_to<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// First staged sample of a strip whose first band starts at sample x0 (a
+// multiple of 4): a TMA box must start on a 16-byte boundary, so 16-bit
+// strips start up to 4 samples early.
+template <typename T> __host__ __device__ __forceinline__ int first_staged(int x0)
+{
+    return sizeof(T) == 2 ? (x0 & ~7) : x0;
+}
+
 // Horizontal pass of one 4-output group for the 32 rows of a staged block:
 // lane = row; rowp = the lane's staged row, hs = its ring slot.
-template <int C>
-__device__ __forceinline__ void h_group(const float *rowp, int cbq, const float *hbq, int JH, float4 *hring, int q,
+template <typename T, int C>
+__device__ __forceinline__ void h_group(const T *rowp, int cbq, const float *hbq, int JH, float4 *hring, int q,
                                         int Q, int HR, int M, int hs)
 {
-    const float4 *src = reinterpret_cast<const float4 *>(rowp + cbq);
+    const T *src = rowp + cbq;
     const float4 *wq = reinterpret_cast<const float4 *>(hbq);
     float acc[kG][C];
 #pragma unroll
@@ -109,13 +166,13 @@ __device__ __forceinline__ void h_group(const float *rowp, int cbq, const float 
         float d[4 * C];
 #pragma unroll
         for (int v = 0; v < C; ++v) {
-            const float4 x = src[v];
+            const float4 x = load4<T>(src + 4 * v);
             d[4 * v] = x.x;
             d[4 * v + 1] = x.y;
             d[4 * v + 2] = x.z;
             d[4 * v + 3] = x.w;
         }
-        src += C;
+        src += 4 * C;
         // ... times the 4 outputs' weights at those pixels (warp-uniform)
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -149,8 +206,8 @@ __device__ __forceinline__ void h_group(const float *rowp, int cbq, const float 
 
 // Vertical pass of one row group (GV output rows) for one 4-sample column:
 // src4 = the column's first tap row in the ring, wv = the group's weights.
-template <int JV, int GV>
-__device__ __forceinline__ void v_task(const float4 *src4, const float4 *wv, float *out, int64_t out_stride,
+template <typename T, int JV, int GV>
+__device__ __forceinline__ void v_task(const float4 *src4, const float4 *wv, T *out, int64_t out_stride,
                                        int64_t y0, int64_t out_h, int64_t sx, int64_t row_samples, bool vec_ok)
 {
     float a[GV][4];
@@ -204,22 +261,21 @@ __device__ __forceinline__ void v_task(const float4 *src4, const float4 *wv, flo
             }
         }
     }
-    float *o = out + y0 * out_stride + sx;
+    T *o = out + y0 * out_stride + sx;
     if (y0 + GV <= out_h && sx + 4 <= row_samples && vec_ok) {
-        // whole rows of 4 samples: 16-byte stores
+        // whole rows of 4 samples: 16-byte (FP32) or 8-byte (16-bit) stores
 #pragma unroll
-        for (int h = 0; h < GV; ++h)
-            *reinterpret_cast<float4 *>(o + h * out_stride) = make_float4(a[h][0], a[h][1], a[h][2], a[h][3]);
+        for (int h = 0; h < GV; ++h) store4<T>(o + h * out_stride, a[h][0], a[h][1], a[h][2], a[h][3]);
     } else {
 #pragma unroll
         for (int h = 0; h < GV; ++h) {
             if (y0 + h >= out_h) break;
-            for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[h * out_stride + i] = a[h][i];
+            for (int i = 0; i < 4 && sx + i < row_samples; ++i) o[h * out_stride + i] = round_to<T>(a[h][i]);
         }
     }
 }
 
-template <int C, int JV, int GV>
+template <typename T, int C, int JV, int GV>
 __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -227,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     const int ngx = p.SW / kG;
     const int JH = p.JH, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, WP = p.WP;
     const int nch = (p.SW * C) / 4; // 4-sample columns of a filtered row
-    const Layout L = layout(NI, P, Q, nch, ngx, JH, WP, JV, p.offB != 0, GV);
+    const Layout L = layout(NI, P, Q, nch, ngx, JH, WP, JV, p.offB != 0, GV, int(sizeof(T)));
     unsigned char *slots = smem;
     // filtered rows, column-major in 4-sample columns: [nch][Q] float4, so the
     // vertical taps of a column are consecutive 16-byte words
@@ -238,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     unsigned char *ctl = smem + NI * L.slot + L.hring + L.hb + L.cb + L.pe;
     uint64_t *full = reinterpret_cast<uint64_t *>(ctl); // [kMaxNI]
     volatile int *abort_flag = reinterpret_cast<volatile int *>(ctl + 8 * kMaxNI);
-    auto slot_in = [&](int s) { return reinterpret_cast<float *>(slots + s * L.slot); };
+    auto slot_in = [&](int s) { return reinterpret_cast<T *>(slots + s * L.slot); };
     auto slot_wv = [&](int s) { return reinterpret_cast<const ulonglong2 *>(slots + s * L.slot + L.in_blk); };
     auto slot_vb = [&](int s) { return reinterpret_cast<const int32_t *>(slots + s * L.slot + L.in_blk + L.wv); };
 
@@ -249,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     if (p0 >= p1) return;
     const int g0 = strip * ngx;
     const int ngv = min(ngx, p.groups_x - g0); // groups of the strip inside the image
-    const int xs = __ldg(p.hbase + g0) * C;    // first staged sample (multiple of 4)
+    const int xs = first_staged<T>(__ldg(p.hbase + g0) * C); // first staged sample (16-byte aligned)
     const int r_lo = __ldg(p.vbase + p0);
     const int r_hi = __ldg(p.vbase + p1 - 1) + JV;
     const int nblk = min((r_hi - r_lo + kRB - 1) / kRB, kMaxBlk);
@@ -313,8 +369,9 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
 
     const int64_t row_samples = p.out_w * C;
     const int64_t x0s = int64_t(strip) * p.SW * C; // first output sample of the strip
-    // 16-byte stores need a 16-byte aligned output and row pitch (chunks are 4 samples)
-    const bool vec_ok = ((reinterpret_cast<uintptr_t>(p.out) | uintptr_t(p.out_stride * 4)) & 15u) == 0;
+    // vector stores of 4 samples need an aligned output and row pitch
+    const bool vec_ok =
+        ((reinterpret_cast<uintptr_t>(p.out) | uintptr_t(p.out_stride * sizeof(T))) & (4 * sizeof(T) - 1)) == 0;
     int k = 0;
     for (; k < nblk; ++k) {
         const int slot = k % NI;
@@ -324,9 +381,9 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
         if (landed) {
             int hs = base_k + lane;
             if (hs >= HR) hs -= HR;
-            const float *rowp = slot_in(slot) + size_t(lane) * P;
+            const T *rowp = slot_in(slot) + size_t(lane) * P;
             for (int q = warp; q < ngv; q += kWarps)
-                h_group<C>(rowp, cb[q], hb + q * JH * kG, JH, hring, q, Q, HR, M, hs);
+                h_group<T, C>(rowp, cb[q], hb + q * JH * kG, JH, hring, q, Q, HR, M, hs);
         }
         // every thread agrees on whether the block landed (a timeout stops all)
         if (!__syncthreads_and(landed ? 1 : 0)) break;
@@ -345,8 +402,9 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
                 int hs0 = base_k + (vbs[pr] - r_lo - k * kRB);
                 if (hs0 < 0) hs0 += HR;
                 if (hs0 >= HR) hs0 -= HR;
-                v_task<JV, GV>(hring + ch * Q + hs0,
-                               reinterpret_cast<const float4 *>(wvs) + po * JV * (vtap_floats(GV) / 4), p.out,
+                v_task<T, JV, GV>(hring + ch * Q + hs0,
+                                  reinterpret_cast<const float4 *>(wvs) + po * JV * (vtap_floats(GV) / 4),
+                                  static_cast<T *>(p.out),
                                p.out_stride, int64_t(GV) * pr, p.out_h, x0s + int64_t(ch) * 4, row_samples, vec_ok);
                 po += dpo;
                 ch += dch;
@@ -384,10 +442,10 @@ struct LayoutWS {
 };
 
 __host__ __device__ inline LayoutWS layout_ws(int NI, int NW, int P, int Q, int nch, int ngx, int JH, int WP, int JV,
-                                              bool two_boxes, int GV)
+                                              bool two_boxes, int GV, int es)
 {
     LayoutWS L;
-    L.in_blk = size_t(kRB) * P * 4 * (two_boxes ? 2 : 1);
+    L.in_blk = size_t(kRB) * P * es * (two_boxes ? 2 : 1);
     L.in_ring = size_t(NI) * L.in_blk; // in_blk is a multiple of 128 bytes
     L.wv = size_t(WP) * JV * vtap_floats(GV) * 4;
     L.vb = fused::align_up(size_t(WP + 8) * 4, 16);
@@ -414,7 +472,7 @@ __device__ __forceinline__ bool group_and(int id, int threads, bool v)
     return r != 0;
 }
 
-template <int C, int JV, int GV>
+template <typename T, int C, int JV, int GV>
 __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                   const Params p)
 {
@@ -423,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
     const int ngx = p.SW / kG;
     const int JH = p.JH, P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, NW = p.NW, WP = p.WP;
     const int nch = (p.SW * C) / 4;
-    const LayoutWS L = layout_ws(NI, NW, P, Q, nch, ngx, JH, WP, JV, p.offB != 0, GV);
+    const LayoutWS L = layout_ws(NI, NW, P, Q, nch, ngx, JH, WP, JV, p.offB != 0, GV, int(sizeof(T)));
     unsigned char *in_ring = smem;
     unsigned char *w_ring = smem + L.in_ring;
     float4 *hring = reinterpret_cast<float4 *>(w_ring + L.w_ring);
@@ -433,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
     uint64_t *bars = reinterpret_cast<uint64_t *>(w_ring + L.w_ring + L.hring + L.hb + L.cb + L.pe);
     uint64_t *full_in = bars, *full_w = bars + kMaxNI, *hdone = bars + 2 * kMaxNI, *vdone = hdone + 2;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(vdone + 2);
-    auto slot_in = [&](int s) { return reinterpret_cast<float *>(in_ring + s * L.in_blk); };
+    auto slot_in = [&](int s) { return reinterpret_cast<T *>(in_ring + s * L.in_blk); };
     auto slot_wv = [&](int s) { return reinterpret_cast<const float4 *>(w_ring + s * L.wslot); };
     auto slot_vb = [&](int s) { return reinterpret_cast<const int32_t *>(w_ring + s * L.wslot + L.wv); };
 
@@ -445,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
     if (p0 >= p1) return;
     const int g0 = strip * ngx;
     const int ngv = min(ngx, p.groups_x - g0);
-    const int xs = __ldg(p.hbase + g0) * C;
+    const int xs = first_staged<T>(__ldg(p.hbase + g0) * C);
     const int r_lo = __ldg(p.vbase + p0);
     const int r_hi = __ldg(p.vbase + p1 - 1) + JV;
     const int nblk = min((r_hi - r_lo + kRB - 1) / kRB, kMaxBlk);
@@ -525,9 +583,9 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
             const int base_k = (k * kRB) % HR;
             int hs = base_k + lane;
             if (hs >= HR) hs -= HR;
-            const float *rowp = slot_in(slot) + size_t(lane) * P;
+            const T *rowp = slot_in(slot) + size_t(lane) * P;
             for (int q = warp; q < ngv; q += kHWarps)
-                h_group<C>(rowp, cb[q], hb + q * JH * kG, JH, hring, q, Q, HR, M, hs);
+                h_group<T, C>(rowp, cb[q], hb + q * JH * kG, JH, hring, q, Q, HR, M, hs);
             fused::named_sync(1, kHThreads); // the staged block is consumed
             if (tid == 0 && k + NI < nblk) issue_in(k + NI);
             fused::mbar_arrive(&hdone[k & 1]);
@@ -539,7 +597,8 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
             for (int b = 0; b < NW && b < nblk; ++b) issue_w(b);
         const int64_t row_samples = p.out_w * C;
         const int64_t x0s = int64_t(strip) * p.SW * C;
-        const bool vec_ok = ((reinterpret_cast<uintptr_t>(p.out) | uintptr_t(p.out_stride * 4)) & 15u) == 0;
+        const bool vec_ok =
+            ((reinterpret_cast<uintptr_t>(p.out) | uintptr_t(p.out_stride * sizeof(T))) & (4 * sizeof(T) - 1)) == 0;
         for (; k < nblk; ++k) {
             const int wslot = k % NW;
             bool good = fused::wait_or_abort(&full_w[wslot], uint32_t((k / NW) & 1), abort_flag, p.err);
@@ -561,7 +620,8 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
                 int hs0 = base_k + (vbs[pr] - r_lo - k * kRB);
                 if (hs0 < 0) hs0 += HR;
                 if (hs0 >= HR) hs0 -= HR;
-                v_task<JV, GV>(hring + ch * Q + hs0, wvs + po * JV * (vtap_floats(GV) / 4), p.out, p.out_stride,
+                v_task<T, JV, GV>(hring + ch * Q + hs0, wvs + po * JV * (vtap_floats(GV) / 4), static_cast<T *>(p.out),
+                                  p.out_stride,
                                int64_t(GV) * pr, p.out_h, x0s + int64_t(ch) * 4, row_samples, vec_ok);
                 po += dpo;
                 ch += dch;
@@ -584,6 +644,48 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
             for (int b = k; b < nblk && b < k + NW; ++b) fused::mbar_wait_bounded(&full_w[b % NW], uint32_t((b / NW) & 1));
     }
 }
+
+// ---------------------------------------------------------------------------
+// Instantiated kernels: storage type x channels x vertical taps x rows per
+// vertical group (a plan's band is padded with zero weights to the next
+// instantiated width): groups of 8 rows up to 16 taps, groups of 4 up to 32.
+// One translation unit per storage type instantiates its table.
+
+template <typename T, int C, int JV, int GV> const void *kernel_of(bool ws)
+{
+    return ws ? reinterpret_cast<const void *>(&stream_ws_kernel<T, C, JV, GV>)
+              : reinterpret_cast<const void *>(&stream_kernel<T, C, JV, GV>);
+}
+
+template <typename T, int C, int GV> const void *kernel_jv(int jv, bool ws)
+{
+    switch (jv) {
+    case 4: return GV == 4 ? kernel_of<T, C, 4, 4>(ws) : nullptr;
+    case 6: return GV == 4 ? kernel_of<T, C, 6, 4>(ws) : nullptr;
+    case 8: return kernel_of<T, C, 8, GV>(ws);
+    case 10: return kernel_of<T, C, 10, GV>(ws);
+    case 12: return kernel_of<T, C, 12, GV>(ws);
+    case 14: return kernel_of<T, C, 14, GV>(ws);
+    case 16: return kernel_of<T, C, 16, GV>(ws);
+    case 20: return GV == 4 ? kernel_of<T, C, 20, 4>(ws) : nullptr;
+    case 24: return GV == 4 ? kernel_of<T, C, 24, 4>(ws) : nullptr;
+    case 28: return GV == 4 ? kernel_of<T, C, 28, 4>(ws) : nullptr;
+    case 32: return GV == 4 ? kernel_of<T, C, 32, 4>(ws) : nullptr;
+    }
+    return nullptr;
+}
+
+template <typename T> const void *kernel_table(int C, int jv, int gv, bool ws)
+{
+    if (C == 1) return gv == 8 ? kernel_jv<T, 1, 8>(jv, ws) : kernel_jv<T, 1, 4>(jv, ws);
+    if (C == 3) return gv == 8 ? kernel_jv<T, 3, 8>(jv, ws) : kernel_jv<T, 3, 4>(jv, ws);
+    return nullptr;
+}
+
+// defined in rs_stream_f32.cu, rs_stream_f16.cu, rs_stream_bf16.cu
+const void *kernel_f32(int C, int jv, int gv, bool ws);
+const void *kernel_f16(int C, int jv, int gv, bool ws);
+const void *kernel_bf16(int C, int jv, int gv, bool ws);
 
 } // namespace stream
 } // namespace rs

@@ -119,13 +119,17 @@ def main():
                            rs.RS_TWO_PASS))
     rows.append(full_image(rs, "256x256 x2 Keys clamp", c1, "f32", 512, 512, "cubic", "clamp", -0.5))
     big = synth.sinusoids(4096, 4096, 3, seed=synth.SEED_C2)
+    tile = rs.RS_FORCE_SIMT | rs.RS_NO_STREAM
     for s in (1.37, 0.3):
         rows.append(sampled(rs, "4096x4096x3 x%g Lanczos-3" % s, big, "f32", s, 0, a.rows))
+        rows.append(sampled(rs, "4096x4096x3 x%g Lanczos-3" % s, big, "f32", s, tile, a.rows))
     for dt in ("bf16", "f16"):
         for s in (1.37, 0.3, 0.125):
+            # the default kernel, then the other kernels that apply
             rows.append(sampled(rs, "4096x4096x3 x%g Lanczos-3" % s, big, dt, s, 0, a.rows))
-            if s < 1:
-                rows.append(sampled(rs, "4096x4096x3 x%g Lanczos-3" % s, big, dt, s, rs.RS_FORCE_SIMT, a.rows))
+            rows.append(sampled(rs, "4096x4096x3 x%g Lanczos-3" % s, big, dt, s, tile, a.rows))
+            if s == 0.3:
+                rows.append(sampled(rs, "4096x4096x3 x%g Lanczos-3" % s, big, dt, s, rs.RS_FORCE_STREAM, a.rows))
     rows.append(batch_rows(rs, a.batch_n))
     print("| configuration | storage | path | max abs error | RMS error |")
     print("|---|---|---|---|---|")

@@ -4,7 +4,10 @@ FP32 images of 1 and 3 channels, every kernel and boundary, upscales and mild
 downscales with ragged strips and row ranges, forced onto the streaming kernel
 and kept off it; the fallback to the tile kernel for an unaligned input; the
 4096x4096x3 x1.37 configuration on sampled rows; recompute and autotune.
-Tolerance FP32 2e-6 (max-abs on [0, 1] data).
+FP16 / BF16 storage (FP32 filtering, rounded stores) on the same cases where
+rows are whole 16-byte words, and the 4096x4096x3 x1.37 / x0.3 cases on
+sampled rows.  Tolerances FP32 2e-6, FP16 2e-3, BF16 1e-2 (max-abs on [0, 1]
+data, the oracle fed the same quantised input).
 """
 import numpy as np
 import pytest
@@ -75,8 +78,11 @@ def test_stream_is_default_for_fp32_upscale(rs):
     p = rs.Plan(4096, 4096, 3, scale=0.125, kernel="lanczos", param=3.0, boundary="mirror")
     assert p.path == "fused"   # band too wide for the streaming kernel
     p.close()
-    with pytest.raises(RuntimeError, match="unsupported"):
-        rs.Plan(64, 64, 3, 100, 100, kernel="lanczos", param=3.0, boundary="mirror", dtype=torch.bfloat16,
+    with pytest.raises(RuntimeError, match="unsupported"):   # FP64 is not streamed
+        rs.Plan(64, 64, 3, 100, 100, kernel="lanczos", param=3.0, boundary="mirror", dtype=torch.float64,
+                flags=rs.RS_FORCE_STREAM)
+    with pytest.raises(RuntimeError, match="unsupported"):   # 61 x 3 16-bit samples: not whole 16-byte rows
+        rs.Plan(64, 61, 3, 100, 100, kernel="lanczos", param=3.0, boundary="mirror", dtype=torch.bfloat16,
                 flags=rs.RS_FORCE_STREAM)
 
 
@@ -189,3 +195,83 @@ def test_autotune_chooses_between_stream_and_tiles(rs, tmp_path):
     q.autotune(x, out, cache_path=cache)
     assert q.path == first
     q.close()
+
+
+# 16-bit rows must be whole 16-byte words (W * C a multiple of 8) for TMA
+SHAPES16 = [((67, 96), (150, 203)),    # x2.2, ragged strips
+            ((96, 136), (131, 181)),   # ~x1.37
+            ((300, 400), (411, 548)),  # x1.37, several row ranges
+            ((33, 40), (33, 40)),      # identity
+            ((64, 104), (50, 77)),     # mild downscale
+            ((40, 400), (90, 999)),    # wide, many strips
+            ((200, 24), (401, 37)),    # tall, one strip
+            ((300, 400), (90, 120)),   # x0.3: wide strips (two boxes per staged row)
+            ((257, 616), (77, 183))]   # ~x0.3, ragged
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+@pytest.mark.parametrize("shape", SHAPES16, ids=[f"{a[0]}x{a[1]}-{b[0]}x{b[1]}" for a, b in SHAPES16])
+@pytest.mark.parametrize("kernel,param", [("linear", None), ("cubic", -0.5), ("lanczos", 3.0),
+                                          ("bspline3", None)])
+@pytest.mark.parametrize("boundary", ["clamp", "mirror", "reflect101", "truncate"])
+@pytest.mark.parametrize("C", [1, 3])
+def test_stream_parity_16bit(rs, dt, shape, kernel, param, boundary, C):
+    (H, W), (OH, OW) = shape
+    img = synth.uniform(H, W, C, seed=(H * 37 + W * 11 + C) & 0xffff)
+    t, exact = quantise(img, dt)
+    want = oracle.resample(exact, OH, OW, kernel, boundary, param=param)
+    try:
+        got, info = run_gpu(t, OH, OW, kernel, boundary, param, rs.RS_FORCE_STREAM)
+    except RuntimeError as e:
+        assert "unsupported" in str(e) and OH < H, e
+        return
+    assert info.path == 3
+    err = np.abs(got - want).max()
+    assert err <= TOL[dt], (err, info.tile_w)
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+def test_stream_16bit_matches_tile_kernel(rs, dt):
+    """Both kernels filter in FP32 and round once: they agree to one rounding step."""
+    img = synth.sinusoids(240, 320, 3, seed=9)
+    t, exact = quantise(img, dt)
+    a, ia = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_STREAM, scale=1.37)
+    b, ib = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_NO_STREAM | rs.RS_FORCE_SIMT, scale=1.37)
+    assert (ia.path, ib.path) == (3, 0)
+    ulp = 2.0 ** -8 if dt == "bf16" else 2.0 ** -11
+    assert np.abs(a - b).max() <= ulp
+    want = oracle.resample(exact, ia.out_h, ia.out_w, "lanczos", "mirror", param=3.0)
+    assert np.abs(a - want).max() <= TOL[dt]
+
+
+def test_stream_is_default_for_16bit_upscale(rs):
+    import torch
+
+    for dt in (torch.bfloat16, torch.float16):
+        p = rs.Plan(4096, 4096, 3, scale=1.37, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt)
+        assert p.path == "stream", (dt, p.path)
+        p.close()
+        # the wide antialiasing downscale keeps its tensor-core tiles unless forced
+        p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt)
+        assert p.path == "tcgen05", (dt, p.path)
+        p.close()
+        p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt,
+                    flags=rs.RS_FORCE_STREAM)
+        assert p.path == "stream", (dt, p.path)
+        p.close()
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+@pytest.mark.parametrize("scale,out", [(1.37, 5612), (0.3, 1229)])
+def test_stream_16bit_full_size_sampled_rows(rs, dt, scale, out):
+    """4096x4096x3 16-bit on the streaming kernel: sampled rows against the oracle."""
+    t, exact = quantise(synth.sinusoids(4096, 4096, 3, seed=synth.SEED_C2), dt)
+    got, info = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_STREAM, scale=scale)
+    assert info.path == 3 and (info.out_h, info.out_w) == (out, out)
+    g = np.random.default_rng(7)
+    rows = sorted(set([0, 1, out // 2, out - 2, out - 1]) | set(int(r) for r in g.integers(0, out, 8)))
+    err = 0.0
+    for r in rows:
+        want = oracle.resample(exact, out, out, "lanczos", "mirror", param=3.0, rows=(r, r + 1))
+        err = max(err, float(np.abs(got[r] - want[0]).max()))
+    assert err <= TOL[dt], err

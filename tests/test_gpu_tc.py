@@ -114,12 +114,16 @@ def test_tc_chosen_automatically_for_wide_16bit(rs):
             p = rs.Plan(4096, 4096, 3, scale=s, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt)
             assert p.path == "tcgen05", (dt, s, p.path)
             p.close()
-        # narrow: the SIMT kernel
+        # narrow: the SIMT streaming kernel
         p = rs.Plan(4096, 4096, 3, scale=1.37, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt)
-        assert p.path == "fused"
+        assert p.path == "stream"
         p.close()
         p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt,
                     flags=rs.RS_FORCE_SIMT)
+        assert p.path == "stream"
+        p.close()
+        p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt,
+                    flags=rs.RS_FORCE_SIMT | rs.RS_NO_STREAM)
         assert p.path == "fused"
         p.close()
     p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=torch.float32)
@@ -156,7 +160,7 @@ def test_tc_matches_simt_path(rs, dt):
     img = synth.sinusoids(480, 640, 3, seed=8)
     t, exact = quantise(img, dt)
     a, ia = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, 0, scale=0.3)
-    b, ib = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_SIMT, scale=0.3)
+    b, ib = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_SIMT | rs.RS_NO_STREAM, scale=0.3)
     assert (ia.path, ib.path) == (2, 0)
     assert np.abs(a - b).max() <= TOL[dt]
     want = oracle.resample(exact, ia.out_h, ia.out_w, "lanczos", "mirror", param=3.0)
