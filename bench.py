@@ -298,7 +298,7 @@ def batched_section(args, dev, stream):
                                      "launches": len(specs)},
             "speedup_vs_plain_fp32": ms_plain / ms_batch,
             "max_abs_diff_fp16_vs_fp32_path": diff, "create_s": round(create_s, 2), "autotune_s": round(tune_s, 2),
-            "config": {"group": info.group, "warps_pass1": info.warps_pass1, "stages": info.stages,
+            "config": {"streamed_images": info.n_streamed, "group": info.group, "warps_pass1": info.warps_pass1, "stages": info.stages,
                        "use_tma": info.use_tma, "smem": info.smem_bytes, "ctas_per_sm": info.ctas_per_sm,
                        "tiles": info.total_tiles}}
 

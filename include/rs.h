@@ -242,7 +242,12 @@ RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in,
  * batch.  Work items are (image, output tile) pairs of the concatenated tile
  * list, dealt round-robin to the persistent CTAs, so every image's tiles
  * spread over the whole GPU.  The launch (parameter upload, kernel) is a CUDA
- * graph built at creation and replayed by rs_batch_run.
+ * graph built at creation and replayed by rs_batch_run.  In a batch planned
+ * for TMA, images of at least 2^20 output pixels that the row-streaming
+ * kernel takes leave the tile list and run on that kernel instead, one launch
+ * each, largest first, spread over four side streams that are forked from
+ * and joined back into the caller's stream around the graph (so they overlap
+ * one another and the persistent kernel; rs_batch_info.n_streamed).
  * ---------------------------------------------------------------------- */
 typedef struct rs_batch rs_batch;
 
@@ -270,6 +275,7 @@ typedef struct {
     int32_t smem_bytes, ctas_per_sm, grid;
     int64_t out_pixels;          /* sum of out_h * out_w                      */
     int64_t in_bytes, out_bytes; /* algorithmic bytes: every input and output once */
+    int32_t n_streamed;          /* images on the row-streaming kernel        */
 } rs_batch_info;
 
 RS_API rs_status rs_batch_get_info(const rs_batch *batch, rs_batch_info *info);

@@ -71,7 +71,7 @@ class rs_batch_info(ctypes.Structure):
                 ("stages", ctypes.c_int32), ("use_tma", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("out_pixels", ctypes.c_int64),
-                ("in_bytes", ctypes.c_int64), ("out_bytes", ctypes.c_int64)]
+                ("in_bytes", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("n_streamed", ctypes.c_int32)]
 
 
 class rs_server_desc(ctypes.Structure):

@@ -1,5 +1,10 @@
 // rs_batch.cu -- batches of uneven images in one persistent fused launch.
 //
+// Images of at least kStreamMinOut output pixels that the row-streaming kernel
+// takes (TMA-planned batches) leave the tile list and run on it, one launch
+// each after the persistent kernel: on large upscales it is 2-4x faster than
+// the tile kernel, and a launch that large fills the GPU by itself.
+//
 // Each image gets an ordinary plan (exact taps, FP64 weight tables); the batch
 // then re-plans every image's fused configuration under one launch-wide
 // choice (kernel variant = group size G, warp split n1, staged-buffer count,
@@ -21,8 +26,16 @@
 
 using namespace rs;
 
+constexpr int64_t kStreamMinOut = int64_t(1) << 20;
+constexpr int kAux = 4; // side streams the streamed images are spread over
+
 struct rs_batch {
     std::vector<rs_plan *> plans;
+    std::vector<char> streamed; // image i runs on the row-streaming kernel
+    int n_streamed = 0;
+    std::vector<int> stream_order; // streamed images, largest output first
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t fork = nullptr, join[kAux] = {};
     int dtype = 0, C = 0;
     // launch-wide choice
     int G = 0, n1 = 4, stages = 1, use_tma = 0, budget_ctas = 2;
@@ -52,6 +65,11 @@ struct rs_batch {
             if (done[k]) cudaEventDestroy(done[k]);
             if (host_stage[k]) cudaFreeHost(host_stage[k]);
         }
+        for (int k = 0; k < kAux; ++k) {
+            if (join[k]) cudaEventDestroy(join[k]);
+            if (aux[k]) cudaStreamDestroy(aux[k]);
+        }
+        if (fork) cudaEventDestroy(fork);
         for (rs_plan *p : plans) rs_destroy(p);
     }
 };
@@ -99,12 +117,20 @@ double plan_images(rs_batch *b, cudaStream_t stream, int G, int stages, int budg
     const size_t target = (227 * 1024) / size_t(budget_ctas);
     std::vector<Candidate> pick(b->plans.size());
     std::vector<std::vector<Candidate>> all(b->plans.size());
-    for (size_t i = 0; i < b->plans.size(); ++i) all[i] = enumerate_candidates(b->plans[i], b->use_tma != 0);
+    std::vector<rs_plan *> tiled;
+    std::vector<size_t> idx;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        if (b->streamed[i]) continue;
+        all[i] = enumerate_candidates(b->plans[i], b->use_tma != 0);
+        idx.push_back(i);
+    }
     double total = INFINITY;
     for (size_t cap = target; cap >= 8 * 1024; cap = cap * 85 / 100) {
         total = 0.0;
         bool ok = true;
-        for (size_t i = 0; i < b->plans.size() && ok; ++i) {
+        std::vector<Candidate> pk;
+        tiled.clear();
+        for (size_t i : idx) {
             const Candidate *best = nullptr;
             for (const Candidate &c : all[i]) {
                 if (c.G != G || c.stages != stages || c.smem > cap) continue;
@@ -115,14 +141,16 @@ double plan_images(rs_batch *b, cudaStream_t stream, int G, int stages, int budg
                 break;
             }
             pick[i] = *best;
+            pk.push_back(*best);
+            tiled.push_back(b->plans[i]);
             total += best->cost * double(b->plans[i]->gy.n_out) * double(b->plans[i]->gx.n_out);
         }
         if (!ok) return INFINITY;
-        if (combined_smem(pick, b->plans, b->dtype, b->use_tma ? stages : 1) <= target) break;
+        if (pk.empty() || combined_smem(pk, tiled, b->dtype, b->use_tma ? stages : 1) <= target) break;
         total = INFINITY;
     }
     if (!std::isfinite(total) || !apply) return total;
-    for (size_t i = 0; i < b->plans.size(); ++i) {
+    for (size_t i : idx) {
         Candidate c = pick[i];
         c.n1 = b->n1;
         *st = apply_fused(b->plans[i], stream, c, b->use_tma != 0);
@@ -141,7 +169,8 @@ rs_status build_launch(rs_batch *b, cudaStream_t stream)
     for (int i = 0; i < n; ++i) {
         const rs_plan *p = b->plans[i];
         const fused::Params &fp = p->fp;
-        off[i + 1] = off[i] + fp.tiles_y * fp.tiles_x;
+        off[i + 1] = off[i] + (b->streamed[i] ? 0 : fp.tiles_y * fp.tiles_x);
+        if (b->streamed[i]) continue;
         fused::Work r;
         work_regions(p, &r);
         w.tin_bytes = std::max(w.tin_bytes, r.tin_bytes);
@@ -169,7 +198,7 @@ rs_status build_launch(rs_batch *b, cudaStream_t stream)
     if (e != cudaSuccess) return cuda_fail(e, "batch: occupancy");
     if (occ < 1) return fail(RS_ERR_UNSUPPORTED, "batch: kernel does not fit on an SM");
     b->ctas = occ;
-    b->grid = int(std::min<int64_t>(b->total_tiles, int64_t(occ) * b->plans[0]->num_sms));
+    b->grid = int(std::max<int64_t>(1, std::min<int64_t>(b->total_tiles, int64_t(occ) * b->plans[0]->num_sms)));
 
     // device arrays (re)allocated for this configuration
     b->dparams.~DeviceBuf();
@@ -267,9 +296,10 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
     bool all_tma = true;
     for (int i = 0; i < n; ++i) {
         rs_plan_desc d = descs[i];
-        // one persistent launch runs every image on the SIMT kernel
+        // the persistent launch runs the images on the SIMT tile kernel; large
+        // ones may take the row-streaming kernel instead (decided below)
         d.flags &= ~uint32_t(RS_TWO_PASS | RS_FORCE_TC | RS_FORCE_STREAM);
-        d.flags |= RS_FORCE_SIMT | RS_NO_STREAM;
+        d.flags |= RS_FORCE_SIMT;
         rs_plan *p = nullptr;
         rs_status st = rs_plan_create(&d, stream, &p);
         if (st != RS_OK) {
@@ -289,6 +319,27 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
     b->use_tma = all_tma ? 1 : 0;
     cudaError_t e = cudaMalloc(&b->derr.p, 16);
     if (e == cudaSuccess) e = cudaMemset(b->derr.p, 0, 16);
+    b->streamed.assign(n, 0);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        rs_plan *p = b->plans[i];
+        if (b->use_tma && p->stream_ok && int64_t(p->gy.n_out) * p->gx.n_out >= kStreamMinOut) {
+            b->streamed[i] = 1;
+            ++b->n_streamed;
+            p->sp.err = static_cast<int *>(b->derr.p); // one error word for the whole batch
+            b->stream_order.push_back(i);
+        }
+    }
+    std::stable_sort(b->stream_order.begin(), b->stream_order.end(), [b](int x, int y) {
+        return int64_t(b->plans[x]->gy.n_out) * b->plans[x]->gx.n_out >
+               int64_t(b->plans[y]->gy.n_out) * b->plans[y]->gx.n_out;
+    });
+    if (e == cudaSuccess && b->n_streamed) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int k = 0; k < kAux && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+        }
+    }
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaHostAlloc(&b->host_stage[k], stage_bytes(n), cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming);
@@ -365,8 +416,30 @@ rs_status rs_batch_run(rs_batch *b, const void *const *d_in, void *const *d_out,
         b->staged_in[k][i] = d_in[i];
         b->staged_out[k][i] = d_out[i];
     }
+    if (b->n_streamed) {
+        // the streamed images, largest first, dealt over side streams forked
+        // from `stream` (after the work already queued there) and joined back
+        // after the graph, so they overlap one another and the persistent
+        // kernel (whose CTAs never wait on one another)
+        e = cudaEventRecord(b->fork, stream);
+        for (int a = 0; a < kAux && e == cudaSuccess; ++a) e = cudaStreamWaitEvent(b->aux[a], b->fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "batch: forking the side streams");
+    }
     e = cudaGraphLaunch(b->exec[k], stream);
-    if (e == cudaSuccess) e = cudaEventRecord(b->done[k], stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: graph launch");
+    if (b->n_streamed) {
+        for (size_t j = 0; j < b->stream_order.size(); ++j) {
+            const int i = b->stream_order[j];
+            const rs_status st = stream::launch(b->plans[i], d_in[i], d_out[i], b->aux[j % kAux]);
+            if (st != RS_OK) return st;
+        }
+        for (int a = 0; a < kAux && e == cudaSuccess; ++a) {
+            e = cudaEventRecord(b->join[a], b->aux[a]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->join[a], 0);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "batch: joining the side streams");
+    }
+    e = cudaEventRecord(b->done[k], stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch: graph launch");
     return RS_OK;
 }
@@ -488,6 +561,7 @@ rs_status rs_batch_get_info(const rs_batch *b, rs_batch_info *info)
     info->out_pixels = b->out_pixels;
     info->in_bytes = b->in_bytes;
     info->out_bytes = b->out_bytes;
+    info->n_streamed = b->n_streamed;
     return RS_OK;
 }
 

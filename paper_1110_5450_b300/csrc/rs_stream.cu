@@ -68,15 +68,17 @@ struct Strip {
     double cost;
 };
 
-// Every strip width (multiple of 4 outputs, at most 128) whose staged width
+// Every strip width (multiple of 4 outputs, at most 128; 252 for one channel) whose staged width
 // fits the TMA boxes and whose CTA keeps two CTAs per SM, for the first
 // staging form that admits any: the warp-specialised kernel first (its
 // filtered-row ring holds two blocks), then narrow strips with >= ni_min
 // staged blocks, wide strips (two boxes per block: the second starts early
 // enough that every group's band fits one of them), narrow with 2 blocks.
 // Each gets its row ranges and a modelled time: whole waves of CTAs, each
-// CTA's work (strip width plus a fixed share, rows of its range plus the
-// band and the pipeline fill); cheapest first.
+// CTA's work (strip width plus a fixed share worth 64 outputs -- the
+// per-block barriers, waits and task rounding, fitted to measured widths --
+// times the rows of its range plus the band and the pipeline fill); cheapest
+// first.
 std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, const std::vector<int32_t> &hb,
                           int JH, int JV, int GV, int WP, const std::vector<int32_t> &vb, int pairs)
 {
@@ -95,7 +97,7 @@ std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, 
         if (i == 1 && opts.ws >= 0) break; // a fixed form has no fallback
         const int hr = (ws ? 2 : 1) * kRB + JV;
         for (int pass = 0; pass < 3 && out.empty(); ++pass)
-            for (int sw = 128; sw >= 16; sw -= 4) {
+            for (int sw = C == 1 ? 252 : 128; sw >= 16; sw -= 4) {
                 const int ngx = sw / kG;
                 int need = 0;
                 for (int g0 = 0; g0 < groups_x; g0 += ngx) {
@@ -161,7 +163,7 @@ std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, 
             }
             const int64_t grid = int64_t(n_strips) * ranges;
             const int64_t waves = (grid + slots - 1) / slots;
-            const double cost = double(waves) * (c.sw + 8) * (rows + 2 * kRB);
+            const double cost = double(waves) * (c.sw + 64) * (rows + 2 * kRB);
             if (cost < c.cost * 0.999) {
                 c.cost = cost;
                 c.ppr = cand;
