@@ -672,7 +672,7 @@ std::string tune_key(const rs_plan *p)
 }
 
 bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int *tw, int *st, int *n1,
-                  int *use_stream)
+                  int *use_stream, int *tc)
 {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
@@ -688,6 +688,8 @@ bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int
             found = true; // the last matching line wins
             const char *r = std::strstr(line, "\"stream\":");
             *use_stream = (r && std::sscanf(r, "\"stream\": %d", use_stream) == 1) ? *use_stream : 0;
+            const char *t = std::strstr(line, "\"tc\":");
+            *tc = (t && std::sscanf(t, "\"tc\": %d", tc) == 1) ? *tc : -1; // -1: the plan's own choice
         }
     }
     std::fclose(f);
@@ -701,8 +703,8 @@ void cache_store(const char *path, const std::string &key, const Candidate &c, d
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"G\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, \"n1\": %d, "
-                 "\"band\": %d, \"us\": %.3f, \"stream\": %d}\n",
-                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us, use_stream);
+                 "\"band\": %d, \"us\": %.3f, \"stream\": %d, \"tc\": %d}\n",
+                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us, use_stream, c.tc);
     std::fclose(f);
 }
 
@@ -946,18 +948,25 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     if (p->path != 0) return RS_OK; // only the fused path has choices to tune
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     const bool tma = tma_layout_ok(p);
-    const bool tc = p->chosen.tc != 0;
+    const bool tc = p->chosen.tc != 0, force_tc = (p->desc.flags & RS_FORCE_TC) != 0;
+    // a tensor-core plan also times the SIMT tiles (and the streaming kernel)
+    // unless the tensor cores were forced
     std::vector<Candidate> cands = enumerate_candidates(p, tma, tc);
+    if (tc && !force_tc) {
+        const std::vector<Candidate> simt = enumerate_candidates(p, tma, false);
+        cands.insert(cands.end(), simt.begin(), simt.end());
+    }
     if (cands.empty()) return RS_OK;
     const std::string key = tune_key(p);
     // the tile configurations are timed on the tile kernel; the streaming
     // kernel (if any) is compared with the winner at the end
-    const int stream_ok = p->stream_ok;
+    const int stream_ok = p->stream_ok && !force_tc;
     p->use_stream = 0;
-    int G, th, tw, st, n1, us_cached = 0;
-    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1, &us_cached)) {
+    int G, th, tw, st, n1, us_cached = 0, tc_cached = -1;
+    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1, &us_cached, &tc_cached)) {
         for (const Candidate &c : cands)
-            if (c.G == G && c.tile_h == th && c.tile_w == tw && c.stages == st) {
+            if (c.G == G && c.tile_h == th && c.tile_w == tw && c.stages == st &&
+                (tc_cached < 0 ? c.tc == int(tc) : c.tc == tc_cached)) {
                 Candidate k = c;
                 k.n1 = n1;
                 const rs_status s2 = apply_fused(p, stream, k, tma);
@@ -979,7 +988,8 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
         const Candidate &c = cands[i];
         int widest = 0;
         for (const Candidate &o : cands)
-            if (o.G == c.G && o.tile_h == c.tile_h && o.stages == c.stages) widest = std::max(widest, o.tile_w);
+            if (o.G == c.G && o.tile_h == c.tile_h && o.stages == c.stages && o.tc == c.tc)
+                widest = std::max(widest, o.tile_w);
         const int ng = widest / c.G;
         const int a = std::max(1, (2 * ng + 2) / 3), b = std::max(1, (ng + 2) / 3);
         const int g = c.tile_w / c.G;
@@ -1002,7 +1012,8 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     }
     // Stage 2: every warp split for the four fastest.
     std::sort(scored.begin(), scored.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
-    for (size_t r = 0; r < scored.size() && r < 4 && !tc; ++r) {
+    for (size_t r = 0; r < scored.size() && r < 4; ++r) {
+        if (scored[r].second.tc) continue; // the tensor-core warp split is fixed
         for (int k1 = 1; k1 < fused::kWarps; ++k1) {
             Candidate c = scored[r].second;
             if (c.n1 == k1) continue;

@@ -167,20 +167,34 @@ def test_tc_matches_simt_path(rs, dt):
     assert np.abs(a - want).max() <= TOL[dt]
 
 
-def test_tc_autotune_keeps_parity(rs, tmp_path):
+@pytest.mark.parametrize("forced", [0, 1])
+def test_tc_autotune_keeps_parity(rs, tmp_path, forced):
+    """Autotuning a tensor-core plan times it against the SIMT kernels (unless
+    the tensor cores are forced) and keeps parity whichever wins; a second plan
+    takes the cached choice."""
     import torch
 
     img = synth.sinusoids(600, 800, 3, seed=6)
     t, exact = quantise(img, "bf16")
     x = t.cuda()
-    p = rs.Plan(600, 800, 3, scale=0.125, kernel="lanczos", param=3.0, boundary="mirror", dtype=torch.bfloat16)
-    assert p.path == "tcgen05"
-    out = torch.empty((p.info.out_h, p.info.out_w, 3), dtype=torch.bfloat16, device="cuda")
-    p.autotune(x, out, cache_path=str(tmp_path / "tc.jsonl"))
-    assert p.path == "tcgen05"
-    y = p(x)
-    torch.cuda.synchronize()
-    p.check()
-    want = oracle.resample(exact, p.info.out_h, p.info.out_w, "lanczos", "mirror", param=3.0)
-    assert np.abs(y.double().cpu().numpy() - want).max() <= TOL["bf16"]
-    p.close()
+    flags = rs.RS_FORCE_TC if forced else 0
+    cache = str(tmp_path / "tc.jsonl")
+    want = None
+    paths = []
+    for _ in range(2):
+        p = rs.Plan(600, 800, 3, scale=0.125, kernel="lanczos", param=3.0, boundary="mirror",
+                    dtype=torch.bfloat16, flags=flags)
+        assert p.path == "tcgen05"
+        out = torch.empty((p.info.out_h, p.info.out_w, 3), dtype=torch.bfloat16, device="cuda")
+        p.autotune(x, out, cache_path=cache)
+        paths.append(p.path)
+        if forced:
+            assert p.path == "tcgen05"
+        y = p(x)
+        torch.cuda.synchronize()
+        p.check()
+        if want is None:
+            want = oracle.resample(exact, p.info.out_h, p.info.out_w, "lanczos", "mirror", param=3.0)
+        assert np.abs(y.double().cpu().numpy() - want).max() <= TOL["bf16"]
+        p.close()
+    assert paths[0] == paths[1]
