@@ -117,6 +117,14 @@ typedef enum {
                                  channels; bands of 4 outputs of at most 40 / 32
                                  inputs across / down); RS_ERR_UNSUPPORTED where
                                  it cannot apply                                   */
+#define RS_FORCE_VFIRST 0x80u /* pick the vertical-first two-pass kernels (FP32/FP16/
+                                 BF16, 1 or 3 channels, out_h <= in_h, bands of at
+                                 most 256); RS_ERR_UNSUPPORTED where they cannot apply */
+/* The vertical-first path runs the vertical pass from the input into an FP32
+ * intermediate of out_h x in_w pixels (plan-owned), then the horizontal pass
+ * into the output: no staged halo, so it suits strong downscales with wide
+ * bands (x0.125: 48 taps).  rs_plan_autotune times it against the other
+ * kernels; it runs untuned only when forced. */
 /* The row-streaming kernel runs the horizontal pass first on staged input rows
  * and the vertical pass on a ring of filtered rows (FP32 whatever the storage
  * type), with deep TMA prefetch and coalesced output rows.  It is chosen for
@@ -184,7 +192,8 @@ typedef struct {
     int32_t taps_h, taps_w;   /* raw taps per output (max over outputs), per axis */
     int32_t table_h, table_w; /* stored (boundary-folded) taps per output         */
     int32_t path;             /* 0 = fused tiles (SIMT), 1 = two-pass SIMT, 2 = fused
-                                 tiles with the tcgen05 vertical pass, 3 = row-streaming */
+                                 tiles with the tcgen05 vertical pass, 3 = row-streaming,
+                                 4 = vertical-first two-pass                         */
     int32_t tile_h, tile_w;   /* output tile of the chosen pass kernel            */
     int32_t group_h, group_w; /* outputs per thread group along each axis         */
     int32_t span_h, span_w;   /* band width (inputs per group)                    */

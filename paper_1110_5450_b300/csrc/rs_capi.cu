@@ -672,7 +672,7 @@ std::string tune_key(const rs_plan *p)
 }
 
 bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int *tw, int *st, int *n1,
-                  int *use_stream, int *tc)
+                  int *use_stream, int *tc, int *vf)
 {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
@@ -690,21 +690,23 @@ bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int
             *use_stream = (r && std::sscanf(r, "\"stream\": %d", use_stream) == 1) ? *use_stream : 0;
             const char *t = std::strstr(line, "\"tc\":");
             *tc = (t && std::sscanf(t, "\"tc\": %d", tc) == 1) ? *tc : -1; // -1: the plan's own choice
+            const char *v = std::strstr(line, "\"vfirst\":");
+            *vf = (v && std::sscanf(v, "\"vfirst\": %d", vf) == 1) ? *vf : 0;
         }
     }
     std::fclose(f);
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, const Candidate &c, double us, int use_stream)
+void cache_store(const char *path, const std::string &key, const Candidate &c, double us, int use_stream, int vf)
 {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"G\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, \"n1\": %d, "
-                 "\"band\": %d, \"us\": %.3f, \"stream\": %d, \"tc\": %d}\n",
-                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us, use_stream, c.tc);
+                 "\"band\": %d, \"us\": %.3f, \"stream\": %d, \"tc\": %d, \"vfirst\": %d}\n",
+                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us, use_stream, c.tc, vf);
     std::fclose(f);
 }
 
@@ -750,7 +752,7 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.out_dtype < RS_F64 || d.out_dtype > RS_BF16)
         return fail(RS_ERR_INVALID_ARG, "unknown dtype");
     if (d.in_dtype != d.out_dtype) return fail(RS_ERR_UNSUPPORTED, "in_dtype and out_dtype must be equal");
-    if (d.flags & ~uint32_t(0x7f)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
+    if (d.flags & ~uint32_t(0xff)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
     if (support_radius(d.kernel, d.param) == 0)
         return fail(RS_ERR_INVALID_ARG, "Lanczos needs an integer R in 1..16");
     if (d.kernel == RS_K_CUBIC && !std::isfinite(d.param)) return fail(RS_ERR_INVALID_ARG, "cubic a not finite");
@@ -858,8 +860,22 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
         return fail(RS_ERR_UNSUPPORTED, "row-streaming kernel needs FP32, FP16 or BF16, 1 or 3 channels, a 16-byte row pitch, "
                                         "a horizontal band of at most 40 and a vertical band of at most 32 inputs");
     }
+    if (d.flags & RS_FORCE_VFIRST) {
+        const rs_status vs = vfirst::setup(p, stream);
+        if (vs != RS_OK) {
+            delete p;
+            return vs == RS_ERR_UNSUPPORTED
+                       ? fail(RS_ERR_UNSUPPORTED, "vertical-first path needs FP32, FP16 or BF16, 1 or 3 channels, "
+                                                  "out_h <= in_h and bands of at most 256 inputs")
+                       : vs;
+        }
+        p->use_vfirst = 1;
+        p->use_stream = 0;
+    }
     if (st != RS_OK) {
         p->path = 1;
+    }
+    if (st != RS_OK && !p->use_vfirst) {
         const size_t bytes = size_t(d.in_h) * size_t(d.out_w) * size_t(d.channels) * wsz;
         e = cudaMalloc(&p->tmp.p, bytes);
         if (e != cudaSuccess) {
@@ -893,6 +909,7 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     const rs_plan_desc &d = p->desc;
     cudaError_t e;
+    if (p->use_vfirst) return vfirst::launch(p, d_in, d_out, stream);
     if (p->path == 0) {
         fused::Params fp = p->fp;
         fp.in = d_in;
@@ -946,6 +963,7 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
 {
     if (!p || !d_in || !d_out) return fail(RS_ERR_INVALID_ARG, "NULL plan or buffer");
     if (p->path != 0) return RS_OK; // only the fused path has choices to tune
+    if (p->desc.flags & RS_FORCE_VFIRST) return RS_OK; // a forced kernel has nothing to choose
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     const bool tma = tma_layout_ok(p);
     const bool tc = p->chosen.tc != 0, force_tc = (p->desc.flags & RS_FORCE_TC) != 0;
@@ -962,8 +980,11 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     // kernel (if any) is compared with the winner at the end
     const int stream_ok = p->stream_ok && !force_tc;
     p->use_stream = 0;
-    int G, th, tw, st, n1, us_cached = 0, tc_cached = -1;
-    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1, &us_cached, &tc_cached)) {
+    p->use_vfirst = 0;
+    // the vertical-first kernels are a candidate unless another kernel is forced
+    const bool vf_try = !(p->desc.flags & (RS_FORCE_TC | RS_FORCE_STREAM));
+    int G, th, tw, st, n1, us_cached = 0, tc_cached = -1, vf_cached = 0;
+    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1, &us_cached, &tc_cached, &vf_cached)) {
         for (const Candidate &c : cands)
             if (c.G == G && c.tile_h == th && c.tile_w == tw && c.stages == st &&
                 (tc_cached < 0 ? c.tc == int(tc) : c.tc == tc_cached)) {
@@ -976,6 +997,11 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
                     const rs_status s3 = stream::setup(p, stream, stream::Opts::decode(us_cached));
                     if (s3 != RS_OK && s3 != RS_ERR_UNSUPPORTED) return s3;
                     p->use_stream = s3 == RS_OK ? 1 : 0;
+                }
+                if (vf_cached && vf_try) {
+                    const rs_status s4 = p->vfirst_ok ? RS_OK : vfirst::setup(p, stream);
+                    if (s4 != RS_OK && s4 != RS_ERR_UNSUPPORTED) return s4;
+                    p->use_vfirst = s4 == RS_OK ? 1 : 0;
                 }
                 return RS_OK;
             }
@@ -1074,7 +1100,33 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
         }
         best_us = std::min(us_tile, best_s);
     }
-    if (best_us < 1e299) cache_store(cache_path, key, best, best_us, stream_choice);
+    // the vertical-first kernels against the winner so far
+    int vf_choice = 0;
+    if (vf_try) {
+        if (best_us >= 1e299) {
+            s = time_plan(p, d_in, d_out, stream, &best_us);
+            if (s != RS_OK) return s;
+        }
+        const rs_status s4 = p->vfirst_ok ? RS_OK : vfirst::setup(p, stream);
+        if (s4 != RS_OK && s4 != RS_ERR_UNSUPPORTED) return s4;
+        if (s4 == RS_OK) {
+            p->use_vfirst = 1;
+            double us_vf = 0;
+            s = time_plan(p, d_in, d_out, stream, &us_vf);
+            if (s != RS_OK) return s;
+            if (us_vf < best_us) {
+                best_us = us_vf;
+                vf_choice = 1;
+            } else {
+                // not kept: release its intermediate
+                p->use_vfirst = 0;
+                p->vfirst_ok = 0;
+                p->vbufs.~DeviceBuf();
+                new (&p->vbufs) DeviceBuf();
+            }
+        }
+    }
+    if (best_us < 1e299) cache_store(cache_path, key, best, best_us, stream_choice, vf_choice);
     return RS_OK;
 }
 
@@ -1084,6 +1136,19 @@ rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     cudaError_t e = launch_plan_weights(p, stream);
     if (e != cudaSuccess) return cuda_fail(e, "weight kernel launch");
+    if (p->use_vfirst) {
+        // the other kernels' bands are rebuilt only if one of them is chosen again
+        p->tile_bands_stale = 1;
+        if (p->stream_ok) {
+            const rs_status s = stream::rebuild(p, stream);
+            if (s != RS_OK) return s;
+        }
+        return vfirst::rebuild(p, stream);
+    }
+    if (p->vfirst_ok) {
+        const rs_status s = vfirst::rebuild(p, stream);
+        if (s != RS_OK) return s;
+    }
     if (p->path == 0 && p->use_stream) {
         // the tile kernel's bands are rebuilt only if a tile launch needs them
         p->tile_bands_stale = 1;
@@ -1115,7 +1180,18 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
     info->table_h = p->gy.t_eff;
     info->table_w = p->gx.t_eff;
     info->path = (p->path == 0 && p->chosen.tc) ? 2 : p->path;
-    if (p->path == 0 && p->use_stream) {
+    if (p->use_vfirst) {
+        info->path = 4;
+        info->tile_h = info->tile_w = 0;
+        info->group_h = 8; // vertical-first kernels: 8 rows x 4 samples, 4 pixels per thread
+        info->group_w = 4;
+        info->span_h = p->vf.JV;
+        info->span_w = p->vf.JH;
+        info->warps_pass1 = 0;
+        info->stages = 0;
+        info->smem_bytes = 0;
+        info->ctas_per_sm = 0;
+    } else if (p->path == 0 && p->use_stream) {
         info->path = 3;
         info->tile_h = stream::kRB;
         info->tile_w = p->sp.SW;

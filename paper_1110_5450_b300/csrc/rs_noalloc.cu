@@ -111,7 +111,7 @@ extern "C" rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d
     if (d.boundary < RS_B_CLAMP || d.boundary > RS_B_TRUNCATE) return bad(RS_ERR_INVALID_ARG, "unknown boundary");
     if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.in_dtype != d.out_dtype)
         return bad(RS_ERR_INVALID_ARG, "dtype unknown or in_dtype != out_dtype");
-    if (d.flags & ~uint32_t(0x7f)) return bad(RS_ERR_INVALID_ARG, "unknown flag bits");
+    if (d.flags & ~uint32_t(0xff)) return bad(RS_ERR_INVALID_ARG, "unknown flag bits");
     const int R = radius(d.kernel, d.param);
     if (R == 0) return bad(RS_ERR_INVALID_ARG, "Lanczos needs an integer R in 1..16");
     const int64_t oh = out_len(d.out_h, d.in_h, d.scale_h), ow = out_len(d.out_w, d.in_w, d.scale_w);

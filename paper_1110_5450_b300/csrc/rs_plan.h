@@ -30,6 +30,14 @@ struct DeviceBuf {
     }
 };
 
+// Vertical-first two-pass path (rs_vfirst.cu): bands and intermediate.
+struct VfParams {
+    int32_t JV = 0, JH = 0, groups_y = 0, groups_x = 0;
+    int64_t tmp_stride = 0; // samples per intermediate row (in_w + JH pixels)
+    int32_t *vbase = nullptr, *hbase = nullptr;
+    float *vband = nullptr, *hband = nullptr, *tmp = nullptr;
+};
+
 // Carve 256-byte aligned pieces out of one allocation.
 struct Carver {
     size_t off = 0;
@@ -81,6 +89,11 @@ struct rs_plan {
     const void *s_fn = nullptr;
     size_t s_smem = 0;
     int s_grid = 0, s_ctas = 0;
+    // vertical-first two-pass path (strong vertical downscales)
+    int vfirst_ok = 0;  // configured (bands and intermediate allocated)
+    int use_vfirst = 0; // rs_resample runs it
+    rs::VfParams vf{};
+    rs::DeviceBuf vbufs;
 };
 
 namespace rs {
@@ -111,6 +124,17 @@ void work_regions(const rs_plan *p, fused::Work *w);
 fused::Work single_work(const rs_plan *p, int use_tma);
 // Cost of a candidate in modelled SM cycles per output pixel (also sets n1).
 double model_cost(Candidate &c, int C, size_t esz, size_t asz, int V);
+
+namespace vfirst {
+// Configures the vertical-first path (allocates its bands and intermediate);
+// RS_ERR_UNSUPPORTED when the plan is not eligible (FP64, channels other than
+// 1 or 3, an upscale in rows, bands wider than 256).
+rs_status setup(rs_plan *p, cudaStream_t s);
+// Rebuilds its bands from the plan's weight tables (after a recompute).
+rs_status rebuild(rs_plan *p, cudaStream_t s);
+// Both passes on `s`.
+rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
+} // namespace vfirst
 
 namespace stream {
 // Choices of a streaming configuration: ws = 1 warp-specialised kernel, 0
