@@ -28,6 +28,12 @@
  *                      (C. Duchon, J. Appl. Meteor. 18, 1979)
  *       RS_K_BSPLINE3  cubic B-spline (M. Unser, IEEE SP Mag. 16(6), 1999),
  *                      used directly as an approximating kernel, R = 2
+ *       RS_K_MITCHELL  Mitchell-Netravali cubic (D. Mitchell, A. Netravali,
+ *                      SIGGRAPH 1988) with B = `param` and C = (1 - B) / 2
+ *                      (the B + 2C = 1 line; B = 1/3 the authors' choice,
+ *                      B = 0 is Keys a = -1/2, B = 1 the cubic B-spline), R = 2
+ *       RS_K_GAUSSIAN  exp(-x^2 / (2 s^2)), s = `param` in (0, 4], truncated
+ *                      at R = ceil(3 s)
  *   - boundary maps B for an axis of n samples:
  *       RS_B_CLAMP       min(max(j, 0), n - 1)
  *       RS_B_MIRROR      half-sample symmetric (edge sample repeated),
@@ -89,7 +95,9 @@ typedef enum {
     RS_K_LINEAR = 0,
     RS_K_CUBIC = 1,   /* param = a, e.g. -0.5 */
     RS_K_LANCZOS = 2, /* param = R, e.g. 3    */
-    RS_K_BSPLINE3 = 3
+    RS_K_BSPLINE3 = 3,
+    RS_K_MITCHELL = 4, /* param = B (C = (1 - B) / 2), e.g. 1/3 */
+    RS_K_GAUSSIAN = 5  /* param = sigma, e.g. 0.5              */
 } rs_kernel;
 
 typedef enum {

@@ -31,9 +31,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rs_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-KERNELS = {"linear": 0, "cubic": 1, "lanczos": 2, "bspline3": 3}
+KERNELS = {"linear": 0, "cubic": 1, "lanczos": 2, "bspline3": 3, "mitchell": 4, "gaussian": 5}
 BOUNDARIES = {"clamp": 0, "mirror": 1, "reflect101": 2, "truncate": 3}
-DEFAULT_PARAM = {"linear": 0.0, "cubic": -0.5, "lanczos": 3.0, "bspline3": 0.0}
+DEFAULT_PARAM = {"linear": 0.0, "cubic": -0.5, "lanczos": 3.0, "bspline3": 0.0, "mitchell": 1.0 / 3.0,
+                 "gaussian": 0.5}
 
 _lock = threading.Lock()
 _default = None

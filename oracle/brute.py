@@ -6,7 +6,8 @@ Written straight from the coordinate definitions, independently of
 sc = max(1, n_in / n_out) when antialiasing, and tap j belongs to output i
 when |j + 1/2 - c_i| / sc < R.  All of this is done in ``fractions.Fraction``,
 so the tap sets are exact.  Polynomial kernels (linear, Keys cubic, cubic
-B-spline) are evaluated exactly as well; Lanczos falls back to float math.
+B-spline, Mitchell-Netravali) are evaluated exactly as well; Lanczos and the
+Gaussian fall back to float math.
 
 The result is the dense resampling matrix M (n_out x n_in) of one axis, with
 the boundary map folded in; a 2-D image resamples as M_h @ X @ M_w^T per
@@ -18,12 +19,14 @@ import functools
 import math
 from fractions import Fraction
 
-SUPPORT = {"linear": 1, "cubic": 2, "bspline3": 2}
+SUPPORT = {"linear": 1, "cubic": 2, "bspline3": 2, "mitchell": 2}
 
 
 def support(kernel: str, param) -> int:
     if kernel == "lanczos":
         return int(param)
+    if kernel == "gaussian":
+        return math.ceil(3 * param)
     return SUPPORT[kernel]
 
 
@@ -45,6 +48,20 @@ def kernel_exact(kernel: str, x: Fraction, param):
         if t < 2:
             return (2 - t) ** 3 / 6
         return Fraction(0)
+    if kernel == "mitchell":
+        # Mitchell & Netravali (1988) with C = (1 - B) / 2, exact in Fraction
+        B = Fraction(param)
+        C = (1 - B) / 2
+        if t < 1:
+            return ((12 - 9 * B - 6 * C) * t ** 3 + (-18 + 12 * B + 6 * C) * t ** 2 + (6 - 2 * B)) / 6
+        if t < 2:
+            return ((-B - 6 * C) * t ** 3 + (6 * B + 30 * C) * t ** 2 + (-12 * B - 48 * C) * t + (8 * B + 24 * C)) / 6
+        return Fraction(0)
+    if kernel == "gaussian":
+        s = float(param)
+        if t >= math.ceil(3 * s):
+            return 0.0
+        return math.exp(-float(x) ** 2 / (2 * s * s))
     if kernel == "lanczos":
         R = int(param)
         if t >= R:
@@ -93,13 +110,14 @@ def axis_matrix(n_in: int, n_out: int, kernel: str, boundary: str, param=None,
                 antialias: bool = True):
     """Dense n_out x n_in matrix (list of lists) of one axis."""
     if param is None:
-        param = {"linear": 0, "cubic": Fraction(-1, 2), "lanczos": 3, "bspline3": 0}[kernel]
+        param = {"linear": 0, "cubic": Fraction(-1, 2), "lanczos": 3, "bspline3": 0, "mitchell": Fraction(1, 3),
+                 "gaussian": 0.5}[kernel]
     R = support(kernel, param)
     sc = scale_factor(n_in, n_out, antialias)
     M = []
     for i in range(n_out):
         c = (i + Fraction(1, 2)) * Fraction(n_in, n_out)
-        row = [Fraction(0)] * n_in if kernel != "lanczos" else [0.0] * n_in
+        row = [Fraction(0)] * n_in if kernel not in ("lanczos", "gaussian") else [0.0] * n_in
         taps = tap_set(n_in, n_out, i, R, antialias)
         ws, ms = [], []
         for j in taps:

@@ -34,6 +34,14 @@
  *        cubic B-spline beta^3, R = 2 (M. Unser, IEEE SP Mag. 16(6), 1999):
  *            2/3 - |x|^2 + |x|^3 / 2               |x| < 1
  *            (2 - |x|)^3 / 6                       1 <= |x| < 2
+ *        Mitchell-Netravali cubic, R = 2 (D. Mitchell, A. Netravali,
+ *        SIGGRAPH 1988), with B = param and C = (1 - B) / 2:
+ *            ((12 - 9B - 6C)|x|^3 + (-18 + 12B + 6C)|x|^2 + (6 - 2B)) / 6
+ *                                                  |x| < 1
+ *            ((-B - 6C)|x|^3 + (6B + 30C)|x|^2 + (-12B - 48C)|x|
+ *             + (8B + 24C)) / 6                    1 <= |x| < 2
+ *        Gaussian, sigma = param in (0, 4], truncated at R = ceil(3 sigma):
+ *            exp(-x^2 / (2 sigma^2))               |x| < R
  *  - Normalisation: w <- w / sum(w) over the taps (for the truncate boundary,
  *    over the in-range taps only).
  *  - Boundary maps B for an index j on an axis of n samples:
@@ -54,7 +62,7 @@
 #include <string.h>
 #include <unistd.h>
 
-enum { ORA_LINEAR = 0, ORA_CUBIC = 1, ORA_LANCZOS = 2, ORA_BSPLINE3 = 3 };
+enum { ORA_LINEAR = 0, ORA_CUBIC = 1, ORA_LANCZOS = 2, ORA_BSPLINE3 = 3, ORA_MITCHELL = 4, ORA_GAUSSIAN = 5 };
 enum { ORA_CLAMP = 0, ORA_MIRROR = 1, ORA_REFLECT101 = 2, ORA_TRUNCATE = 3 };
 
 #define ORA_PI 3.14159265358979323846
@@ -69,6 +77,14 @@ int ora_support(int kernel, double param, int64_t *R)
     case ORA_LANCZOS:
         if (!(param >= 1.0 && param <= 16.0) || param != floor(param)) return -1;
         *R = (int64_t)param;
+        return 0;
+    case ORA_MITCHELL:
+        if (!(param >= 0.0 && param <= 1.0)) return -1;
+        *R = 2;
+        return 0;
+    case ORA_GAUSSIAN:
+        if (!(param > 0.0 && param <= 4.0)) return -1;
+        *R = (int64_t)ceil(3.0 * param);
         return 0;
     }
     return -1;
@@ -113,6 +129,22 @@ double ora_kernel_value(int kernel, double param, double x)
         if (t < 1.0) return 2.0 / 3.0 - t * t + t * t * t / 2.0;
         if (t < 2.0) return (2.0 - t) * (2.0 - t) * (2.0 - t) / 6.0;
         return 0.0;
+    case ORA_MITCHELL: {
+        double B = param, C = (1.0 - B) / 2.0;
+        if (t < 1.0)
+            return ((12.0 - 9.0 * B - 6.0 * C) * t * t * t + (-18.0 + 12.0 * B + 6.0 * C) * t * t + (6.0 - 2.0 * B)) /
+                   6.0;
+        if (t < 2.0)
+            return ((-B - 6.0 * C) * t * t * t + (6.0 * B + 30.0 * C) * t * t + (-12.0 * B - 48.0 * C) * t +
+                    (8.0 * B + 24.0 * C)) /
+                   6.0;
+        return 0.0;
+    }
+    case ORA_GAUSSIAN: {
+        double R = ceil(3.0 * param);
+        if (t >= R) return 0.0;
+        return exp(-(x * x) / (2.0 * param * param));
+    }
     }
     return 0.0;
 }

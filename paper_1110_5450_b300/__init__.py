@@ -29,16 +29,17 @@ _lib = ctypes.CDLL(LIB_PATH)
 RS_OK, RS_ERR_INVALID_ARG, RS_ERR_UNSUPPORTED, RS_ERR_OOM, RS_ERR_BUDGET = 0, 1, 2, 3, 4
 RS_ERR_CUDA, RS_ERR_TIMEOUT, RS_ERR_BUSY, RS_ERR_DEVICE = 5, 6, 7, 8
 RS_F64, RS_F32, RS_F16, RS_BF16 = 0, 1, 2, 3
-RS_K_LINEAR, RS_K_CUBIC, RS_K_LANCZOS, RS_K_BSPLINE3 = 0, 1, 2, 3
+RS_K_LINEAR, RS_K_CUBIC, RS_K_LANCZOS, RS_K_BSPLINE3, RS_K_MITCHELL, RS_K_GAUSSIAN = 0, 1, 2, 3, 4, 5
 RS_B_CLAMP, RS_B_MIRROR, RS_B_REFLECT101, RS_B_TRUNCATE = 0, 1, 2, 3
 RS_NO_ANTIALIAS, RS_FORCE_SIMT, RS_FORCE_TC, RS_TWO_PASS, RS_CHECK = 0x1, 0x2, 0x4, 0x8, 0x10
 RS_NO_STREAM, RS_FORCE_STREAM, RS_FORCE_VFIRST = 0x20, 0x40, 0x80
 
 KERNELS = {"linear": RS_K_LINEAR, "cubic": RS_K_CUBIC, "lanczos": RS_K_LANCZOS,
-           "bspline3": RS_K_BSPLINE3}
+           "bspline3": RS_K_BSPLINE3, "mitchell": RS_K_MITCHELL, "gaussian": RS_K_GAUSSIAN}
 BOUNDARIES = {"clamp": RS_B_CLAMP, "mirror": RS_B_MIRROR, "reflect101": RS_B_REFLECT101,
               "truncate": RS_B_TRUNCATE}
-DEFAULT_PARAM = {"linear": 0.0, "cubic": -0.5, "lanczos": 3.0, "bspline3": 0.0}
+DEFAULT_PARAM = {"linear": 0.0, "cubic": -0.5, "lanczos": 3.0, "bspline3": 0.0, "mitchell": 1.0 / 3.0,
+                 "gaussian": 0.5}
 PATHS = {0: "fused", 1: "two_pass", 2: "tcgen05", 3: "stream", 4: "vfirst"}
 
 

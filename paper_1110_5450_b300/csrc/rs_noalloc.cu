@@ -73,6 +73,12 @@ int radius(int kernel, double param)
     case RS_K_LANCZOS:
         if (!(param >= 1.0 && param <= 16.0) || param != std::floor(param)) return 0;
         return int(param);
+    case RS_K_MITCHELL:
+        if (!(param >= 0.0 && param <= 1.0)) return 0;
+        return 2;
+    case RS_K_GAUSSIAN:
+        if (!(param > 0.0 && param <= 4.0)) return 0;
+        return int(std::ceil(3.0 * param));
     }
     return 0;
 }
@@ -107,7 +113,7 @@ extern "C" rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d
         return bad(RS_ERR_INVALID_ARG, "input size out of range");
     if (d.channels < 1 || d.channels > 64) return bad(RS_ERR_INVALID_ARG, "channels must be 1..64");
     if (d.out_h < 0 || d.out_w < 0) return bad(RS_ERR_INVALID_ARG, "negative output size");
-    if (d.kernel < RS_K_LINEAR || d.kernel > RS_K_BSPLINE3) return bad(RS_ERR_INVALID_ARG, "unknown kernel");
+    if (d.kernel < RS_K_LINEAR || d.kernel > RS_K_GAUSSIAN) return bad(RS_ERR_INVALID_ARG, "unknown kernel");
     if (d.boundary < RS_B_CLAMP || d.boundary > RS_B_TRUNCATE) return bad(RS_ERR_INVALID_ARG, "unknown boundary");
     if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.in_dtype != d.out_dtype)
         return bad(RS_ERR_INVALID_ARG, "dtype unknown or in_dtype != out_dtype");

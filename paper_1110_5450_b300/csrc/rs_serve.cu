@@ -186,7 +186,7 @@ FastPlan fast_plan(rs_server *S, Req *q)
     if (C != 1 && C != 3) return {false, RS_ERR_UNSUPPORTED, "server: 1 or 3 channels"};
     if (d.in_dtype != d.out_dtype || d.in_dtype < RS_F64 || d.in_dtype > RS_BF16)
         return {false, RS_ERR_INVALID_ARG, "server: dtype"};
-    if (d.kernel < RS_K_LINEAR || d.kernel > RS_K_BSPLINE3 || d.boundary < RS_B_CLAMP || d.boundary > RS_B_TRUNCATE)
+    if (d.kernel < RS_K_LINEAR || d.kernel > RS_K_GAUSSIAN || d.boundary < RS_B_CLAMP || d.boundary > RS_B_TRUNCATE)
         return {false, RS_ERR_INVALID_ARG, "server: kernel or boundary"};
     const int R = support_radius(d.kernel, d.param);
     if (!R) return {false, RS_ERR_INVALID_ARG, "server: kernel parameter"};

@@ -59,6 +59,19 @@ __device__ double kernel_eval(int kernel, double a, int64_t R, double x)
             return u * u * u / 6.0;
         }
         return 0.0;
+    case RS_K_MITCHELL: {
+        // Mitchell-Netravali cubic on the B + 2C = 1 line (B = a), Horner form
+        const double B = a, Cm = 0.5 * (1.0 - B);
+        if (t < 1.0) return (((12.0 - 9.0 * B - 6.0 * Cm) * t + (-18.0 + 12.0 * B + 6.0 * Cm)) * t * t + (6.0 - 2.0 * B)) / 6.0;
+        if (t < 2.0)
+            return (((-B - 6.0 * Cm) * t + (6.0 * B + 30.0 * Cm)) * t + (-12.0 * B - 48.0 * Cm)) * t / 6.0 +
+                   (8.0 * B + 24.0 * Cm) / 6.0;
+        return 0.0;
+    }
+    case RS_K_GAUSSIAN:
+        // a = sigma, truncated at the integer support R = ceil(3 sigma)
+        if (t >= double(R)) return 0.0;
+        return exp(-0.5 * (x / a) * (x / a));
     }
     return 0.0;
 }

@@ -19,7 +19,7 @@ import numpy as np
 from oracle import brute
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-KERNELS = ["linear", "cubic", "lanczos", "bspline3"]
+KERNELS = ["linear", "cubic", "lanczos", "bspline3", "mitchell", "gaussian"]
 BOUNDARIES = ["clamp", "mirror", "reflect101", "truncate"]
 
 
@@ -224,6 +224,32 @@ def pin_brute(o):
                 assert np.abs(got - want).max() < 1e-13, (H, W, OH, OW, kernel, boundary)
 
 
+# ------------------------------------------------ Mitchell-Netravali, Gaussian
+def pin_mitchell_gaussian(o):
+    """Mitchell-Netravali on the B + 2C = 1 line: B = 0 is Keys a = -1/2, B = 1
+    the cubic B-spline; for every B the integer shifts sum to 1, the first
+    moment vanishes and the second is B / 3 (D. Mitchell, A. Netravali,
+    SIGGRAPH 1988).  Gaussian: exp(-x^2 / 2 sigma^2) at sigma and 2 sigma,
+    zero from the truncation radius ceil(3 sigma) on."""
+    xs = np.linspace(-2.5, 2.5, 201)
+    for x in xs:  # the same polynomials in other forms: a few ulps of the coefficients (~24)
+        assert abs(o.kernel_value("mitchell", x, 0.0) - o.kernel_value("cubic", x, -0.5)) < 1e-14
+        assert abs(o.kernel_value("mitchell", x, 1.0) - o.kernel_value("bspline3", x)) < 1e-14
+    for B in (0.0, 1 / 3, 0.5, 0.8, 1.0):
+        for x in np.linspace(0.0, 0.99, 34):
+            ks = [(x + k, o.kernel_value("mitchell", x + k, B)) for k in range(-3, 4)]
+            assert abs(sum(w for _, w in ks) - 1.0) < 1e-14, (B, x)
+            assert abs(sum(d * w for d, w in ks)) < 1e-14, (B, x)
+            assert abs(sum(d * d * w for d, w in ks) - B / 3) < 1e-14, (B, x)
+    for s in (0.5, 0.8, 1.3):
+        R = math.ceil(3 * s)
+        assert o.kernel_value("gaussian", 0.0, s) == 1.0
+        assert abs(o.kernel_value("gaussian", s, s) - math.exp(-0.5)) < 1e-16
+        assert abs(o.kernel_value("gaussian", -2 * s, s) - math.exp(-2.0)) < 1e-16
+        assert o.kernel_value("gaussian", R, s) == 0.0 and o.kernel_value("gaussian", -R, s) == 0.0
+        assert o.kernel_value("gaussian", R - 1e-9, s) > 0.0
+
+
 # --------------------------------------------------------------------- invariants
 def pin_invariants(o):
     """Linearity, transpose symmetry and channel independence."""
@@ -244,4 +270,4 @@ def pin_invariants(o):
 
 ALL_PINS = [pin_kernel_values, pin_keys_x2, pin_bilinear_aa_half, pin_identity, pin_constant,
             pin_polynomials, pin_polynomial_image, pin_torch, pin_boundary_pad,
-            pin_taps_fractions, pin_brute, pin_invariants]
+            pin_taps_fractions, pin_brute, pin_invariants, pin_mitchell_gaussian]

@@ -33,12 +33,18 @@ MUTANTS = [
     ("truncate_keeps_weight", "w[k] = (m < 0) ? 0.0 : ora_kernel_value(kernel, param, x);",
      "w[k] = ora_kernel_value(kernel, param, x);"),
     ("sinc_sign", "return (fmod(k, 2.0) != 0.0) ? -s : s;", "return s;"),
+    ("mitchell_c_relation", "double B = param, C = (1.0 - B) / 2.0;", "double B = param, C = (1.0 - B) / 3.0;"),
+    ("mitchell_outer_term", "(-12.0 * B - 48.0 * C) * t +", "(-12.0 * B - 46.0 * C) * t +"),
+    ("gaussian_width", "return exp(-(x * x) / (2.0 * param * param));", "return exp(-(x * x) / (param * param));"),
+    ("gaussian_no_truncation", "        if (t >= R) return 0.0;\n        return exp(",
+     "        (void)R;\n        return exp("),
 ]
 
 # fast pins first; the exhaustive tap scan last
 ORDER = [pins.pin_kernel_values, pins.pin_keys_x2, pins.pin_bilinear_aa_half, pins.pin_identity,
          pins.pin_constant, pins.pin_polynomials, pins.pin_polynomial_image, pins.pin_boundary_pad,
-         pins.pin_invariants, pins.pin_brute, pins.pin_torch, pins.pin_taps_fractions]
+         pins.pin_invariants, pins.pin_mitchell_gaussian, pins.pin_brute, pins.pin_torch,
+         pins.pin_taps_fractions]
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
