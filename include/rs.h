@@ -125,6 +125,14 @@ typedef enum {
                                  channels; bands of 4 outputs of at most 40 / 32
                                  inputs across / down); RS_ERR_UNSUPPORTED where
                                  it cannot apply                                   */
+#define RS_PREFILTER 0x100u   /* interpolating cubic B-spline: with RS_K_BSPLINE3, the
+                                 input is first replaced by its B-spline coefficients
+                                 (per axis (c[k-1] + 4 c[k] + c[k+1]) / 6 = s[k], c
+                                 extended by the boundary rule), so the result passes
+                                 through the samples (M. Unser, IEEE SP Mag. 16(6),
+                                 1999).  FP32 or FP64 storage; clamp, mirror or
+                                 reflect101; not in batches or the server.  The plan
+                                 holds the coefficients (in_h x in_row_stride FP32/FP64). */
 #define RS_FORCE_VFIRST 0x80u /* pick the vertical-first two-pass kernels (FP32/FP16/
                                  BF16, 1 or 3 channels, out_h <= in_h, bands of at
                                  most 256); RS_ERR_UNSUPPORTED where they cannot apply */

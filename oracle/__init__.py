@@ -128,13 +128,44 @@ class Oracle:
                          np.array(w[:n], dtype=np.float64)))
         return rows
 
+    def bspline_matrix(self, n: int, boundary: str) -> np.ndarray:
+        """n x n matrix of the cubic B-spline interpolation condition on one
+        axis (M. Unser, IEEE SP Mag. 16(6), 1999): sample k equals
+        sum_j beta3(k - j) c[B(j)] over the integers j, the coefficients c
+        extended by the boundary map B."""
+        M = np.zeros((n, n))
+        for k in range(n):
+            for j in range(k - 2, k + 3):
+                M[k, self.boundary_map(j, n, boundary)] += self.kernel_value("bspline3", float(k - j))
+        return M
+
+    def bspline_coefficients(self, img, boundary: str) -> np.ndarray:
+        """Cubic B-spline coefficients of an (H, W) or (H, W, C) image: the
+        interpolation condition solved along the columns, then the rows."""
+        a = np.asarray(img, dtype=np.float64)
+        squeeze = a.ndim == 2
+        if squeeze:
+            a = a[:, :, None]
+        H, W, C = a.shape
+        Mh, Mw = self.bspline_matrix(H, boundary), self.bspline_matrix(W, boundary)
+        c = np.linalg.solve(Mh, a.reshape(H, W * C)).reshape(H, W, C)
+        c = np.linalg.solve(Mw, c.transpose(1, 0, 2).reshape(W, H * C)).reshape(W, H, C).transpose(1, 0, 2)
+        c = np.ascontiguousarray(c)
+        return c[:, :, 0] if squeeze else c
+
     def resample(self, img, out_h: int, out_w: int, kernel: str, boundary: str, param=None,
-                 antialias: bool = True, rows=None, nthreads: int = 0) -> np.ndarray:
+                 antialias: bool = True, rows=None, nthreads: int = 0, prefilter: bool = False) -> np.ndarray:
         """Resample an (H, W) or (H, W, C) image in FP64.
 
         ``rows=(y0, y1)`` computes only output rows [y0, y1) (used to time a
-        bounded sample).  The input is converted to float64 exactly.
+        bounded sample).  The input is converted to float64 exactly.  With
+        ``prefilter`` (cubic B-spline only) the image is first replaced by its
+        B-spline coefficients, which makes the B-spline interpolating.
         """
+        if prefilter:
+            if kernel != "bspline3":
+                raise ValueError("prefilter applies to the cubic B-spline")
+            img = self.bspline_coefficients(img, boundary)
         a = np.asarray(img)
         squeeze = a.ndim == 2
         if squeeze:
@@ -189,6 +220,10 @@ def axis_weights(n_in: int, n_out: int, kernel: str, boundary: str, param=None, 
 
 
 def resample(img, out_h: int, out_w: int, kernel: str, boundary: str, param=None,
-             antialias: bool = True, rows=None, nthreads: int = 0) -> np.ndarray:
+             antialias: bool = True, rows=None, nthreads: int = 0, prefilter: bool = False) -> np.ndarray:
     return default().resample(img, out_h, out_w, kernel, boundary, param, antialias, rows,
-                              nthreads)
+                              nthreads, prefilter)
+
+
+def bspline_coefficients(img, boundary: str) -> np.ndarray:
+    return default().bspline_coefficients(img, boundary)

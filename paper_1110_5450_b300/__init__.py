@@ -32,7 +32,7 @@ RS_F64, RS_F32, RS_F16, RS_BF16 = 0, 1, 2, 3
 RS_K_LINEAR, RS_K_CUBIC, RS_K_LANCZOS, RS_K_BSPLINE3, RS_K_MITCHELL, RS_K_GAUSSIAN = 0, 1, 2, 3, 4, 5
 RS_B_CLAMP, RS_B_MIRROR, RS_B_REFLECT101, RS_B_TRUNCATE = 0, 1, 2, 3
 RS_NO_ANTIALIAS, RS_FORCE_SIMT, RS_FORCE_TC, RS_TWO_PASS, RS_CHECK = 0x1, 0x2, 0x4, 0x8, 0x10
-RS_NO_STREAM, RS_FORCE_STREAM, RS_FORCE_VFIRST = 0x20, 0x40, 0x80
+RS_NO_STREAM, RS_FORCE_STREAM, RS_FORCE_VFIRST, RS_PREFILTER = 0x20, 0x40, 0x80, 0x100
 
 KERNELS = {"linear": RS_K_LINEAR, "cubic": RS_K_CUBIC, "lanczos": RS_K_LANCZOS,
            "bspline3": RS_K_BSPLINE3, "mitchell": RS_K_MITCHELL, "gaussian": RS_K_GAUSSIAN}

@@ -288,6 +288,8 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
             return fail(RS_ERR_UNSUPPORTED, "batch: channels and dtype must be equal across the batch");
     if (descs[0].channels != 1 && descs[0].channels != 3)
         return fail(RS_ERR_UNSUPPORTED, "batch: 1 or 3 channels");
+    for (int i = 0; i < n; ++i)
+        if (descs[i].flags & RS_PREFILTER) return fail(RS_ERR_UNSUPPORTED, "batch: RS_PREFILTER is per plan only");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     rs_batch *b = new (std::nothrow) rs_batch();
     if (!b) return fail(RS_ERR_OOM, "host allocation failed");

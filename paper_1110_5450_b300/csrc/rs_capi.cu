@@ -758,7 +758,11 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.out_dtype < RS_F64 || d.out_dtype > RS_BF16)
         return fail(RS_ERR_INVALID_ARG, "unknown dtype");
     if (d.in_dtype != d.out_dtype) return fail(RS_ERR_UNSUPPORTED, "in_dtype and out_dtype must be equal");
-    if (d.flags & ~uint32_t(0xff)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
+    if (d.flags & ~uint32_t(0x1ff)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
+    if ((d.flags & RS_PREFILTER) &&
+        (d.kernel != RS_K_BSPLINE3 || d.boundary == RS_B_TRUNCATE || (d.in_dtype != RS_F32 && d.in_dtype != RS_F64)))
+        return fail(RS_ERR_UNSUPPORTED, "RS_PREFILTER needs RS_K_BSPLINE3, FP32 or FP64 storage and the clamp, "
+                                        "mirror or reflect101 boundary");
     if (support_radius(d.kernel, d.param) == 0)
         return fail(RS_ERR_INVALID_ARG, "Lanczos needs an integer R in 1..16");
     if (d.kernel == RS_K_CUBIC && !std::isfinite(d.param)) return fail(RS_ERR_INVALID_ARG, "cubic a not finite");
@@ -890,6 +894,14 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
         }
         p->tmp.n = bytes;
     }
+    if (d.flags & RS_PREFILTER) {
+        const rs_status ps = prefilter::setup(p);
+        if (ps != RS_OK) {
+            delete p;
+            return ps;
+        }
+        p->prefilter = 1;
+    }
     // read the error word once: a failing table means a bad plan
     int herr = 0;
     e = cudaMemcpyAsync(&herr, p->d_err, 4, cudaMemcpyDeviceToHost, stream);
@@ -915,6 +927,12 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     const rs_plan_desc &d = p->desc;
     cudaError_t e;
+    if (p->prefilter) {
+        // the resampling kernels read the B-spline coefficients instead
+        const rs_status ps = prefilter::launch(p, d_in, stream);
+        if (ps != RS_OK) return ps;
+        d_in = p->coef;
+    }
     if (p->use_vfirst) return vfirst::launch(p, d_in, d_out, stream);
     if (p->path == 0) {
         fused::Params fp = p->fp;

@@ -89,6 +89,11 @@ struct rs_plan {
     const void *s_fn = nullptr;
     size_t s_smem = 0;
     int s_grid = 0, s_ctas = 0;
+    // interpolating cubic B-spline: coefficients of the input (RS_PREFILTER)
+    int prefilter = 0;
+    rs::DeviceBuf pbufs;
+    void *coef = nullptr;                       // [in_h][in_row_stride] FP32 (FP64 for RS_F64)
+    const void *pf_h = nullptr, *pf_w = nullptr; // per axis: 1/pivot, factor, sub-diagonal
     // vertical-first two-pass path (strong vertical downscales)
     int vfirst_ok = 0;  // configured (bands and intermediate allocated)
     int use_vfirst = 0; // rs_resample runs it
@@ -124,6 +129,14 @@ void work_regions(const rs_plan *p, fused::Work *w);
 fused::Work single_work(const rs_plan *p, int use_tma);
 // Cost of a candidate in modelled SM cycles per output pixel (also sets n1).
 double model_cost(Candidate &c, int C, size_t esz, size_t asz, int V);
+
+namespace prefilter {
+// Allocates the coefficient buffer and uploads the elimination factors.
+rs_status setup(rs_plan *p);
+// Replaces the input by its cubic B-spline coefficients in p->coef (rows,
+// then columns), on `s`.
+rs_status launch(rs_plan *p, const void *d_in, cudaStream_t s);
+} // namespace prefilter
 
 namespace vfirst {
 // Configures the vertical-first path (allocates its bands and intermediate);

@@ -190,6 +190,7 @@ FastPlan fast_plan(rs_server *S, Req *q)
         return {false, RS_ERR_INVALID_ARG, "server: kernel or boundary"};
     const int R = support_radius(d.kernel, d.param);
     if (!R) return {false, RS_ERR_INVALID_ARG, "server: kernel parameter"};
+    if (d.flags & RS_PREFILTER) return {false, RS_ERR_UNSUPPORTED, "server: RS_PREFILTER is per plan only"};
     if (d.in_h < 1 || d.in_w < 1 || d.in_h > kMaxSide || d.in_w > kMaxSide)
         return {false, RS_ERR_INVALID_ARG, "server: input size"};
     auto derive = [](int32_t given, int64_t n, double s) -> int64_t {

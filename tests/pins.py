@@ -250,6 +250,36 @@ def pin_mitchell_gaussian(o):
         assert o.kernel_value("gaussian", R - 1e-9, s) > 0.0
 
 
+# ---------------------------------------------- interpolating cubic B-spline
+def pin_prefilter(o):
+    """B-spline coefficients from the interpolation condition: the prefiltered
+    B-spline reproduces the samples at scale 1 (every boundary rule); the
+    coefficients equal scipy's recursive spline filter (its 'reflect' is the
+    half-sample 'mirror' here, its 'mirror' the whole-sample 'reflect101'),
+    and resampling equals scipy's cubic spline interpolation at the same
+    half-pixel coordinates."""
+    import scipy.ndimage as nd
+
+    rng = _rng(5)
+    img = rng.random((13, 11, 2))
+    for boundary in ("clamp", "mirror", "reflect101"):
+        out = o.resample(img, 13, 11, "bspline3", boundary, prefilter=True)
+        assert np.abs(out - img).max() < 1e-13, boundary
+    for boundary, mode in (("mirror", "reflect"), ("reflect101", "mirror")):
+        for n in (1, 2, 3, 9, 40):
+            x = rng.random(n)
+            c = o.bspline_coefficients(x[:, None], boundary)[:, 0]
+            assert np.abs(c - nd.spline_filter1d(x, order=3, mode=mode)).max() < 1e-13, (boundary, n)
+        src = rng.random((20, 24))
+        for oh, ow in ((40, 48), (31, 37), (20, 24)):
+            out = o.resample(src, oh, ow, "bspline3", boundary, prefilter=True)
+            yy = (np.arange(oh) + 0.5) * 20 / oh - 0.5
+            xx = (np.arange(ow) + 0.5) * 24 / ow - 0.5
+            Y, X = np.meshgrid(yy, xx, indexing="ij")
+            ref = nd.map_coordinates(src, [Y, X], order=3, mode=mode, prefilter=True)
+            assert np.abs(out - ref).max() < 1e-13, (boundary, oh, ow)
+
+
 # --------------------------------------------------------------------- invariants
 def pin_invariants(o):
     """Linearity, transpose symmetry and channel independence."""
@@ -270,4 +300,4 @@ def pin_invariants(o):
 
 ALL_PINS = [pin_kernel_values, pin_keys_x2, pin_bilinear_aa_half, pin_identity, pin_constant,
             pin_polynomials, pin_polynomial_image, pin_torch, pin_boundary_pad,
-            pin_taps_fractions, pin_brute, pin_invariants, pin_mitchell_gaussian]
+            pin_taps_fractions, pin_brute, pin_invariants, pin_mitchell_gaussian, pin_prefilter]

@@ -65,7 +65,8 @@ def _desc(rs, **kw):
 @pytest.mark.parametrize("bad", [
     dict(in_h=0), dict(in_w=-3), dict(channels=0), dict(channels=65), dict(out_h=-1),
     dict(in_h=1 << 23), dict(out_h=0, scale_h=0.0), dict(out_w=0, scale_w=float("nan")),
-    dict(kernel="lanczos", param=2.5), dict(kernel="lanczos", param=0.0), dict(flags=0x100),
+    dict(kernel="lanczos", param=2.5), dict(kernel="lanczos", param=0.0), dict(flags=0x200),
+    dict(kernel="mitchell", param=1.5), dict(kernel="gaussian", param=0.0),
     dict(in_row_stride=5),
 ])
 def test_invalid_descriptors_rejected_without_gpu(rs, bad):
@@ -73,6 +74,16 @@ def test_invalid_descriptors_rejected_without_gpu(rs, bad):
     with pytest.raises(rs.RSError) as ei:
         rs.rs_plan_create(d, 0)
     assert ei.value.status == rs.RS_ERR_INVALID_ARG, str(ei.value)
+
+
+@pytest.mark.parametrize("bad", [dict(kernel="lanczos"), dict(kernel="bspline3", boundary="truncate"),
+                                 dict(kernel="bspline3", dtype=3)])
+def test_prefilter_misuse_rejected_without_gpu(rs, bad):
+    """RS_PREFILTER takes the cubic B-spline, FP32/FP64 and a symmetric or clamped boundary."""
+    d = _desc(rs, flags=rs.RS_PREFILTER, **bad)
+    with pytest.raises(rs.RSError) as ei:
+        rs.rs_plan_create(d, 0)
+    assert ei.value.status == rs.RS_ERR_UNSUPPORTED, str(ei.value)
 
 
 def test_unknown_enum_and_dtype_mismatch(rs):
