@@ -94,6 +94,7 @@ struct rs_plan {
     rs::DeviceBuf pbufs;
     void *coef = nullptr;                       // [in_h][in_row_stride] FP32 (FP64 for RS_F64)
     const void *pf_h = nullptr, *pf_w = nullptr; // per axis: 1/pivot, factor, sub-diagonal
+    void *pf_dp = nullptr;                       // forward-elimination scratch, as coef
     // vertical-first two-pass path (strong vertical downscales)
     int vfirst_ok = 0;  // configured (bands and intermediate allocated)
     int use_vfirst = 0; // rs_resample runs it
