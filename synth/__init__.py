@@ -16,7 +16,15 @@ so each recipe is stated here and in the design notes):
                kernel ~ U{linear, cubic a=-1/2, Lanczos-3};
   * serving:   Poisson arrivals at 2000 req/s for 60 s, square images with
                side ~ logU[32, 4096], channels 1 or 3 (p = 1/2),
-               scale ~ logU[1/8, 8], kernel ~ U{cubic a=-1/2, Lanczos-3}.
+               scale ~ logU[1/8, 8], kernel ~ U{cubic a=-1/2, Lanczos-3};
+  * ToF frames (the clustering workload): 204 x 204 depth / distance /
+               intensity frames of a piecewise-planar scene -- a tilted
+               background plane at 1.5-3 m and 3-6 tilted rectangles at
+               0.5-1.5 m, each surface with a reflectivity in [0.2, 1];
+               pinhole camera (focal length 200 px, centre at the middle):
+               radial distance d = z sqrt(1 + r^2 / f^2), intensity
+               I = reflectivity / d^2; noise N(0, 3 mm) on z (d follows it)
+               and 1% multiplicative noise on I.  float32.
 """
 from __future__ import annotations
 
@@ -29,6 +37,7 @@ SEED_C1 = 11105450
 SEED_C2 = 11105451
 SEED_C4 = 11105452
 SEED_C5 = 11105453
+SEED_TOF = 11105454
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -120,3 +129,30 @@ def serving_trace(rate: float = 2000.0, duration_s: float = 60.0, seed: int = SE
         reqs.append(Request(t, ImageSpec(n, n, c, s, k, p, seed * 1000 + i)))
         i += 1
     return reqs
+
+
+def tof_frames(n: int, h: int = 204, w: int = 204, seed: int = SEED_TOF):
+    """(z, d, intensity): three (n, h, w) float32 arrays of synthetic ToF frames."""
+    g = rng(seed)
+    v, u = np.mgrid[0:h, 0:w].astype(np.float64)
+    f_px, cx, cy = 200.0, (w - 1) / 2.0, (h - 1) / 2.0
+    ray = np.sqrt(1.0 + ((u - cx) ** 2 + (v - cy) ** 2) / f_px ** 2)
+    Z = np.empty((n, h, w), np.float32)
+    D = np.empty((n, h, w), np.float32)
+    I = np.empty((n, h, w), np.float32)
+    for k in range(n):
+        z = g.uniform(1.5, 3.0) + g.uniform(-0.002, 0.002) * (u - cx) + g.uniform(-0.002, 0.002) * (v - cy)
+        refl = np.full((h, w), g.uniform(0.2, 1.0))
+        for _ in range(int(g.integers(3, 7))):
+            y0, x0 = int(g.integers(0, h - 8)), int(g.integers(0, w - 8))
+            y1, x1 = int(g.integers(y0 + 8, min(h, y0 + h // 2) + 1)), int(g.integers(x0 + 8, min(w, x0 + w // 2) + 1))
+            zc = g.uniform(0.5, 1.5)
+            gy, gx = g.uniform(-0.003, 0.003), g.uniform(-0.003, 0.003)
+            sl = (slice(y0, y1), slice(x0, x1))
+            z[sl] = zc + gx * (u[sl] - x0) + gy * (v[sl] - y0)
+            refl[sl] = g.uniform(0.2, 1.0)
+        z = z + g.normal(0.0, 0.003, (h, w))
+        d = z * ray
+        inten = refl / (d * d) * (1.0 + g.normal(0.0, 0.01, (h, w)))
+        Z[k], D[k], I[k] = z, d, np.maximum(inten, 1e-6)
+    return Z, D, I
