@@ -389,6 +389,50 @@ RS_API rs_status rs_tc_selftest(int32_t m, int32_t n, int32_t k, int32_t a_mn, i
  * kernels set (RS_CHECK builds and bounded waits); clears the word. */
 RS_API rs_status rs_plan_check(rs_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * Clustering: the paper's parallel merging of ToF frames (arXiv:1110.5450,
+ * Sec. "Parallel Merging Algorithm" and "Merging Criterion").
+ *
+ * Every pixel of a frame starts as a region whose ID is its linear index
+ * (y * width + x), with descriptor w = (z, phi), phi = arctan(d sqrt(I))
+ * (z: distance along the optical axis, d: radial distance, I: intensity).
+ * In synchronous rounds every region picks, among its 4-neighbourhood
+ * neighbour regions S with |z - z_S| <= t_z and |phi - phi_S| <= t_phi
+ * (Eq. 1), the one minimising f = alpha_z |dz| + alpha_phi |dphi| (Eq. 2),
+ * ties to the larger ID; mutual choices merge into the larger ID, whose
+ * descriptor becomes the mean over the merged pixels.  Rounds repeat until no
+ * region has a qualifying neighbour (or max_rounds; 0 = no limit but the pixel
+ * count).  Decisions are taken in FP32, each operation rounded on its own.
+ * Table 1 of the paper: t_z = 0.04 m, t_phi = 0.009 rad, alpha_z = 8 / pi,
+ * alpha_phi = 4 / 3.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_frames, height, width; /* frames per run, 1 <= height * width <= 2^24 */
+    float t_z, t_phi;                /* merge thresholds (Eq. 1), >= 0                 */
+    float alpha_z, alpha_phi;        /* weights of f (Eq. 2), >= 0                     */
+    int32_t max_rounds;              /* 0: until no region has a partner               */
+} rs_cluster_desc;
+
+typedef struct rs_cluster rs_cluster;
+
+/* Allocates the per-frame region state (32 bytes per pixel per frame). */
+RS_API rs_status rs_cluster_create(const rs_cluster_desc *desc, rs_cluster **out);
+
+/* Clusters n_frames frames, one thread block each, asynchronously on
+ * `stream`.  Device pointers, frames back to back, row-major:
+ * z, d, intensity [n_frames][height][width] (FP32, read only);
+ * labels [n_frames][height][width] (int32, written: each pixel's region ID);
+ * rounds [n_frames] (int32, written: merge rounds run);
+ * region_z, region_phi [n_frames][height * width] (FP32) and region_size
+ * (int32), indexed by region ID: the final descriptor and pixel count of
+ * every region (size 0 for IDs merged away); each may be NULL. */
+RS_API rs_status rs_cluster_run(rs_cluster *c, const float *z, const float *d, const float *intensity,
+                                int32_t *labels, int32_t *rounds, float *region_z, float *region_phi,
+                                int32_t *region_size, void *stream);
+
+/* Waits for the device and frees.  NULL is accepted. */
+RS_API rs_status rs_cluster_destroy(rs_cluster *c);
+
 RS_API const char *rs_status_string(rs_status status);
 RS_API const char *rs_last_error(void);
 

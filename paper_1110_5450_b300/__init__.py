@@ -75,6 +75,13 @@ class rs_batch_info(ctypes.Structure):
                 ("in_bytes", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("n_streamed", ctypes.c_int32)]
 
 
+class rs_cluster_desc(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("t_z", ctypes.c_float), ("t_phi", ctypes.c_float),
+                ("alpha_z", ctypes.c_float), ("alpha_phi", ctypes.c_float),
+                ("max_rounds", ctypes.c_int32)]
+
+
 class rs_server_desc(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("warps_pass1", ctypes.c_int32),
@@ -137,6 +144,12 @@ _lib.rs_batch_get_info.restype = ctypes.c_int
 _lib.rs_batch_get_info.argtypes = [_vp, ctypes.POINTER(rs_batch_info)]
 _lib.rs_batch_destroy.restype = ctypes.c_int
 _lib.rs_batch_destroy.argtypes = [_vp]
+_lib.rs_cluster_create.restype = ctypes.c_int
+_lib.rs_cluster_create.argtypes = [ctypes.POINTER(rs_cluster_desc), ctypes.POINTER(_vp)]
+_lib.rs_cluster_run.restype = ctypes.c_int
+_lib.rs_cluster_run.argtypes = [_vp] * 9 + [_vp]
+_lib.rs_cluster_destroy.restype = ctypes.c_int
+_lib.rs_cluster_destroy.argtypes = [_vp]
 _lib.rs_tc_selftest.restype = ctypes.c_int
 _lib.rs_tc_selftest.argtypes = [ctypes.c_int32] * 7 + [_vp, _vp, _vp]
 _lib.rs_server_create.restype = ctypes.c_int
@@ -160,7 +173,7 @@ EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "
            "rs_resample_noalloc", "rs_plan_autotune", "rs_batch_create", "rs_batch_run",
            "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
            "rs_batch_submit", "rs_batch_poll", "rs_server_release", "rs_server_drain", "rs_server_get_stats",
-           "rs_server_destroy", "rs_tc_selftest"]
+           "rs_server_destroy", "rs_tc_selftest", "rs_cluster_create", "rs_cluster_run", "rs_cluster_destroy"]
 
 
 class RSError(RuntimeError):
@@ -484,6 +497,76 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             rs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- clustering
+# Table 1 of arXiv:1110.5450 (clustering rows)
+CLUSTER_T_Z, CLUSTER_T_PHI = 0.04, 0.009
+CLUSTER_ALPHA_Z, CLUSTER_ALPHA_PHI = 8.0 / math.pi, 4.0 / 3.0
+
+
+def rs_cluster_create(desc: rs_cluster_desc):
+    h = _vp()
+    _check(_lib.rs_cluster_create(ctypes.byref(desc), ctypes.byref(h)), "rs_cluster_create")
+    return h
+
+
+def rs_cluster_run(handle, z, d, intensity, labels, rounds, region_z=0, region_phi=0, region_size=0, stream=0):
+    _check(_lib.rs_cluster_run(handle, z, d, intensity, labels, rounds, region_z or None, region_phi or None,
+                               region_size or None, stream), "rs_cluster_run")
+
+
+def rs_cluster_destroy(handle):
+    _check(_lib.rs_cluster_destroy(handle), "rs_cluster_destroy")
+
+
+class Cluster:
+    """The paper's parallel merging clustering of n_frames (height x width)
+    ToF frames per call (one thread block per frame).
+
+    >>> c = Cluster(64, 204, 204)
+    >>> labels, rounds = c(z, d, intensity)   # (64, 204, 204) float32 CUDA tensors
+    """
+
+    def __init__(self, n_frames, height, width, t_z=CLUSTER_T_Z, t_phi=CLUSTER_T_PHI, alpha_z=CLUSTER_ALPHA_Z,
+                 alpha_phi=CLUSTER_ALPHA_PHI, max_rounds=0):
+        self.shape = (int(n_frames), int(height), int(width))
+        self.desc = rs_cluster_desc(int(n_frames), int(height), int(width), float(t_z), float(t_phi),
+                                    float(alpha_z), float(alpha_phi), int(max_rounds))
+        self.handle = rs_cluster_create(self.desc)
+
+    def __call__(self, z, d, intensity, regions=False, stream=None):
+        """Returns (labels int32 (n, h, w), rounds int32 (n,)) and, with
+        regions=True, also (mean z, mean phi, pixel count) per region ID."""
+        import torch
+
+        for t in (z, d, intensity):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == self.shape):
+                raise ValueError("inputs must be contiguous float32 CUDA tensors of shape %s" % (self.shape,))
+        dev = z.device
+        labels = torch.empty(self.shape, dtype=torch.int32, device=dev)
+        rounds = torch.empty(self.shape[0], dtype=torch.int32, device=dev)
+        rz = rp = rn = None
+        if regions:
+            rz = torch.empty(self.shape, dtype=torch.float32, device=dev)
+            rp = torch.empty(self.shape, dtype=torch.float32, device=dev)
+            rn = torch.empty(self.shape, dtype=torch.int32, device=dev)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rs_cluster_run(self.handle, z.data_ptr(), d.data_ptr(), intensity.data_ptr(), labels.data_ptr(),
+                       rounds.data_ptr(), rz.data_ptr() if regions else 0, rp.data_ptr() if regions else 0,
+                       rn.data_ptr() if regions else 0, s.cuda_stream)
+        return (labels, rounds, rz, rp, rn) if regions else (labels, rounds)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_cluster_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
