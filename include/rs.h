@@ -415,7 +415,7 @@ typedef struct {
 
 typedef struct rs_cluster rs_cluster;
 
-/* Allocates the per-frame region state (32 bytes per pixel per frame). */
+/* Allocates the per-frame region state (72 bytes per pixel per frame). */
 RS_API rs_status rs_cluster_create(const rs_cluster_desc *desc, rs_cluster **out);
 
 /* Clusters n_frames frames, one thread block each, asynchronously on
