@@ -204,6 +204,19 @@ def cpu_baseline(img, budget_s: float):
         rows.append(k)
         dt += t
         full_s += t * (n / k)  # seconds for all n rows at the sampled rate
+    if all(k == n for k, n in zip(rows, outs)):
+        # the whole workload fits the budget: repeat it to fill the budget
+        passes = 1
+        while dt < budget_s:
+            t0 = time.perf_counter()
+            for n in outs:
+                o.resample(img, n, n, "lanczos", "mirror", param=3.0)
+            t = time.perf_counter() - t0
+            dt += t
+            passes += 1
+        value = passes * total_px / dt / 1e6
+        sample = "the whole workload (both outputs), %d passes (%.1f s)" % (passes, dt)
+        return value, o.default_threads(), sample
     value = total_px / full_s / 1e6
     sample = "central bands of %s output rows of the x1.37 and x0.3 outputs (%.1f s)" % (
         "+".join(str(k) for k in rows), dt)
