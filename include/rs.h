@@ -151,6 +151,14 @@ typedef enum {
  * autotuner measures it faster; an input pointer that is not 16-byte aligned
  * at rs_resample falls back to the tile kernel of the same plan. */
 
+/* Debugging knobs: the environment variable RS_PLAN_FLAGS (read once per
+ * process) adds kernel-choice flags to every plan created, e.g.
+ * RS_PLAN_FLAGS=FORCE_SIMT,CHECK; accepted names: FORCE_SIMT, FORCE_TC,
+ * TWO_PASS, CHECK, NO_STREAM, FORCE_STREAM, FORCE_VFIRST (an unknown name
+ * makes rs_plan_create return RS_ERR_INVALID_ARG).  Every API call that
+ * launches work opens an NVTX range named after it (no cost without a
+ * profiler). */
+
 /* Plan descriptor.  Sizes are in samples/elements, not bytes. */
 typedef struct {
     int32_t in_h, in_w, channels; /* source grid, HWC interleaved, 1 <= channels <= 64 */

@@ -386,6 +386,7 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
 
 rs_status rs_batch_run(rs_batch *b, const void *const *d_in, void *const *d_out, void *stream_v)
 {
+    const Range range("rs_batch_run");
     if (!b || !valid_ptrs(b, d_in, d_out)) return fail(RS_ERR_INVALID_ARG, "batch: NULL batch or buffer");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     const int n = int(b->plans.size());

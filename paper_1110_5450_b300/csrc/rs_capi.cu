@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <cstdlib>
 #include <new>
 #include <string>
 #include <vector>
@@ -56,6 +57,42 @@ EncodeTiledFn encode_fn()
             fn = reinterpret_cast<EncodeTiledFn>(p);
     });
     return fn;
+}
+
+int64_t env_plan_flags()
+{
+    static const int64_t flags = [] {
+        const char *v = std::getenv("RS_PLAN_FLAGS");
+        if (!v || !*v) return int64_t(0);
+        static const struct {
+            const char *name;
+            uint32_t bit;
+        } known[] = {{"FORCE_SIMT", RS_FORCE_SIMT},     {"FORCE_TC", RS_FORCE_TC},       {"TWO_PASS", RS_TWO_PASS},
+                     {"CHECK", RS_CHECK},               {"NO_STREAM", RS_NO_STREAM},     {"FORCE_STREAM", RS_FORCE_STREAM},
+                     {"FORCE_VFIRST", RS_FORCE_VFIRST}};
+        int64_t f = 0;
+        std::string s(v);
+        size_t a = 0;
+        while (a <= s.size()) {
+            size_t b = s.find(',', a);
+            if (b == std::string::npos) b = s.size();
+            std::string name = s.substr(a, b - a);
+            while (!name.empty() && name.front() == ' ') name.erase(name.begin());
+            while (!name.empty() && name.back() == ' ') name.pop_back();
+            if (!name.empty()) {
+                bool hit = false;
+                for (const auto &k : known)
+                    if (name == k.name) {
+                        f |= k.bit;
+                        hit = true;
+                    }
+                if (!hit) return int64_t(-1);
+            }
+            a = b + 1;
+        }
+        return f;
+    }();
+    return flags;
 }
 
 int support_radius(int kernel, double param)
@@ -745,10 +782,14 @@ int32_t rs_version(void) { return 1; }
 
 rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out)
 {
+    const Range range("rs_plan_create");
     if (!out) return fail(RS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!desc) return fail(RS_ERR_INVALID_ARG, "desc is NULL");
     rs_plan_desc d = *desc;
+    const int64_t ef = env_plan_flags();
+    if (ef < 0) return fail(RS_ERR_INVALID_ARG, "RS_PLAN_FLAGS names an unknown flag");
+    d.flags |= uint32_t(ef);
     if (d.in_h < 1 || d.in_w < 1 || d.in_h > kMaxSide || d.in_w > kMaxSide)
         return fail(RS_ERR_INVALID_ARG, "input size out of range");
     if (d.channels < 1 || d.channels > 64) return fail(RS_ERR_INVALID_ARG, "channels must be 1..64");
@@ -923,6 +964,7 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
 
 rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
 {
+    const Range range("rs_resample");
     if (!p || !d_in || !d_out) return fail(RS_ERR_INVALID_ARG, "NULL plan or buffer");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     const rs_plan_desc &d = p->desc;
@@ -985,6 +1027,7 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
 
 rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stream_v, const char *cache_path)
 {
+    const Range range("rs_plan_autotune");
     if (!p || !d_in || !d_out) return fail(RS_ERR_INVALID_ARG, "NULL plan or buffer");
     if (p->path != 0) return RS_OK; // only the fused path has choices to tune
     if (p->desc.flags & RS_FORCE_VFIRST) return RS_OK; // a forced kernel has nothing to choose
@@ -1156,6 +1199,7 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
 
 rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
 {
+    const Range range("rs_plan_recompute");
     if (!p) return fail(RS_ERR_INVALID_ARG, "NULL plan");
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     cudaError_t e = launch_plan_weights(p, stream);

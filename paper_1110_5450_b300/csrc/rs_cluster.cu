@@ -263,6 +263,7 @@ rs_status rs_cluster_create(const rs_cluster_desc *desc, rs_cluster **out)
 rs_status rs_cluster_run(rs_cluster *c, const float *z, const float *d, const float *intensity, int32_t *labels,
                          int32_t *rounds, float *region_z, float *region_phi, int32_t *region_size, void *stream)
 {
+    const Range range("rs_cluster_run");
     if (!c || !z || !d || !intensity || !labels || !rounds)
         return fail(RS_ERR_INVALID_ARG, "cluster: NULL handle or buffer");
     const rs_cluster_desc &dd = c->desc;

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rs_fused.cuh"
 #include "rs_internal.h"
 #include "rs_stream.cuh"
@@ -37,6 +39,18 @@ struct VfParams {
     int32_t *vbase = nullptr, *hbase = nullptr;
     float *vband = nullptr, *hband = nullptr, *tmp = nullptr;
 };
+
+// An NVTX range around an API call (free when no profiler is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
+// Kernel-choice flags from the RS_PLAN_FLAGS environment variable (comma-
+// separated names without the RS_ prefix); -1 if a name is not one of them.
+int64_t env_plan_flags();
 
 // Carve 256-byte aligned pieces out of one allocation.
 struct Carver {

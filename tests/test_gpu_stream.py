@@ -275,3 +275,23 @@ def test_stream_16bit_full_size_sampled_rows(rs, dt, scale, out):
         want = oracle.resample(exact, out, out, "lanczos", "mirror", param=3.0, rows=(r, r + 1))
         err = max(err, float(np.abs(got[r] - want[0]).max()))
     assert err <= TOL[dt], err
+
+
+@pytest.mark.parametrize("env,want", [("NO_STREAM", "fused"), ("FORCE_SIMT, NO_STREAM", "fused"), ("", "stream"),
+                                      ("BOGUS", "error")])
+def test_plan_flags_environment(rs, env, want):
+    """RS_PLAN_FLAGS adds kernel-choice flags to every plan of the process."""
+    import os
+    import subprocess
+    import sys
+
+    code = ("import paper_1110_5450_b300 as rs\n"
+            "try:\n"
+            "    p = rs.Plan(300, 400, 3, scale=1.37, kernel='lanczos', boundary='mirror')\n"
+            "    print(p.path)\n"
+            "except RuntimeError as e:\n"
+            "    print('error' if 'RS_PLAN_FLAGS' in str(e) else str(e))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env_vars = dict(os.environ, RS_PLAN_FLAGS=env, PYTHONPATH=root)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env_vars, timeout=300)
+    assert out.stdout.strip().splitlines()[-1] == want, out.stdout + out.stderr
