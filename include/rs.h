@@ -398,6 +398,37 @@ RS_API rs_status rs_tc_selftest(int32_t m, int32_t n, int32_t k, int32_t a_mn, i
 RS_API rs_status rs_plan_check(rs_plan *plan);
 
 /* ------------------------------------------------------------------------
+ * Affine warps with elliptical weighted average filtering (non-separable):
+ * P. Heckbert, "Fundamentals of Texture Mapping and Image Warping", 1989;
+ * N. Greene and P. Heckbert, IEEE CG&A 6(6), 1986.
+ *
+ * Output pixel (x, y) maps to the input point
+ *   u = a[0] (x + 1/2) + a[1] (y + 1/2) + a[2],  v = a[3] (x + 1/2) + a[4] (y + 1/2) + a[5]
+ * (input sample (i, j) sits at (i + 1/2, j + 1/2)).  With J = [[a0, a1],
+ * [a3, a4]] the filter covariance is V = sigma^2 (J J^T + I) (a Gaussian
+ * reconstruction filter of width sigma convolved with the prefilter of the
+ * same width in output pixels); input sample s weighs
+ * exp(-Q / 2) - exp(-cutoff^2 / 2) for Q = (s - c)^T V^-1 (s - c) < cutoff^2,
+ * else 0; the result is the weighted mean (0 where no weight is left, e.g.
+ * far outside with RS_B_TRUNCATE).  Boundary maps as for resampling.  FP32
+ * weights and accumulation; storage FP32, FP16 or BF16; 1-4 channels, HWC.
+ * Stateless: one call, one kernel launch on `stream`.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t in_h, in_w, channels;     /* source grid, HWC interleaved, 1..4 channels */
+    int32_t out_h, out_w;             /* target grid                                 */
+    double a[6];                      /* output centre -> input point (see above)    */
+    double sigma;                     /* filter width in pixels, (0, 64]; e.g. 0.5   */
+    double cutoff;                    /* ellipse radius in filter widths, (0, 8]     */
+    int32_t boundary;                 /* rs_boundary                                 */
+    int32_t dtype;                    /* rs_dtype: RS_F32, RS_F16 or RS_BF16         */
+    int64_t in_row_stride, out_row_stride; /* elements; 0 => packed                  */
+} rs_warp_desc;
+
+/* Warps d_in into d_out (device pointers, layouts per the descriptor). */
+RS_API rs_status rs_warp(const rs_warp_desc *desc, const void *d_in, void *d_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Clustering: the paper's parallel merging of ToF frames (arXiv:1110.5450,
  * Sec. "Parallel Merging Algorithm" and "Merging Criterion").
  *

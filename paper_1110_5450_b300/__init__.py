@@ -75,6 +75,14 @@ class rs_batch_info(ctypes.Structure):
                 ("in_bytes", ctypes.c_int64), ("out_bytes", ctypes.c_int64), ("n_streamed", ctypes.c_int32)]
 
 
+class rs_warp_desc(ctypes.Structure):
+    _fields_ = [("in_h", ctypes.c_int32), ("in_w", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("out_h", ctypes.c_int32), ("out_w", ctypes.c_int32), ("a", ctypes.c_double * 6),
+                ("sigma", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("boundary", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("in_row_stride", ctypes.c_int64), ("out_row_stride", ctypes.c_int64)]
+
+
 class rs_cluster_desc(ctypes.Structure):
     _fields_ = [("n_frames", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("t_z", ctypes.c_float), ("t_phi", ctypes.c_float),
@@ -144,6 +152,8 @@ _lib.rs_batch_get_info.restype = ctypes.c_int
 _lib.rs_batch_get_info.argtypes = [_vp, ctypes.POINTER(rs_batch_info)]
 _lib.rs_batch_destroy.restype = ctypes.c_int
 _lib.rs_batch_destroy.argtypes = [_vp]
+_lib.rs_warp.restype = ctypes.c_int
+_lib.rs_warp.argtypes = [ctypes.POINTER(rs_warp_desc), _vp, _vp, _vp]
 _lib.rs_cluster_create.restype = ctypes.c_int
 _lib.rs_cluster_create.argtypes = [ctypes.POINTER(rs_cluster_desc), ctypes.POINTER(_vp)]
 _lib.rs_cluster_run.restype = ctypes.c_int
@@ -173,7 +183,8 @@ EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "
            "rs_resample_noalloc", "rs_plan_autotune", "rs_batch_create", "rs_batch_run",
            "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
            "rs_batch_submit", "rs_batch_poll", "rs_server_release", "rs_server_drain", "rs_server_get_stats",
-           "rs_server_destroy", "rs_tc_selftest", "rs_cluster_create", "rs_cluster_run", "rs_cluster_destroy"]
+           "rs_server_destroy", "rs_tc_selftest", "rs_cluster_create", "rs_cluster_run", "rs_cluster_destroy",
+           "rs_warp"]
 
 
 class RSError(RuntimeError):
@@ -504,6 +515,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------- affine warps
+def rs_warp(desc: rs_warp_desc, d_in, d_out, stream=0):
+    _check(_lib.rs_warp(ctypes.byref(desc), d_in, d_out, stream), "rs_warp")
+
+
+def warp(x, out_h, out_w, a, sigma=0.5, cutoff=3.0, boundary="clamp", out=None, stream=None):
+    """Affine warp of an (H, W, C) CUDA tensor with EWA filtering: output
+    pixel centre (x + 1/2, y + 1/2) maps to input point
+    (a0 x' + a1 y' + a2, a3 x' + a4 y' + a5).  Returns (out_h, out_w, C)."""
+    import torch
+
+    if not (x.is_cuda and x.is_contiguous() and x.dim() == 3):
+        raise ValueError("input must be a contiguous (H, W, C) CUDA tensor")
+    H, W, C = x.shape
+    if out is None:
+        out = torch.empty((out_h, out_w, C), dtype=x.dtype, device=x.device)
+    d = rs_warp_desc(int(H), int(W), int(C), int(out_h), int(out_w), (ctypes.c_double * 6)(*[float(v) for v in a]),
+                     float(sigma), float(cutoff), BOUNDARIES[boundary], _torch_dtype_code(x.dtype), 0, 0)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rs_warp(d, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+    return out
 
 
 # ---------------------------------------------------------------- clustering
