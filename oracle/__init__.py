@@ -128,6 +128,22 @@ class Oracle:
                          np.array(w[:n], dtype=np.float64)))
         return rows
 
+    def axis_weights_at(self, n_in: int, n_out: int, kernel: str, boundary: str, i: int, param=None,
+                        antialias=True):
+        """(j_first, mapped index array, normalised FP64 weights) of output i
+        alone (for sampled outputs of long axes)."""
+        k, p = _kp(kernel, param)
+        cap = 4 * (n_in // max(1, n_out) + 2) * 16 + 64
+        idx = (ctypes.c_int64 * cap)()
+        w = (ctypes.c_double * cap)()
+        jf, cnt = ctypes.c_int64(), ctypes.c_int64()
+        rc = self.lib.ora_axis_weights(n_in, n_out, k, p, BOUNDARIES[boundary], int(bool(antialias)), i, cap,
+                                       ctypes.byref(jf), ctypes.byref(cnt), idx, w)
+        if rc:
+            raise ValueError("ora_axis_weights failed: %d" % rc)
+        n = cnt.value
+        return int(jf.value), np.array(idx[:n], dtype=np.int64), np.array(w[:n], dtype=np.float64)
+
     def bspline_matrix(self, n: int, boundary: str) -> np.ndarray:
         """n x n matrix of the cubic B-spline interpolation condition on one
         axis (M. Unser, IEEE SP Mag. 16(6), 1999): sample k equals
@@ -217,6 +233,10 @@ def axis_taps(n_in: int, n_out: int, kernel: str, i: int, param=None, antialias=
 
 def axis_weights(n_in: int, n_out: int, kernel: str, boundary: str, param=None, antialias=True):
     return default().axis_weights(n_in, n_out, kernel, boundary, param, antialias)
+
+
+def axis_weights_at(n_in: int, n_out: int, kernel: str, boundary: str, i: int, param=None, antialias=True):
+    return default().axis_weights_at(n_in, n_out, kernel, boundary, i, param, antialias)
 
 
 def resample(img, out_h: int, out_w: int, kernel: str, boundary: str, param=None,

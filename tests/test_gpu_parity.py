@@ -87,6 +87,37 @@ def test_folded_weights_match_oracle(rs, n_in, n_out, kernel, param, boundary):
     assert np.abs(ww.sum(axis=1) - 1.0).max() < 2.5e-7
 
 
+@pytest.mark.parametrize("n_in,n_out", [(4_000_000, 3_000_017), (4_000_000, 1_300_001), (1_234_567, 4_194_304)])
+@pytest.mark.parametrize("kernel,param", [("lanczos", 3.0), ("lanczos", 16.0), ("cubic", -0.5)])
+@pytest.mark.parametrize("boundary", ["mirror", "truncate"])
+def test_long_axis_tables(rs, n_in, n_out, kernel, param, boundary):
+    """Axes near the 2^22 side limit (tap numerators near 2^46, Lanczos
+    argument numerators near 2^27): tap indices bit-exact and folded weights
+    within the table tolerance on sampled outputs, both ends included."""
+    import torch
+
+    p = rs.Plan(n_in, 4, 1, n_out, 4, kernel=kernel, param=param, boundary=boundary, dtype=torch.float32)
+    jlo, cnt, start, w64, ww = p.tables(0)
+    p.close()
+    g = np.random.default_rng(n_in + n_out)
+    sample = sorted(set(range(40)) | set(range(n_out - 40, n_out)) | set(g.integers(0, n_out, 200).tolist()))
+    te = w64.shape[1]
+    for i in sample:
+        jf, idx, w = oracle.axis_weights_at(n_in, n_out, kernel, boundary, i, param=param)
+        assert (int(jlo[i]), int(cnt[i])) == (jf, len(idx)), i
+        want = {}
+        for m, v in zip(idx.tolist(), w.tolist()):
+            if m >= 0:
+                want[m] = want.get(m, 0.0) + v
+        s0 = int(start[i])
+        assert all(s0 <= m < s0 + te for m in want), i
+        dense = np.zeros(te)
+        for m, v in want.items():
+            dense[m - s0] = v
+        assert np.abs(w64[i] - dense).max() < 2e-15, i
+        assert np.abs(ww[i].astype(np.float64) - dense).max() < 1.2e-7, i
+
+
 def test_keys_x2_tables_exact(rs):
     """Keys a=-1/2 at x2: dyadic weights {-9, 111, 29, -3}/128 in FP64 and FP32."""
     import torch
