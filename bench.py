@@ -5,9 +5,10 @@ N(0, 0.05^2) noise, clipped to [0, 1] (synthetic; seeded), resampled with
 Lanczos-3 and the mirror boundary by scale 1.37 (-> 5612x5612x3) and by scale
 0.3 with antialiasing (-> 1229x1229x3, ~20 taps per axis).  Each step runs the
 whole path on the GPU: the FP64 weight-table and band kernels of both plans and
-the two resample kernels, replayed as one CUDA graph (the step's launches
-captured once; replaying them removes the host launch gaps between the short
-table kernels).  Inputs stay resident in HBM; the input (201 MB) is larger
+the two resample kernels, each scale on its own stream (the scales are
+independent, so their kernels overlap), replayed as one CUDA graph (the
+step's launches captured once; replaying them removes the host launch gaps
+between the short table kernels).  Inputs stay resident in HBM; the input (201 MB) is larger
 than L2 (126 MB), so no explicit flush is needed between steps.  The
 dominant kernel is also timed alone (K launches between CUDA events on its
 stream) for the roofline.
@@ -617,15 +618,17 @@ def main():
     side = torch.cuda.Stream()
 
     def step():
-        # the plans' tables are independent: both at once on two streams,
-        # then the resamples (each fills the GPU) one after the other
+        # the plans are independent: each plan's tables and resample on its
+        # own stream, so the short table kernels overlap and the second
+        # resample's CTAs fill the SMs the first one leaves idle (measured
+        # 0.258 against 0.266 ms per step with the resamples in sequence)
         side.wait_stream(stream)
-        for p in plans[1:]:
+        for p, y in zip(plans[1:], ys[1:]):
             p.recompute(side)
+            p(x, out=y, stream=side)
         plans[0].recompute(stream)
+        plans[0](x, out=ys[0], stream=stream)
         stream.wait_stream(side)
-        for p, y in zip(plans, ys):
-            p(x, out=y, stream=stream)
 
     for _ in range(2):
         step()
@@ -768,7 +771,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "C2 4096x4096x3 FP32 sinusoids+noise, Lanczos-3 mirror, x1.37 and x0.3",
                        "outputs": ["%dx%dx%d" % (n, n, C) for n in outs],
-                       "step": "weight-table + band kernels + resample, both scales, replayed as one CUDA graph",
+                       "step": "weight-table + band kernels + resample, both scales (one stream per scale), replayed as one CUDA graph",
                        "autotune_s": round(t_tune, 3),
                        "l2": "input 201 MB > 126 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single",
