@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) cluster_kernel(const Args a)
     __shared__ int any, n_edges_next, n_live_next, changed;
 
     // every pixel a region; edge 2p = (p, right neighbour), 2p + 1 = (p, lower
-    // neighbour); a missing neighbour gives an inner pair, dropped in round 1
+    // neighbour); a missing neighbour gives an inner pair, dropped in the first merge round
     for (int64_t p = threadIdx.x; p < n; p += kThreads) {
         const float zf = a.z[off + p];
         const float ph = float(atan(double(a.d[off + p]) * sqrt(double(a.inten[off + p]))));
