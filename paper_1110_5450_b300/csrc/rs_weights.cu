@@ -1,15 +1,19 @@
 // rs_weights.cu -- FP64 weight-table kernel and register-band builder.
 //
-// Blocks of consecutive output samples of an axis.  Tap indices come from a closed
-// form in 64-bit integers (exact), weights from the kernel evaluated in FP64
-// at x = ((2j+1) n_out - (2i+1) n_in) / D (one correctly rounded division of
-// exact integers), normalised by their FP64 sum, folded through the boundary
-// map into a window of t_eff consecutive in-range inputs, then rounded to the
-// working precision with the rounding residual put back on the largest tap.
+// A block per SM owns a run of outputs of an axis and their mirror outputs.
+// Tap indices come from a closed form in 64-bit integers (exact), weights
+// from the kernel evaluated in FP64 at x = N / D with the exact integer
+// numerator N = (2j+1) n_out - (2i+1) n_in (Lanczos: both sine arguments
+// reduced exactly in integers first), normalised by their FP64 sum, folded
+// through the boundary map into a window of t_eff consecutive in-range
+// inputs, then rounded to the working precision with the rounding residual
+// put back on the largest tap.
 //
 // Kernel definitions (standard): tent; Keys cubic convolution (R. Keys, IEEE
 // Trans. ASSP 29(6), 1981); Lanczos windowed sinc (C. Duchon, J. Appl.
-// Meteor. 18, 1979); cubic B-spline (M. Unser, IEEE SP Mag. 16(6), 1999).
+// Meteor. 18, 1979); cubic B-spline (M. Unser, IEEE SP Mag. 16(6), 1999);
+// Mitchell-Netravali cubic (D. Mitchell, A. Netravali, SIGGRAPH 1988);
+// Gaussian.
 #include "rs_internal.h"
 
 namespace rs {
