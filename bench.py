@@ -16,8 +16,10 @@ stream) for the roofline.
 Printed line (rank 0): output Mpixel/s over the K timed steps, the roofline of
 the dominant kernel (the x1.37 resample), an end-to-end figure through the C
 ABI with host buffers (H2D of the input and D2H of both outputs inside the
-timed region), SM clocks sampled during the timed region, and the FP64 CPU
-oracle timed on the host cores on a bounded sample of the same workload.
+timed region), SM clocks sampled during the timed region, the FP64 CPU
+oracle timed on the host cores on a bounded sample of the same workload, and
+side figures: the C1 FP64 call latency, the C4 batch, the C5 serving trace,
+16-bit storage, and the paper's clustering.
 
 ``--impl reference`` times that oracle alone (the project has no other
 reference implementation: the paper ships no code).  Under torchrun each rank
@@ -388,6 +390,56 @@ def tc_section(args, dev, stream):
     return res
 
 
+def c1_section(dev, stream):
+    """C1: 256x256x1 FP64 U[0,1) -> 512x512, Keys a = -1/2, clamp, FP64
+    accumulation.  2.6 MB move in 0.4 us at full HBM bandwidth, so there is
+    no meaningful roofline: after autotuning, the device time of one call
+    (weight tables, bands if any, and resample; CUDA events over 200 calls on
+    the stream) and the host round trip of one call (call plus synchronize;
+    p50 / p99 of 200)."""
+    import torch
+
+    import paper_1110_5450_b300 as rs
+    import synth
+
+    img = torch.from_numpy(synth.uniform(256, 256, 1, seed=synth.SEED_C1)).to(dev)
+    with torch.cuda.stream(stream):
+        p = rs.Plan(256, 256, 1, 512, 512, kernel="cubic", param=-0.5, boundary="clamp",
+                    dtype=torch.float64, stream=stream)
+        y = torch.empty(p.out_shape, dtype=torch.float64, device=dev)
+    # measured choice of kernel (tile, two-pass) for this small problem
+    p.autotune(img, out=y, stream=stream)
+
+    def call():
+        p.recompute(stream)
+        p(img, out=y, stream=stream)
+
+    for _ in range(20):
+        call()
+    torch.cuda.synchronize()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(200):
+        call()
+    b_.record(stream)
+    torch.cuda.synchronize()
+    dev_us = a.elapsed_time(b_) / 200 * 1e3
+    rt = []
+    for _ in range(200):
+        t0 = time.perf_counter()
+        call()
+        stream.synchronize()
+        rt.append((time.perf_counter() - t0) * 1e6)
+    p.check()
+    info = p.info
+    p.close()
+    rt.sort()
+    return {"workload": "C1 256x256x1 FP64 U[0,1) -> 512x512, Keys -1/2, clamp",
+            "path": rs.PATHS[info.path], "device_us_per_call": dev_us,
+            "roundtrip_us_p50": rt[len(rt) // 2], "roundtrip_us_p99": rt[int(0.99 * len(rt))],
+            "launches_per_call": 3, "autotuned": True}
+
+
 def cluster_section(args, dev, stream):
     """The paper's own data-parallel path: parallel merging clustering of
     synthetic 204 x 204 ToF frames (depth, distance, intensity), Table 1
@@ -752,6 +804,7 @@ def main():
     clustering = None
     if not args.no_cluster and rank == 0:
         clustering = cluster_section(args, dev, stream)
+    c1 = c1_section(dev, stream) if rank == 0 else None
     tc16 = None
     if not args.no_tc and rank == 0:
         tc16 = tc_section(args, dev, stream)
@@ -782,7 +835,7 @@ def main():
                                  for sc, pl in zip(SCALES, plans)}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(),
-                         "kernel": "fused resample x1.37", "algorithmic_bytes": alg,
+                         "kernel": "resample x1.37 (%s kernel)" % rs.PATHS[plans[0].info.path], "algorithmic_bytes": alg,
                          "avg_kernel_ms": k_avg_s * 1e3, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps + args.steps,
@@ -790,6 +843,7 @@ def main():
             "cpu_baseline": cpu,
             "batched": batched,
             "clustering": clustering,
+            "c1_latency": c1,
             "precision_16bit": tc16,
             "serving": serving,
         }

@@ -203,7 +203,12 @@ RS_API rs_status rs_plan_recompute(rs_plan *plan, void *stream);
  * tables while it runs.  cache_path (may be NULL) names a JSON-lines file of
  * earlier results keyed by device, dtype, channels, kernel, boundary and
  * geometry; a hit applies the cached choice without timing, a miss appends
- * the new result.  Plans on the two-pass path return RS_OK unchanged. */
+ * the new result.  Unless RS_FORCE_TC or RS_FORCE_STREAM is set, the
+ * winner is also timed against the two-pass path (H then V through an HBM
+ * intermediate of in_h x out_w x channels accumulation samples, allocated
+ * for the trial and kept only if that path wins: small problems such as
+ * FP64 256x256 -> 512x512); the chosen path is in rs_plan_info.path.  Plans
+ * created on the two-pass path return RS_OK unchanged. */
 RS_API rs_status rs_plan_autotune(rs_plan *plan, const void *d_in, void *d_out, void *stream,
                                   const char *cache_path);
 

@@ -715,7 +715,7 @@ std::string tune_key(const rs_plan *p)
 }
 
 bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int *tw, int *st, int *n1,
-                  int *use_stream, int *tc, int *vf)
+                  int *use_stream, int *tc, int *vf, int *tp)
 {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
@@ -735,22 +735,51 @@ bool cache_lookup(const char *path, const std::string &key, int *G, int *th, int
             *tc = (t && std::sscanf(t, "\"tc\": %d", tc) == 1) ? *tc : -1; // -1: the plan's own choice
             const char *v = std::strstr(line, "\"vfirst\":");
             *vf = (v && std::sscanf(v, "\"vfirst\": %d", vf) == 1) ? *vf : 0;
+            const char *w = std::strstr(line, "\"two_pass\":");
+            *tp = (w && std::sscanf(w, "\"two_pass\": %d", tp) == 1) ? *tp : 0;
         }
     }
     std::fclose(f);
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, const Candidate &c, double us, int use_stream, int vf)
+void cache_store(const char *path, const std::string &key, const Candidate &c, double us, int use_stream, int vf,
+                 int tp)
 {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"G\": %d, \"tile_h\": %d, \"tile_w\": %d, \"stages\": %d, \"n1\": %d, "
-                 "\"band\": %d, \"us\": %.3f, \"stream\": %d, \"tc\": %d, \"vfirst\": %d}\n",
-                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us, use_stream, c.tc, vf);
+                 "\"band\": %d, \"us\": %.3f, \"stream\": %d, \"tc\": %d, \"vfirst\": %d, \"two_pass\": %d}\n",
+                 key.c_str(), c.G, c.tile_h, c.tile_w, c.stages, c.n1, c.J, us, use_stream, c.tc, vf, tp);
     std::fclose(f);
+}
+
+// The two-pass path's intermediate (in_h x out_w x C samples of the
+// accumulation type), allocated on first use.
+rs_status ensure_two_pass_tmp(rs_plan *p)
+{
+    if (p->tmp.p) return RS_OK;
+    const size_t bytes =
+        size_t(p->desc.in_h) * size_t(p->desc.out_w) * size_t(p->desc.channels) * (p->work_double ? 8 : 4);
+    const cudaError_t e = cudaMalloc(&p->tmp.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p->tmp.p = nullptr;
+        return RS_ERR_OOM;
+    }
+    p->tmp.n = bytes;
+    p->scratch_bytes += int64_t(bytes);
+    return RS_OK;
+}
+
+void release_two_pass_tmp(rs_plan *p)
+{
+    if (!p->tmp.p) return;
+    p->scratch_bytes -= int64_t(p->tmp.n);
+    p->tmp.~DeviceBuf();
+    new (&p->tmp) DeviceBuf();
 }
 
 // Mean launch time (µs) of the plan's current configuration.
@@ -1050,8 +1079,10 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     p->use_vfirst = 0;
     // the vertical-first kernels are a candidate unless another kernel is forced
     const bool vf_try = !(p->desc.flags & (RS_FORCE_TC | RS_FORCE_STREAM));
-    int G, th, tw, st, n1, us_cached = 0, tc_cached = -1, vf_cached = 0;
-    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1, &us_cached, &tc_cached, &vf_cached)) {
+    // the two-pass path (H then V through HBM) likewise
+    const bool tp_try = !(p->desc.flags & (RS_FORCE_TC | RS_FORCE_STREAM));
+    int G, th, tw, st, n1, us_cached = 0, tc_cached = -1, vf_cached = 0, tp_cached = 0;
+    if (cache_lookup(cache_path, key, &G, &th, &tw, &st, &n1, &us_cached, &tc_cached, &vf_cached, &tp_cached)) {
         for (const Candidate &c : cands)
             if (c.G == G && c.tile_h == th && c.tile_w == tw && c.stages == st &&
                 (tc_cached < 0 ? c.tc == int(tc) : c.tc == tc_cached)) {
@@ -1069,6 +1100,12 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
                     const rs_status s4 = p->vfirst_ok ? RS_OK : vfirst::setup(p, stream);
                     if (s4 != RS_OK && s4 != RS_ERR_UNSUPPORTED) return s4;
                     p->use_vfirst = s4 == RS_OK ? 1 : 0;
+                }
+                if (tp_cached && tp_try && ensure_two_pass_tmp(p) == RS_OK) {
+                    p->path = 1;
+                    p->use_stream = 0;
+                    p->use_vfirst = 0;
+                    p->tile_bands_stale = 1;
                 }
                 return RS_OK;
             }
@@ -1193,7 +1230,42 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
             }
         }
     }
-    if (best_us < 1e299) cache_store(cache_path, key, best, best_us, stream_choice, vf_choice);
+    // the two-pass path against the winner so far (it wins on small problems
+    // whose work is too little to fill the GPU in tiles, e.g. FP64 256x256)
+    int tp_choice = 0;
+    if (tp_try) {
+        if (best_us >= 1e299) {
+            s = time_plan(p, d_in, d_out, stream, &best_us);
+            if (s != RS_OK) return s;
+        }
+        if (ensure_two_pass_tmp(p) == RS_OK) {
+            const int keep_stream = p->use_stream, keep_vfirst = p->use_vfirst;
+            p->path = 1;
+            p->use_stream = 0;
+            p->use_vfirst = 0;
+            double us_tp = 0;
+            s = time_plan(p, d_in, d_out, stream, &us_tp);
+            if (s != RS_OK) return s;
+            if (us_tp < best_us) {
+                best_us = us_tp;
+                tp_choice = 1;
+                stream_choice = 0;
+                p->tile_bands_stale = 1;
+                if (vf_choice) {
+                    vf_choice = 0;
+                    p->vfirst_ok = 0;
+                    p->vbufs.~DeviceBuf();
+                    new (&p->vbufs) DeviceBuf();
+                }
+            } else {
+                p->path = 0;
+                p->use_stream = keep_stream;
+                p->use_vfirst = keep_vfirst;
+                release_two_pass_tmp(p);
+            }
+        }
+    }
+    if (best_us < 1e299) cache_store(cache_path, key, best, best_us, stream_choice, vf_choice, tp_choice);
     return RS_OK;
 }
 
@@ -1204,6 +1276,12 @@ rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     cudaError_t e = launch_plan_weights(p, stream);
     if (e != cudaSuccess) return cuda_fail(e, "weight kernel launch");
+    if (p->path == 1) {
+        // the two-pass kernels read the weight tables directly; the other
+        // kernels' bands are rebuilt only if one of them is chosen again
+        p->tile_bands_stale = 1;
+        return RS_OK;
+    }
     if (p->use_vfirst) {
         // the other kernels' bands are rebuilt only if one of them is chosen again
         p->tile_bands_stale = 1;

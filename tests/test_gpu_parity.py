@@ -323,6 +323,37 @@ def test_two_plans_sharing_a_kernel_variant(rs):
         p.close()
 
 
+def test_fp64_autotune_times_the_two_pass_path(rs, tmp_path):
+    """A small FP64 plan (256x256 -> 512x512, Keys): the autotuner also times
+    the two-pass path; whichever wins keeps parity with the oracle, the
+    recomputed tables give the same result, and a second plan takes the
+    cached choice."""
+    import torch
+
+    img = synth.uniform(256, 256, 1, seed=synth.SEED_C1)
+    x = torch.from_numpy(img).cuda()
+    want = oracle.resample(img, 512, 512, "cubic", "clamp", param=-0.5)
+    cache = str(tmp_path / "fp64.jsonl")
+    paths = []
+    for _ in range(2):
+        p = rs.Plan(256, 256, 1, 512, 512, kernel="cubic", param=-0.5, boundary="clamp", dtype=torch.float64)
+        out = torch.empty(p.out_shape, dtype=torch.float64, device="cuda")
+        p.autotune(x, out, cache_path=cache)
+        paths.append(p.path)
+        y = p(x).clone()
+        p.recompute()
+        y2 = p(x)
+        torch.cuda.synchronize()
+        p.check()
+        assert torch.equal(y, y2)
+        got = y.cpu().numpy()
+        assert got.shape == want.shape
+        assert np.abs(got - want).max() < 1e-13
+        p.close()
+    assert paths[0] == paths[1]
+    assert '"two_pass":' in open(cache).read()
+
+
 def test_autotune_keeps_parity_and_uses_cache(rs, tmp_path):
     import torch
 

@@ -183,7 +183,7 @@ def test_autotune_chooses_between_stream_and_tiles(rs, tmp_path):
     out = torch.empty(p.out_shape, device="cuda")
     p.autotune(x, out, cache_path=cache)
     first = p.path
-    assert first in ("stream", "fused")
+    assert first in ("stream", "fused", "two_pass")
     y = p(x)
     torch.cuda.synchronize()
     p.check()
