@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
     ap.add_argument("--no-tc", action="store_true", help="skip the 16-bit tensor-core section")
     ap.add_argument("--no-cluster", action="store_true", help="skip the clustering section")
+    ap.add_argument("--no-c1", action="store_true", help="skip the C1 FP64 latency section")
     ap.add_argument("--cluster-frames", type=int, default=592, help="204x204 ToF frames per clustering run")
     ap.add_argument("--cluster-only", action="store_true", help="run only the clustering section")
     ap.add_argument("--tc-only", action="store_true",
@@ -804,7 +805,7 @@ def main():
     clustering = None
     if not args.no_cluster and rank == 0:
         clustering = cluster_section(args, dev, stream)
-    c1 = c1_section(dev, stream) if rank == 0 else None
+    c1 = c1_section(dev, stream) if rank == 0 and not args.no_c1 else None
     tc16 = None
     if not args.no_tc and rank == 0:
         tc16 = tc_section(args, dev, stream)
