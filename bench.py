@@ -92,6 +92,19 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(ms, device):
+    """The timed region of the slowest rank (the bench reports whole-job
+    throughput over it): a MAX all-reduce of each rank's milliseconds, then a
+    barrier.  Needs an initialised process group (NCCL on the GPUs; the CPU
+    tests use gloo)."""
+    import torch
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.barrier()
+    return float(t.item())
+
+
 def out_sizes():
     return [max(1, int(math.floor(N_IN * s + 0.5))) for s in SCALES]
 
@@ -724,10 +737,7 @@ def main():
     ms = t_start.elapsed_time(t_end)
     kms = [ka.elapsed_time(kb) / args.steps]
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
 
     mpx_step = sum(n * n for n in outs) / 1e6
     value = world * args.steps * mpx_step / (ms / 1e3)
