@@ -15,7 +15,12 @@
 //
 // One thread per output pixel.  The input point is computed in FP64 and
 // split into an integer base and a fraction, so the per-tap offsets (small
-// numbers) are exact to FP32 rounding; weights and sums are FP32.
+// numbers) are exact to FP32 rounding; weights and sums are FP32.  Along a
+// row of taps the quadratic form is advanced by forward differences (two
+// additions per tap), the exponential is the fast intrinsic, and the
+// boundary map is skipped when the whole footprint lies inside the image.
+// The weights are continuous (zero at the ellipse), so rounding that moves a
+// tap across the ellipse changes nothing measurable.
 #include <cmath>
 
 #include <cuda_bf16.h>
@@ -72,7 +77,7 @@ __device__ __forceinline__ int64_t map_idx(int64_t j, int64_t n, int boundary)
     return -1; // truncate
 }
 
-template <typename T, int C> __global__ void __launch_bounds__(kThreads) warp_kernel(const Args a)
+template <typename T, int C> __global__ void __launch_bounds__(kThreads, 4) warp_kernel(const Args a)
 {
     const int64_t t = int64_t(blockIdx.x) * kThreads + threadIdx.x;
     if (t >= int64_t(a.out_h) * a.out_w) return;
@@ -88,24 +93,46 @@ template <typename T, int C> __global__ void __launch_bounds__(kThreads) warp_ke
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] = 0.f;
     float wsum = 0.f;
+    const bool inside = i0 >= 0 && i1 < a.in_w && j0 >= 0 && j1 < a.in_h;
+    const int ni = int(i1 - i0) + 1;
+    const float dd = 2.f * a.vi00; // second difference of q along a row
     for (int64_t j = j0; j <= j1; ++j) {
-        const int64_t mj = map_idx(j, a.in_h, a.boundary);
+        const int64_t mj = inside ? j : map_idx(j, a.in_h, a.boundary);
         if (mj < 0) continue;
         const float dv = fv + float(j - j0);
         const float qv = a.vi11 * dv * dv;
         const float quv = 2.f * a.vi01 * dv;
         const T *row = src + mj * a.in_stride;
-        for (int64_t i = i0; i <= i1; ++i) {
-            const float du = fu + float(i - i0);
-            const float q = fmaf(a.vi00 * du + quv, du, qv);
-            if (!(q < a.r2)) continue;
-            const int64_t mi = map_idx(i, a.in_w, a.boundary);
-            if (mi < 0) continue;
-            const float w = expf(-0.5f * q) - a.wcut;
-            const T *s = row + mi * C;
+        // q(du) = vi00 du^2 + quv du + qv at du = fu, fu + 1, ...
+        float q = fmaf(fmaf(a.vi00, fu, quv), fu, qv);
+        float d = fmaf(a.vi00, fmaf(2.f, fu, 1.f), quv);
+        if (inside) {
+            const T *s = row + i0 * C;
+            for (int k = 0; k < ni; ++k, s += C) {
+                if (q < a.r2) {
+                    const float w = __expf(-0.5f * q) - a.wcut;
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = fmaf(w, ld<T>(s + c), acc[c]);
-            wsum += w;
+                    for (int c = 0; c < C; ++c) acc[c] = fmaf(w, ld<T>(s + c), acc[c]);
+                    wsum += w;
+                }
+                q += d;
+                d += dd;
+            }
+        } else {
+            for (int k = 0; k < ni; ++k) {
+                if (q < a.r2) {
+                    const int64_t mi = map_idx(i0 + k, a.in_w, a.boundary);
+                    if (mi >= 0) {
+                        const float w = __expf(-0.5f * q) - a.wcut;
+                        const T *s = row + mi * C;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) acc[c] = fmaf(w, ld<T>(s + c), acc[c]);
+                        wsum += w;
+                    }
+                }
+                q += d;
+                d += dd;
+            }
         }
     }
     T *o = static_cast<T *>(a.out) + y * a.out_stride + x * C;
@@ -185,6 +212,8 @@ extern "C" rs_status rs_warp(const rs_warp_desc *desc, const void *d_in, void *d
                                           : warp::fn_for<float>(d.channels);
     void *args[1] = {&a};
     const int64_t n = int64_t(d.out_h) * d.out_w;
+    if ((n + warp::kThreads - 1) / warp::kThreads > int64_t(0x7fffffff))
+        return fail(RS_ERR_UNSUPPORTED, "warp: output too large for one launch");
     const cudaError_t e = cudaLaunchKernel(fn, dim3(unsigned((n + warp::kThreads - 1) / warp::kThreads)),
                                            dim3(warp::kThreads), args, 0, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "warp kernel launch");
