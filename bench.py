@@ -144,7 +144,9 @@ def recorded_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running
+    (the bench runs it over a 0.4 s burst of the timed step's own replays and
+    the timed region)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -717,7 +719,15 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    time.sleep(0.3)
+    # keep the GPU under this step's load (untimed replays of the same graph)
+    # for 0.4 s, so that the sampler's 100 ms samples see the clocks the
+    # workload runs at; the timed steps follow without a gap
+    t_load = time.perf_counter()
+    with torch.cuda.stream(stream):
+        while time.perf_counter() - t_load < 0.4:
+            for _ in range(40):
+                graph.replay()
+            stream.synchronize()
     with torch.cuda.stream(stream):
         t_start.record(stream)
         for _ in range(args.steps):
