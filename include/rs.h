@@ -212,6 +212,40 @@ RS_API rs_status rs_plan_recompute(rs_plan *plan, void *stream);
 RS_API rs_status rs_plan_autotune(rs_plan *plan, const void *d_in, void *d_out, void *stream,
                                   const char *cache_path);
 
+/* Forms of the row-streaming kernel (plan path 3).  kind 0: the band kernel
+ * with phases that alternate between block barriers; 1: the band kernel with
+ * warps specialised on the two passes; 2: the pipelined kernel (upscales and
+ * scale 1 with 4 or 6 taps per output on both axes: groups of 4 outputs on
+ * bands of taps + 3 inputs built on chip from the plan's weight tables, a
+ * producer warp and horizontal / vertical warps handing staged blocks over
+ * through mbarriers).  Zeros choose a field's default.  The choice is a
+ * performance knob: every form computes the same sums (each output's taps in
+ * increasing order, FP32 accumulation; band zeros add exact zeros). */
+typedef struct {
+    int32_t kind;          /* 0, 1 or 2 as above                                      */
+    int32_t h_warps;       /* warps on the horizontal pass (kind 1: 2..6; kind 2: 1..6) */
+    int32_t staged_blocks; /* staged 32-row input blocks, 2..4                          */
+    int32_t strip_width;   /* output pixels per strip (a multiple of 4)                 */
+    int32_t prefetch;      /* kind 2: 1 = prefetch the block after the staging ring
+                              into L2                                                 */
+    int32_t packed;        /* kind 2: 1 = the vertical pass multiplies packed FP32 pairs
+                              (fma.rn.f32x2; bitwise the same as scalar FMAs)        */
+    int32_t v_warps;       /* kind 2: warps on the vertical pass (a CTA has one producer
+                              warp plus h_warps + v_warps <= 11)                      */
+} rs_stream_form;
+
+/* Makes the plan run the row-streaming kernel in the given form (configuring
+ * it on `stream`, which it does not synchronise).  RS_ERR_UNSUPPORTED when the
+ * plan cannot take that form (then the plan keeps its previous kernel);
+ * RS_ERR_INVALID_ARG for a malformed form.  rs_plan_autotune chooses among the
+ * same forms by timing them. */
+RS_API rs_status rs_plan_set_stream_form(rs_plan *plan, const rs_stream_form *form, void *stream);
+
+/* The form the plan's streaming kernel is configured in (RS_ERR_UNSUPPORTED
+ * if the plan has no streaming configuration); whether rs_resample runs it is
+ * rs_plan_info.path == 3. */
+RS_API rs_status rs_plan_get_stream_form(const rs_plan *plan, rs_stream_form *form);
+
 /* Free a plan after waiting for its work to finish.  NULL is accepted. */
 RS_API rs_status rs_destroy(rs_plan *plan);
 

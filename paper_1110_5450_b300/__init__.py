@@ -66,6 +66,12 @@ class rs_plan_info(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_int64)]
 
 
+class rs_stream_form(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("h_warps", ctypes.c_int32), ("staged_blocks", ctypes.c_int32),
+                ("strip_width", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("packed", ctypes.c_int32),
+                ("v_warps", ctypes.c_int32)]
+
+
 class rs_batch_info(ctypes.Structure):
     _fields_ = [("n_images", ctypes.c_int32), ("total_tiles", ctypes.c_int32),
                 ("group", ctypes.c_int32), ("warps_pass1", ctypes.c_int32),
@@ -138,6 +144,10 @@ _lib.rs_version.restype = ctypes.c_int32
 _lib.rs_version.argtypes = []
 _lib.rs_plan_autotune.restype = ctypes.c_int
 _lib.rs_plan_autotune.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_char_p]
+_lib.rs_plan_set_stream_form.restype = ctypes.c_int
+_lib.rs_plan_set_stream_form.argtypes = [_vp, ctypes.POINTER(rs_stream_form), _vp]
+_lib.rs_plan_get_stream_form.restype = ctypes.c_int
+_lib.rs_plan_get_stream_form.argtypes = [_vp, ctypes.POINTER(rs_stream_form)]
 _lib.rs_resample_noalloc.restype = ctypes.c_int
 _lib.rs_resample_noalloc.argtypes = [ctypes.POINTER(rs_plan_desc), _vp, _vp, _vp]
 RS_STATIC_SCRATCH_BYTES = 32 << 20
@@ -184,7 +194,7 @@ EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "
            "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
            "rs_batch_submit", "rs_batch_poll", "rs_server_release", "rs_server_drain", "rs_server_get_stats",
            "rs_server_destroy", "rs_tc_selftest", "rs_cluster_create", "rs_cluster_run", "rs_cluster_destroy",
-           "rs_warp"]
+           "rs_warp", "rs_plan_set_stream_form", "rs_plan_get_stream_form"]
 
 
 class RSError(RuntimeError):
@@ -233,6 +243,23 @@ def rs_plan_autotune(plan: int, d_in: int, d_out: int, stream: int = 0, cache_pa
     """Measured autotuning of the fused path on the caller's buffers."""
     cp = None if cache_path is None else os.fsencode(cache_path)
     _check(_lib.rs_plan_autotune(_vp(plan), _vp(d_in), _vp(d_out), _vp(stream), cp), "rs_plan_autotune")
+
+
+def rs_plan_set_stream_form(plan: int, kind: int, h_warps: int = 0, staged_blocks: int = 0,
+                            strip_width: int = 0, prefetch: int = 0, stream: int = 0, packed: int = 0,
+                            v_warps: int = 0) -> None:
+    """Runs the plan's row-streaming kernel in the given form (0 band kernel,
+    phase-alternating; 1 band kernel, warp-specialised; 2 pipelined, with
+    `prefetch`, `packed` and `v_warps` options)."""
+    f = rs_stream_form(int(kind), int(h_warps), int(staged_blocks), int(strip_width), int(prefetch),
+                       int(packed), int(v_warps))
+    _check(_lib.rs_plan_set_stream_form(_vp(plan), ctypes.byref(f), _vp(stream)), "rs_plan_set_stream_form")
+
+
+def rs_plan_get_stream_form(plan: int) -> rs_stream_form:
+    f = rs_stream_form()
+    _check(_lib.rs_plan_get_stream_form(_vp(plan), ctypes.byref(f)), "rs_plan_get_stream_form")
+    return f
 
 
 def rs_plan_recompute(plan: int, stream: int = 0) -> None:

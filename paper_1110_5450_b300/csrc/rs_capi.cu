@@ -881,8 +881,10 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
         o[a][0] = cv.take(size_t(g.n_out) * 4);
         o[a][1] = cv.take(size_t(g.n_out) * 4);
         o[a][2] = cv.take(size_t(g.n_out) * 4);
-        o[a][3] = cv.take(size_t(g.n_out) * g.t_eff * 8);
-        o[a][4] = cv.take(size_t(g.n_out) * g.t_eff * wsz);
+        // (the weight tables get 4 spare rows: kernels that read outputs in
+        // groups of 4 may read a last group's missing members)
+        o[a][3] = cv.take(size_t(g.n_out + 4) * g.t_eff * 8);
+        o[a][4] = cv.take(size_t(g.n_out + 4) * g.t_eff * wsz);
     }
     e = cudaMalloc(&p->tables.p, cv.off);
     if (e != cudaSuccess) {
@@ -901,7 +903,7 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
         t.w64 = reinterpret_cast<double *>(base + o[b][3]);
         t.wwork = base + o[b][4];
     }
-    e = cudaMemsetAsync(p->d_err, 0, 16, stream);
+    e = cudaMemsetAsync(p->tables.p, 0, p->tables.n, stream); // error word and spare rows start at zero
     if (e == cudaSuccess) e = launch_plan_weights(p, stream);
     if (e != cudaSuccess) {
         delete p;
@@ -1166,14 +1168,26 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
         double us_tile = 0;
         s = time_plan(p, d_in, d_out, stream, &us_tile);
         if (s != RS_OK) return s;
-        const int cands_s[][3] = {{0, 0, 3}, {0, 0, 2}, {1, 4, 3}, {1, 4, 2}, {1, 3, 3}, {1, 5, 3}, {1, 5, 2}};
+        // {pipelined kernel, warp-specialised, horizontal warps, staged blocks, L2 prefetch, packed,
+        //  vertical warps of the pipelined kernel}
+        const int cands_s[][7] = {{0, 0, 0, 3, 0, 0, 0}, {0, 0, 0, 2, 0, 0, 0}, {0, 1, 4, 3, 0, 0, 0},
+                                  {0, 1, 4, 2, 0, 0, 0}, {0, 1, 3, 3, 0, 0, 0}, {0, 1, 5, 3, 0, 0, 0},
+                                  {0, 1, 5, 2, 0, 0, 0}, {1, 0, 4, 2, 0, 0, 4}, {1, 0, 4, 2, 0, 0, 3},
+                                  {1, 0, 5, 2, 0, 0, 4}, {1, 0, 4, 2, 0, 0, 5}, {1, 0, 3, 2, 0, 0, 4},
+                                  {1, 0, 4, 3, 0, 0, 4}, {1, 0, 4, 2, 0, 1, 4}};
+        const bool x_ok = xstream::eligible(p);
         double best_s = 1e300;
         int best_code = 0;
         for (const auto &c : cands_s) {
+            if (c[0] && !x_ok) continue;
             stream::Opts o;
-            o.ws = c[0];
-            o.hw = c[1];
-            o.ni_min = c[2];
+            o.ex = c[0];
+            o.ws = c[1];
+            o.hw = c[2];
+            o.ni_min = c[3];
+            o.pf = c[4];
+            o.vp = c[5];
+            o.vw = c[6];
             // the cost model's three best strip widths for this configuration
             int w[3];
             const int nw = stream::widths(p, o, w, 3);
@@ -1269,6 +1283,56 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
     return RS_OK;
 }
 
+rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *stream_v)
+{
+    if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
+    if (f->kind < 0 || f->kind > 2 || f->h_warps < 0 || f->h_warps > 6 || f->v_warps < 0 || f->v_warps > 10 ||
+        (f->v_warps && f->kind != 2) || f->h_warps + f->v_warps > 11 || f->staged_blocks < 0 ||
+        f->staged_blocks > 4 || (f->staged_blocks > 0 && f->staged_blocks < 2) || f->strip_width < 0 ||
+        f->strip_width > 252 || f->strip_width % 4 || (f->prefetch != 0 && f->prefetch != 1) ||
+        (f->packed != 0 && f->packed != 1) || ((f->prefetch || f->packed) && f->kind != 2))
+        return fail(RS_ERR_INVALID_ARG, "malformed streaming form");
+    if (p->path != 0 || p->prefilter)
+        return fail(RS_ERR_UNSUPPORTED, "the plan has no fused path for the streaming kernel");
+    stream::Opts o;
+    o.ex = f->kind == 2 ? 1 : 0;
+    o.ws = f->kind == 1 ? 1 : 0;
+    o.hw = f->h_warps;
+    if (f->kind == 1 && f->h_warps == 1) return fail(RS_ERR_INVALID_ARG, "kind 1 takes 2..6 horizontal warps");
+    o.ni_min = f->staged_blocks ? f->staged_blocks : (f->kind == 2 ? 2 : 3);
+    o.sw = f->strip_width;
+    o.pf = f->prefetch;
+    o.vp = f->packed;
+    o.vw = f->v_warps;
+    // keep the previous configuration if the form cannot apply
+    const int keep_code = p->stream_ok ? p->stream_code : 0, keep_use = p->use_stream;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const rs_status s = stream::setup(p, stream, o);
+    if (s != RS_OK) {
+        if (keep_code) stream::setup(p, stream, stream::Opts::decode(keep_code));
+        p->use_stream = keep_use;
+        return s == RS_ERR_UNSUPPORTED ? fail(s, "the plan cannot take this streaming form") : s;
+    }
+    p->use_stream = 1;
+    p->use_vfirst = 0;
+    return RS_OK;
+}
+
+rs_status rs_plan_get_stream_form(const rs_plan *p, rs_stream_form *f)
+{
+    if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
+    if (!p->stream_ok) return fail(RS_ERR_UNSUPPORTED, "the plan has no streaming configuration");
+    const stream::Opts o = stream::Opts::decode(p->stream_code);
+    f->kind = o.ex > 0 ? 2 : (o.ws > 0 ? 1 : 0);
+    f->h_warps = p->x_on ? p->xp.HW : (o.ws > 0 ? p->sp.HW : 0);
+    f->staged_blocks = p->x_on ? p->xp.NI : p->sp.NI;
+    f->strip_width = p->x_on ? p->xp.SW : p->sp.SW;
+    f->prefetch = p->x_on ? p->xp.pf : 0;
+    f->packed = p->x_on ? p->xp.vp : 0;
+    f->v_warps = p->x_on ? p->xp.VW : 0;
+    return RS_OK;
+}
+
 rs_status rs_plan_recompute(rs_plan *p, void *stream_v)
 {
     const Range range("rs_plan_recompute");
@@ -1337,6 +1401,17 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
         info->stages = 0;
         info->smem_bytes = 0;
         info->ctas_per_sm = 0;
+    } else if (p->path == 0 && p->use_stream && p->x_on) {
+        info->path = 3;
+        info->tile_h = xstream::kRB;
+        info->tile_w = p->xp.SW;
+        info->group_h = info->group_w = xstream::kG;
+        info->span_h = p->xp.JV;
+        info->span_w = p->xp.JH;
+        info->warps_pass1 = p->xp.HW; // horizontal warps (vertical: 7 - this)
+        info->stages = p->xp.NI;
+        info->smem_bytes = int32_t(p->s_smem);
+        info->ctas_per_sm = p->s_ctas;
     } else if (p->path == 0 && p->use_stream) {
         info->path = 3;
         info->tile_h = stream::kRB;

@@ -12,6 +12,7 @@
 #include "rs_fused.cuh"
 #include "rs_internal.h"
 #include "rs_stream.cuh"
+#include "rs_xstream.cuh"
 
 namespace rs {
 
@@ -101,8 +102,15 @@ struct rs_plan {
     CUtensorMap stmap;
     const void *stmap_ptr = nullptr;
     const void *s_fn = nullptr;
+    int s_block = 0; // threads per CTA of the streaming kernel in use
     size_t s_smem = 0;
     int s_grid = 0, s_ctas = 0;
+    // the pipelined form of the streaming kernel (upscales, 4 or 6 taps):
+    // when x_on, s_fn / s_smem / s_grid / s_ctas describe it and xp holds its
+    // parameters (its group descriptors live in xbufs)
+    int x_on = 0;
+    rs::xstream::Params xp{};
+    rs::DeviceBuf xbufs;
     // interpolating cubic B-spline: coefficients of the input (RS_PREFILTER)
     int prefilter = 0;
     rs::DeviceBuf pbufs;
@@ -165,13 +173,25 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 } // namespace vfirst
 
 namespace stream {
-// Choices of a streaming configuration: ws = 1 warp-specialised kernel, 0
-// phase-alternating, -1 either (warp-specialised first); hw = warps on the
-// horizontal pass (0: 4); ni_min = fewest staged input blocks of a narrow strip.
+// Choices of a streaming configuration: ex = 1 the pipelined kernel
+// (rs_xstream.cuh), 0 the band kernels of rs_stream.cuh, -1 the pipelined
+// kernel where it applies with its default choices, else the band kernels; ws = 1
+// warp-specialised band kernel, 0 phase-alternating, -1 either
+// (warp-specialised first); hw = warps on the horizontal pass (0: the form's
+// default); ni_min = fewest staged input blocks of a narrow strip (the
+// pipelined kernel: its staged blocks); pf = 1: the pipelined kernel
+// prefetches the block after its ring into L2.
 struct Opts {
     int ws = -1, hw = 0, ni_min = 3;
     int sw = 0; // strip width (0: the cost model's choice)
-    int code() const { return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4); }
+    int ex = -1, pf = 0;
+    int vp = 0; // pipelined kernel: 1 = packed FP32 pairs in the vertical pass
+    int vw = 0; // pipelined kernel: warps on the vertical pass (0: the default)
+    int code() const
+    {
+        return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4) + (ex > 0 ? 32768 : 0) + (pf ? 65536 : 0) +
+               (vp ? 131072 : 0) + (vw << 18);
+    }
     static Opts decode(int c)
     {
         Opts o;
@@ -179,6 +199,10 @@ struct Opts {
         o.hw = (c >> 2) & 15;
         o.ni_min = (c >> 6) & 7;
         o.sw = ((c >> 9) & 63) * 4;
+        o.ex = (c >> 15) & 1;
+        o.pf = (c >> 16) & 1;
+        o.vp = (c >> 17) & 1;
+        o.vw = (c >> 18) & 15;
         return o;
     }
 };
@@ -192,5 +216,18 @@ int widths(rs_plan *p, const Opts &o, int *out, int n);
 rs_status rebuild(rs_plan *p, cudaStream_t s);
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 } // namespace stream
+
+namespace xstream {
+// Whether the plan can run the pipelined kernel (FP32/FP16/BF16, 1 or 3
+// channels, a 16-byte row pitch, 4 or 6 taps per output on both axes, window
+// starts that advance by 0 or 1 per output: an upscale or scale 1).
+bool eligible(const rs_plan *p);
+// Configures it (o.hw horizontal warps, o.ni_min staged blocks, o.sw strip
+// width, o.pf, o.vp; zeros choose the defaults); RS_ERR_UNSUPPORTED when the plan
+// is not eligible.  The kernel reads the plan's weight tables directly.
+rs_status setup(rs_plan *p, const stream::Opts &o);
+// Strip widths it admits, best first by the cost model (at most n).
+int widths(rs_plan *p, const stream::Opts &o, int *out, int n);
+} // namespace xstream
 
 } // namespace rs

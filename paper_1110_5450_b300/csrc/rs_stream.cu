@@ -237,6 +237,7 @@ rs_status bands_of(const rs_plan *p, Bands &b)
 
 int widths(rs_plan *p, const Opts &opts, int *out, int n)
 {
+    if (opts.ex > 0) return xstream::widths(p, opts, out, n);
     Bands b;
     if (bands_of(p, b) != RS_OK) return 0;
     const std::vector<Strip> c = strips(p, opts, b.C, b.groups_x, b.hb, b.JH, b.JV, b.GV, b.WP, b.vb, b.pairs);
@@ -248,6 +249,12 @@ int widths(rs_plan *p, const Opts &opts, int *out, int n)
 rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
 {
     p->stream_ok = 0;
+    // the exact-window form where it applies (or when asked for)
+    if (opts.ex != 0) {
+        const rs_status xs = xstream::setup(p, opts);
+        if (xs == RS_OK || opts.ex > 0) return xs;
+    }
+    p->x_on = 0;
     Bands bd;
     const rs_status bst = bands_of(p, bd);
     if (bst != RS_OK) return bst;
@@ -337,6 +344,7 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
 
 rs_status rebuild(rs_plan *p, cudaStream_t s)
 {
+    if (p->x_on) return RS_OK; // the exact-window kernel reads the weight tables directly
     // both bands in one launch of the band kernel:
     //  * vertical: groups of 4 rows, every weight twice -> per tap (w0, w0, .., w3, w3);
     //  * horizontal: groups of 4 outputs, 4-pixel aligned bases, per pixel (w0, .., w3)
@@ -378,7 +386,7 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s)
         cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};
         const int es = dt_size(d.in_dtype);
         cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * es)};
-        cuuint32_t box[2] = {cuuint32_t(p->sp.P), cuuint32_t(kRB)};
+        cuuint32_t box[2] = {cuuint32_t(p->x_on ? p->xp.P : p->sp.P), cuuint32_t(kRB)};
         cuuint32_t estr[2] = {1, 1};
         const CUtensorMapDataType ty = d.in_dtype == RS_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                        : d.in_dtype == RS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -392,8 +400,11 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s)
     Params sp = p->sp;
     sp.in = d_in;
     sp.out = d_out;
-    void *args[2] = {&p->stmap, &sp};
-    cudaError_t e = cudaLaunchKernel(p->s_fn, dim3(p->s_grid), dim3(kThreads), args, p->s_smem, s);
+    xstream::Params xp = p->xp;
+    xp.in = d_in;
+    xp.out = d_out;
+    void *args[2] = {&p->stmap, p->x_on ? static_cast<void *>(&xp) : static_cast<void *>(&sp)};
+    cudaError_t e = cudaLaunchKernel(p->s_fn, dim3(p->s_grid), dim3(p->x_on ? p->s_block : kThreads), args, p->s_smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "stream kernel launch");
     return RS_OK;
 }

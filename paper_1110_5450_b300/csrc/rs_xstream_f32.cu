@@ -1,0 +1,11 @@
+// rs_xstream_f32.cu -- the pipelined streaming kernel instantiated for
+// float storage (one translation unit per storage type keeps the builds parallel).
+#include "rs_xstream.cuh"
+
+namespace rs {
+namespace xstream {
+
+const void *kernel_f32(int C, int taps, int vp) { return kernel_table<float>(C, taps, vp); }
+
+} // namespace xstream
+} // namespace rs
