@@ -232,6 +232,8 @@ typedef struct {
                               (fma.rn.f32x2; bitwise the same as scalar FMAs)        */
     int32_t v_warps;       /* kind 2: warps on the vertical pass (a CTA has one producer
                               warp plus h_warps + v_warps <= 11)                      */
+    int32_t row_ranges;    /* kind 2: output row ranges, one CTA per (strip, range);
+                              1..255                                                  */
 } rs_stream_form;
 
 /* Makes the plan run the row-streaming kernel in the given form (configuring

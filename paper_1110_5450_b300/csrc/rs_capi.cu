@@ -1287,7 +1287,8 @@ rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *str
 {
     if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
     if (f->kind < 0 || f->kind > 2 || f->h_warps < 0 || f->h_warps > 6 || f->v_warps < 0 || f->v_warps > 10 ||
-        (f->v_warps && f->kind != 2) || f->h_warps + f->v_warps > 11 || f->staged_blocks < 0 ||
+        (f->v_warps && f->kind != 2) || f->h_warps + f->v_warps > 11 || f->row_ranges < 0 || f->row_ranges > 255 ||
+        (f->row_ranges && f->kind != 2) || f->staged_blocks < 0 ||
         f->staged_blocks > 4 || (f->staged_blocks > 0 && f->staged_blocks < 2) || f->strip_width < 0 ||
         f->strip_width > 252 || f->strip_width % 4 || (f->prefetch != 0 && f->prefetch != 1) ||
         (f->packed != 0 && f->packed != 1) || ((f->prefetch || f->packed) && f->kind != 2))
@@ -1304,6 +1305,7 @@ rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *str
     o.pf = f->prefetch;
     o.vp = f->packed;
     o.vw = f->v_warps;
+    o.nr = f->row_ranges;
     // keep the previous configuration if the form cannot apply
     const int keep_code = p->stream_ok ? p->stream_code : 0, keep_use = p->use_stream;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
@@ -1330,6 +1332,7 @@ rs_status rs_plan_get_stream_form(const rs_plan *p, rs_stream_form *f)
     f->prefetch = p->x_on ? p->xp.pf : 0;
     f->packed = p->x_on ? p->xp.vp : 0;
     f->v_warps = p->x_on ? p->xp.VW : 0;
+    f->row_ranges = p->x_on ? (p->xp.groups_y + p->xp.gpr - 1) / p->xp.gpr : 0;
     return RS_OK;
 }
 

@@ -187,10 +187,11 @@ struct Opts {
     int ex = -1, pf = 0;
     int vp = 0; // pipelined kernel: 1 = packed FP32 pairs in the vertical pass
     int vw = 0; // pipelined kernel: warps on the vertical pass (0: the default)
+    int nr = 0; // pipelined kernel: row ranges (0: the cost model's choice), < 256
     int code() const
     {
         return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4) + (ex > 0 ? 32768 : 0) + (pf ? 65536 : 0) +
-               (vp ? 131072 : 0) + (vw << 18);
+               (vp ? 131072 : 0) + (vw << 18) + (nr << 22);
     }
     static Opts decode(int c)
     {
@@ -203,6 +204,7 @@ struct Opts {
         o.pf = (c >> 16) & 1;
         o.vp = (c >> 17) & 1;
         o.vw = (c >> 18) & 15;
+        o.nr = (c >> 22) & 255;
         return o;
     }
 };

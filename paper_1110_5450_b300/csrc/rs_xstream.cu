@@ -111,7 +111,7 @@ rs_status geometry(const rs_plan *p, Geometry &g, int vp)
 // Every strip width (a multiple of 4 outputs) whose staged rows fit one or two
 // TMA boxes, with its best row ranges by a cost model (the busiest SM's CTAs
 // times each CTA's work), cheapest first.
-std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nthreads)
+std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nthreads, int nr_force)
 {
     std::vector<Choice> out;
     const int C = g.C, es = g.es;
@@ -158,9 +158,9 @@ std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nth
             if (!P) continue;
         }
         Choice best;
-        for (int nr = 1; nr <= 4096; ++nr) {
+        for (int nr = nr_force > 0 ? nr_force : 1; nr <= (nr_force > 0 ? nr_force : 4096); ++nr) {
             const int gpr = (g.groups_y + nr - 1) / nr;
-            if (gpr < 8 && nr > 1) break;
+            if (gpr < 8 && nr > 1 && nr_force <= 0) break;
             const int ranges = (g.groups_y + gpr - 1) / gpr;
             int rows = 0;
             for (int q0 = 0; q0 < g.groups_y; q0 += gpr) {
@@ -231,7 +231,7 @@ int widths(rs_plan *p, const stream::Opts &o, int *out, int n)
     const int NI = o.ex > 0 && o.ni_min >= 2 && o.ni_min <= kMaxNI ? o.ni_min : 2;
     int HW, VW;
     warps_of(o, HW, VW);
-    const std::vector<Choice> c = choices(p, g, NI, 32 * (1 + HW + VW));
+    const std::vector<Choice> c = choices(p, g, NI, 32 * (1 + HW + VW), o.ex > 0 ? o.nr : 0);
     int k = 0;
     for (; k < n && k < int(c.size()); ++k) out[k] = c[k].sw;
     return k;
@@ -248,7 +248,7 @@ rs_status setup(rs_plan *p, const stream::Opts &o)
     const int NI = o.ex > 0 && o.ni_min >= 2 && o.ni_min <= kMaxNI ? o.ni_min : 2;
     int HW, VW;
     warps_of(o, HW, VW);
-    const std::vector<Choice> cands = choices(p, g, NI, 32 * (1 + HW + VW));
+    const std::vector<Choice> cands = choices(p, g, NI, 32 * (1 + HW + VW), o.ex > 0 ? o.nr : 0);
     if (cands.empty()) return RS_ERR_UNSUPPORTED;
     const Choice *pick = &cands[0];
     if (o.sw > 0) {
@@ -314,6 +314,7 @@ rs_status setup(rs_plan *p, const stream::Opts &o)
         used.ws = 0;
         used.hw = HW;
         used.vw = VW;
+        used.nr = o.ex > 0 ? o.nr : 0;
         used.ni_min = NI;
         used.sw = pick->sw;
         used.pf = xp.pf;
