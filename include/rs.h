@@ -223,15 +223,14 @@ RS_API rs_status rs_plan_autotune(rs_plan *plan, const void *d_in, void *d_out, 
  * increasing order, FP32 accumulation; band zeros add exact zeros). */
 typedef struct {
     int32_t kind;          /* 0, 1 or 2 as above                                      */
-    int32_t h_warps;       /* warps on the horizontal pass (kind 1: 2..6; kind 2: 1..6) */
+    int32_t h_warps;       /* warps on the horizontal pass (kind 1: 2..6; kind 2: 1..8) */
     int32_t staged_blocks; /* staged 32-row input blocks, 2..4                          */
     int32_t strip_width;   /* output pixels per strip (a multiple of 4)                 */
     int32_t prefetch;      /* kind 2: 1 = prefetch the block after the staging ring
                               into L2                                                 */
-    int32_t packed;        /* kind 2: 1 = the vertical pass multiplies packed FP32 pairs
-                              (fma.rn.f32x2; bitwise the same as scalar FMAs)        */
     int32_t v_warps;       /* kind 2: warps on the vertical pass (a CTA has one producer
-                              warp plus h_warps + v_warps <= 11)                      */
+                              warp plus h_warps + v_warps <= 15; above 11 the CTA
+                              takes a whole SM)                                       */
     int32_t row_ranges;    /* kind 2: output row ranges, one CTA per (strip, range);
                               1..255                                                  */
 } rs_stream_form;

@@ -68,7 +68,7 @@ class rs_plan_info(ctypes.Structure):
 
 class rs_stream_form(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("h_warps", ctypes.c_int32), ("staged_blocks", ctypes.c_int32),
-                ("strip_width", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("packed", ctypes.c_int32),
+                ("strip_width", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("v_warps", ctypes.c_int32), ("row_ranges", ctypes.c_int32)]
 
 
@@ -246,13 +246,13 @@ def rs_plan_autotune(plan: int, d_in: int, d_out: int, stream: int = 0, cache_pa
 
 
 def rs_plan_set_stream_form(plan: int, kind: int, h_warps: int = 0, staged_blocks: int = 0,
-                            strip_width: int = 0, prefetch: int = 0, stream: int = 0, packed: int = 0,
-                            v_warps: int = 0, row_ranges: int = 0) -> None:
+                            strip_width: int = 0, prefetch: int = 0, stream: int = 0, v_warps: int = 0,
+                            row_ranges: int = 0) -> None:
     """Runs the plan's row-streaming kernel in the given form (0 band kernel,
     phase-alternating; 1 band kernel, warp-specialised; 2 pipelined, with
-    `prefetch`, `packed`, `v_warps` and `row_ranges` options)."""
+    `prefetch`, `v_warps` and `row_ranges` options)."""
     f = rs_stream_form(int(kind), int(h_warps), int(staged_blocks), int(strip_width), int(prefetch),
-                       int(packed), int(v_warps), int(row_ranges))
+                       int(v_warps), int(row_ranges))
     _check(_lib.rs_plan_set_stream_form(_vp(plan), ctypes.byref(f), _vp(stream)), "rs_plan_set_stream_form")
 
 

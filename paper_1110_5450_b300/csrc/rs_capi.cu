@@ -1168,13 +1168,13 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
         double us_tile = 0;
         s = time_plan(p, d_in, d_out, stream, &us_tile);
         if (s != RS_OK) return s;
-        // {pipelined kernel, warp-specialised, horizontal warps, staged blocks, L2 prefetch, packed,
+        // {pipelined kernel, warp-specialised, horizontal warps, staged blocks, L2 prefetch, unused,
         //  vertical warps of the pipelined kernel}
         const int cands_s[][7] = {{0, 0, 0, 3, 0, 0, 0}, {0, 0, 0, 2, 0, 0, 0}, {0, 1, 4, 3, 0, 0, 0},
                                   {0, 1, 4, 2, 0, 0, 0}, {0, 1, 3, 3, 0, 0, 0}, {0, 1, 5, 3, 0, 0, 0},
                                   {0, 1, 5, 2, 0, 0, 0}, {1, 0, 4, 2, 0, 0, 4}, {1, 0, 4, 2, 0, 0, 3},
                                   {1, 0, 5, 2, 0, 0, 4}, {1, 0, 4, 2, 0, 0, 5}, {1, 0, 3, 2, 0, 0, 4},
-                                  {1, 0, 4, 3, 0, 0, 4}, {1, 0, 4, 2, 0, 1, 4}};
+                                  {1, 0, 4, 3, 0, 0, 4}, {1, 0, 7, 2, 0, 0, 8}, {1, 0, 8, 2, 0, 0, 7}};
         const bool x_ok = xstream::eligible(p);
         double best_s = 1e300;
         int best_code = 0;
@@ -1186,7 +1186,6 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
             o.hw = c[2];
             o.ni_min = c[3];
             o.pf = c[4];
-            o.vp = c[5];
             o.vw = c[6];
             // the cost model's three best strip widths for this configuration
             int w[3];
@@ -1286,12 +1285,13 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
 rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *stream_v)
 {
     if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
-    if (f->kind < 0 || f->kind > 2 || f->h_warps < 0 || f->h_warps > 6 || f->v_warps < 0 || f->v_warps > 10 ||
-        (f->v_warps && f->kind != 2) || f->h_warps + f->v_warps > 11 || f->row_ranges < 0 || f->row_ranges > 255 ||
+    if (f->kind < 0 || f->kind > 2 || f->h_warps < 0 || f->h_warps > 8 || (f->kind != 2 && f->h_warps > 6) ||
+        f->v_warps < 0 || f->v_warps > 12 || (f->v_warps && f->kind != 2) || f->h_warps + f->v_warps > 15 ||
+        f->row_ranges < 0 || f->row_ranges > 255 ||
         (f->row_ranges && f->kind != 2) || f->staged_blocks < 0 ||
         f->staged_blocks > 4 || (f->staged_blocks > 0 && f->staged_blocks < 2) || f->strip_width < 0 ||
         f->strip_width > 252 || f->strip_width % 4 || (f->prefetch != 0 && f->prefetch != 1) ||
-        (f->packed != 0 && f->packed != 1) || ((f->prefetch || f->packed) && f->kind != 2))
+        (f->prefetch && f->kind != 2))
         return fail(RS_ERR_INVALID_ARG, "malformed streaming form");
     if (p->path != 0 || p->prefilter)
         return fail(RS_ERR_UNSUPPORTED, "the plan has no fused path for the streaming kernel");
@@ -1303,7 +1303,6 @@ rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *str
     o.ni_min = f->staged_blocks ? f->staged_blocks : (f->kind == 2 ? 2 : 3);
     o.sw = f->strip_width;
     o.pf = f->prefetch;
-    o.vp = f->packed;
     o.vw = f->v_warps;
     o.nr = f->row_ranges;
     // keep the previous configuration if the form cannot apply
@@ -1330,7 +1329,6 @@ rs_status rs_plan_get_stream_form(const rs_plan *p, rs_stream_form *f)
     f->staged_blocks = p->x_on ? p->xp.NI : p->sp.NI;
     f->strip_width = p->x_on ? p->xp.SW : p->sp.SW;
     f->prefetch = p->x_on ? p->xp.pf : 0;
-    f->packed = p->x_on ? p->xp.vp : 0;
     f->v_warps = p->x_on ? p->xp.VW : 0;
     f->row_ranges = p->x_on ? (p->xp.groups_y + p->xp.gpr - 1) / p->xp.gpr : 0;
     return RS_OK;

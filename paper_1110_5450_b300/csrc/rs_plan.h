@@ -185,13 +185,12 @@ struct Opts {
     int ws = -1, hw = 0, ni_min = 3;
     int sw = 0; // strip width (0: the cost model's choice)
     int ex = -1, pf = 0;
-    int vp = 0; // pipelined kernel: 1 = packed FP32 pairs in the vertical pass
     int vw = 0; // pipelined kernel: warps on the vertical pass (0: the default)
     int nr = 0; // pipelined kernel: row ranges (0: the cost model's choice), < 256
     int code() const
     {
         return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4) + (ex > 0 ? 32768 : 0) + (pf ? 65536 : 0) +
-               (vp ? 131072 : 0) + (vw << 18) + (nr << 22);
+               (vw << 18) + (nr << 22);
     }
     static Opts decode(int c)
     {
@@ -202,7 +201,6 @@ struct Opts {
         o.sw = ((c >> 9) & 63) * 4;
         o.ex = (c >> 15) & 1;
         o.pf = (c >> 16) & 1;
-        o.vp = (c >> 17) & 1;
         o.vw = (c >> 18) & 15;
         o.nr = (c >> 22) & 255;
         return o;
@@ -225,7 +223,7 @@ namespace xstream {
 // starts that advance by 0 or 1 per output: an upscale or scale 1).
 bool eligible(const rs_plan *p);
 // Configures it (o.hw horizontal warps, o.ni_min staged blocks, o.sw strip
-// width, o.pf, o.vp; zeros choose the defaults); RS_ERR_UNSUPPORTED when the plan
+// width, o.pf, o.vw, o.nr; zeros choose the defaults); RS_ERR_UNSUPPORTED when the plan
 // is not eligible.  The kernel reads the plan's weight tables directly.
 rs_status setup(rs_plan *p, const stream::Opts &o);
 // Strip widths it admits, best first by the cost model (at most n).

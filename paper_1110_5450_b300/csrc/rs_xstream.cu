@@ -16,12 +16,12 @@ namespace rs {
 namespace xstream {
 namespace {
 
-const void *kernel_for(int dtype, int C, int taps, int vp)
+const void *kernel_for(int dtype, int C, int taps, int big)
 {
     switch (dtype) {
-    case RS_F32: return kernel_f32(C, taps, vp);
-    case RS_F16: return kernel_f16(C, taps, vp);
-    case RS_BF16: return kernel_bf16(C, taps, vp);
+    case RS_F32: return kernel_f32(C, taps, big);
+    case RS_F16: return kernel_f16(C, taps, big);
+    case RS_BF16: return kernel_bf16(C, taps, big);
     }
     return nullptr;
 }
@@ -72,14 +72,12 @@ struct Choice {
 };
 
 struct Geometry {
-    int C = 0, T = 0, es = 0, groups_x = 0, groups_y = 0, JH = 0, JV = 0, WP = 0, vp = 0;
+    int C = 0, T = 0, es = 0, groups_x = 0, groups_y = 0, JH = 0, JV = 0, WP = 0;
     std::vector<int32_t> hinfo, vinfo, hend, vend;
 };
 
-// vp: the packed vertical pass (its bands take twice the space).
-rs_status geometry(const rs_plan *p, Geometry &g, int vp)
+rs_status geometry(const rs_plan *p, Geometry &g)
 {
-    g.vp = vp;
     const rs_plan_desc &d = p->desc;
     g.C = d.channels;
     if ((d.in_dtype != RS_F32 && d.in_dtype != RS_F16 && d.in_dtype != RS_BF16) || d.out_dtype != d.in_dtype ||
@@ -87,7 +85,7 @@ rs_status geometry(const rs_plan *p, Geometry &g, int vp)
         return RS_ERR_UNSUPPORTED;
     if (!tma_layout_ok(p)) return RS_ERR_UNSUPPORTED;
     g.T = p->gx.t_eff;
-    if (p->gy.t_eff != g.T || (g.T != 4 && g.T != 6) || !kernel_for(d.in_dtype, g.C, g.T, vp))
+    if (p->gy.t_eff != g.T || (g.T != 4 && g.T != 6) || !kernel_for(d.in_dtype, g.C, g.T, 0))
         return RS_ERR_UNSUPPORTED;
     g.es = int(dt_size(d.in_dtype));
     if (!groups_of(p->host_start_x, int(p->gx.n_in), g.T, 4, g.hinfo, g.hend)) return RS_ERR_UNSUPPORTED;
@@ -116,7 +114,7 @@ std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nth
     std::vector<Choice> out;
     const int C = g.C, es = g.es;
     const int HR = 2 * kRB + g.JV, M = g.JV - 1, Q = (HR + M) | 1;
-    const void *fn = kernel_for(p->desc.in_dtype, C, g.T, g.vp);
+    const void *fn = kernel_for(p->desc.in_dtype, C, g.T, nthreads > 32 * kSmallWarps ? 1 : 0);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess) {
         cudaGetLastError();
         return out;
@@ -169,7 +167,7 @@ std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nth
             }
             const int nblk = (rows + kRB - 1) / kRB;
             if (nblk <= 512) {
-                const size_t smem = layout(NI, P, Q, nch, ngx, g.T, g.WP, nblk, offB != 0, es, g.vp).total;
+                const size_t smem = layout(NI, P, Q, nch, ngx, g.T, g.WP, nblk, offB != 0, es).total;
                 const int occ = smem <= 227 * 1024 ? occupancy(smem) : 0;
                 if (occ >= 1) {
                     const int64_t grid = int64_t(n_strips) * ranges;
@@ -221,13 +219,13 @@ void warps_of(const stream::Opts &o, int &HW, int &VW)
 bool eligible(const rs_plan *p)
 {
     Geometry g;
-    return geometry(p, g, 0) == RS_OK;
+    return geometry(p, g) == RS_OK;
 }
 
 int widths(rs_plan *p, const stream::Opts &o, int *out, int n)
 {
     Geometry g;
-    if (geometry(p, g, o.ex > 0 ? o.vp : 0) != RS_OK) return 0;
+    if (geometry(p, g) != RS_OK) return 0;
     const int NI = o.ex > 0 && o.ni_min >= 2 && o.ni_min <= kMaxNI ? o.ni_min : 2;
     int HW, VW;
     warps_of(o, HW, VW);
@@ -241,8 +239,7 @@ rs_status setup(rs_plan *p, const stream::Opts &o)
 {
     p->x_on = 0;
     Geometry g;
-    const int vp = o.ex > 0 ? o.vp : 0;
-    const rs_status gs = geometry(p, g, vp);
+    const rs_status gs = geometry(p, g);
     if (gs != RS_OK) return gs;
     // the caller's choices apply to this form only when it asked for it (ex = 1)
     const int NI = o.ex > 0 && o.ni_min >= 2 && o.ni_min <= kMaxNI ? o.ni_min : 2;
@@ -306,7 +303,7 @@ rs_status setup(rs_plan *p, const stream::Opts &o)
     xp.HW = HW;
     xp.VW = VW;
     xp.pf = o.ex > 0 && o.pf ? 1 : 0;
-    xp.vp = vp;
+
     xp.err = p->d_err;
     {
         stream::Opts used;
@@ -318,10 +315,10 @@ rs_status setup(rs_plan *p, const stream::Opts &o)
         used.ni_min = NI;
         used.sw = pick->sw;
         used.pf = xp.pf;
-        used.vp = vp;
+
         p->stream_code = used.code();
     }
-    p->s_fn = kernel_for(d.in_dtype, g.C, g.T, vp);
+    p->s_fn = kernel_for(d.in_dtype, g.C, g.T, 1 + HW + VW > kSmallWarps ? 1 : 0);
     p->s_block = 32 * (1 + HW + VW);
     p->s_smem = pick->smem;
     p->s_grid = pick->grid;

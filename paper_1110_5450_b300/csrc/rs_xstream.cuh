@@ -47,8 +47,8 @@
 namespace rs {
 namespace xstream {
 
-constexpr int kMaxWarps = 12; // producer + horizontal + vertical warps of a CTA, at most
-constexpr int kMaxThreads = 32 * kMaxWarps;
+constexpr int kMaxWarps = 16;   // producer + horizontal + vertical warps of a CTA, at most
+constexpr int kSmallWarps = 12; // at most this many: the kernel variant for 2 CTAs per SM
 constexpr int kRB = 32;   // input rows per staged block (one per lane of a horizontal task)
 constexpr int kG = 4;     // outputs per group (columns across, rows down)
 constexpr int kMaxNI = 4; // staged input blocks at most
@@ -82,7 +82,6 @@ struct Params {
     int32_t nblk;    // most blocks of a row range (shared-memory table size)
     int32_t HW, VW;  // horizontal / vertical warps (the CTA has 1 + HW + VW warps)
     int32_t pf;      // 1: prefetch the block after the ring into L2
-    int32_t vp;      // 1: packed FP32 pairs in the vertical pass (the kernel's template argument)
     int *err;
 };
 
@@ -96,7 +95,7 @@ struct Layout {
 };
 
 __host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx, int T, int WP, int nblk,
-                                         bool two_boxes, int es, int vp)
+                                         bool two_boxes, int es)
 {
     const int HB = T + 3;
     Layout L;
@@ -105,7 +104,7 @@ __host__ __device__ inline Layout layout(int NI, int P, int Q, int nch, int ngx,
     L.wv = size_t(WP) * kG * T * 4;
     L.vi = fused::align_up(size_t(WP + 8) * 4, 16);
     L.stg = fused::align_up(L.wv + L.vi, 128);
-    L.vb = size_t(WP) * kG * HB * 4 * (vp ? 2 : 1);
+    L.vb = size_t(WP) * kG * HB * 4;
     L.bslot = fused::align_up(L.vb + size_t(WP) * 4, 128);
     L.b_ring = size_t(kNW) * L.bslot;
     L.hring = fused::align_up(size_t(nch) * Q * 16, 128);
@@ -206,52 +205,27 @@ __device__ __forceinline__ void h_dispatch(int o0, const float (&win)[3][4 * C],
 
 // Vertical pass of one row group for one 4-sample ring column: src = the
 // column at the group's first window row, wb = the group's band, j-major (the
-// 4 rows' weights at ring row j; with VP every weight twice, for packed
-// pairs); writes the group's 4 output rows of the column.
-template <typename T, int TAPS, int VP>
+// 4 rows' weights at ring row j); writes the group's 4 output rows of the
+// column.
+template <typename T, int TAPS>
 __device__ __forceinline__ void v_band(const float4 *src, const float4 *wb, T *o, int64_t out_stride, int rows,
                                        int nsamp, bool vec_ok)
 {
     constexpr int HB = TAPS + 3;
     float a[kG][4];
-    if constexpr (VP) {
-        uint64_t acc[kG][2];
 #pragma unroll
-        for (int r = 0; r < kG; ++r) acc[r][0] = acc[r][1] = 0ull;
-        const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
-        const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(wb);
+    for (int r = 0; r < kG; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
 #pragma unroll
-        for (int j = 0; j < HB; ++j) {
-            const ulonglong2 d = s2[j];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const ulonglong2 w = w2[2 * j + h]; // rows 2h, 2h + 1, each weight twice
-                acc[2 * h][0] = fused::fma2(w.x, d.x, acc[2 * h][0]);
-                acc[2 * h][1] = fused::fma2(w.x, d.y, acc[2 * h][1]);
-                acc[2 * h + 1][0] = fused::fma2(w.y, d.x, acc[2 * h + 1][0]);
-                acc[2 * h + 1][1] = fused::fma2(w.y, d.y, acc[2 * h + 1][1]);
-            }
-        }
+    for (int j = 0; j < HB; ++j) {
+        const float4 d = src[j];
+        const float4 wq = wb[j];
+        const float wr[kG] = {wq.x, wq.y, wq.z, wq.w};
 #pragma unroll
         for (int r = 0; r < kG; ++r) {
-            fused::unpack2(acc[r][0], a[r][0], a[r][1]);
-            fused::unpack2(acc[r][1], a[r][2], a[r][3]);
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < kG; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = 0.f;
-#pragma unroll
-        for (int j = 0; j < HB; ++j) {
-            const float4 d = src[j];
-            const float4 wq = wb[j];
-            const float wr[kG] = {wq.x, wq.y, wq.z, wq.w};
-#pragma unroll
-            for (int r = 0; r < kG; ++r) {
-                a[r][0] = fmaf(wr[r], d.x, a[r][0]);
-                a[r][1] = fmaf(wr[r], d.y, a[r][1]);
-                a[r][2] = fmaf(wr[r], d.z, a[r][2]);
-                a[r][3] = fmaf(wr[r], d.w, a[r][3]);
-            }
+            a[r][0] = fmaf(wr[r], d.x, a[r][0]);
+            a[r][1] = fmaf(wr[r], d.y, a[r][1]);
+            a[r][2] = fmaf(wr[r], d.z, a[r][2]);
+            a[r][3] = fmaf(wr[r], d.w, a[r][3]);
         }
     }
     if (rows == kG && nsamp == 4 && vec_ok) {
@@ -273,18 +247,20 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
     return __all_sync(0xffffffffu, ok);
 }
 
-template <typename T, int C, int TAPS, int VP>
-__global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+// BIG = 0: up to kSmallWarps warps, two CTAs per SM (at most 85 registers a
+// thread); BIG = 1: up to kMaxWarps warps, one CTA per SM.
+template <typename T, int C, int TAPS, int BIG>
+__global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ? 1 : 2)
+    xstream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
 {
-    constexpr int HB = TAPS + 3;     // band width
-    constexpr int GB = kG * HB;      // band weights per group
-    constexpr int VB = GB * (VP + 1); // vertical band floats per group (VP: every weight twice)
+    constexpr int HB = TAPS + 3; // band width
+    constexpr int GB = kG * HB;  // band weights per group
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (fused::smem_addr(smem_raw) & 127u)) & 127u);
     const int ngx = p.SW / kG;
     const int P = p.P, Q = p.Q, HR = p.HR, M = p.M, NI = p.NI, WP = p.WP;
     const int nch = (p.SW * C) / 4; // 4-sample ring columns
-    const Layout L = layout(NI, P, Q, nch, ngx, TAPS, WP, p.nblk, p.offB != 0, int(sizeof(T)), VP);
+    const Layout L = layout(NI, P, Q, nch, ngx, TAPS, WP, p.nblk, p.offB != 0, int(sizeof(T)));
     unsigned char *in_ring = smem;
     unsigned char *stg = in_ring + L.in_ring;
     unsigned char *b_ring = stg + L.stg;
@@ -318,6 +294,18 @@ __global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_co
     };
     const int r_lo = __ldg(p.vinfo + p0) & 0xffffff;
     const int nblk = min((last_row(p1 - 1) + 1 - r_lo + kRB - 1) / kRB, p.nblk);
+    const uint32_t blk_bytes = uint32_t(kRB) * P * sizeof(T) * (p.offB ? 2u : 1u);
+    // one thread: the input copy of block k into slot k % NI
+    auto issue_in = [&](int k) {
+        const int s = k % NI;
+        fused::mbar_arrive_expect_tx(&full_in[s], blk_bytes);
+        fused::tma_load_2d(slot_in(s), &tmap, &full_in[s], xs, r_lo + k * kRB);
+        if (p.offB) fused::tma_load_2d(slot_in(s) + kRB * P, &tmap, &full_in[s], xs + p.offB, r_lo + k * kRB);
+        if (p.pf && k + NI < nblk) {
+            fused::tma_prefetch_2d(&tmap, xs, r_lo + (k + NI) * kRB);
+            if (p.offB) fused::tma_prefetch_2d(&tmap, xs + p.offB, r_lo + (k + NI) * kRB);
+        }
+    };
 
     if (tid == 0) {
         for (int s = 0; s < NI; ++s) {
@@ -335,6 +323,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_co
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // the first staged blocks' copies, so their latency overlaps the set-up
+        // below (which does not touch the input slots)
+        for (int k = 0; k < NI && k < nblk; ++k) issue_in(k);
     }
     // the strip's horizontal band: member g's weight at input j of the run
     // from the group's first window (groups past the image: zeros)
@@ -384,8 +375,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_co
         // Per block k: the input copy, then block k - 1's bands (from the
         // weights staged last time), then block k's weights into the staging
         // area, so the copies of block k fly while the bands are built.
-        const uint32_t blk_bytes = uint32_t(kRB) * P * sizeof(T) * (p.offB ? 2u : 1u);
-        int ki = 0, kw = 0; // blocks whose input copies / weight copies were issued
+        int ki = min(NI, nblk), kw = 0; // blocks whose input copies / weight copies were issued
         bool ok = true;
         // builds block j's vertical bands from the staged window weights (all lanes)
         auto build = [&](int j) {
@@ -408,20 +398,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_co
                 float w[TAPS];
 #pragma unroll
                 for (int t = 0; t < TAPS; ++t) w[t] = src[t];
-                if constexpr (VP) {
-                    // rows in pairs, every weight twice: [j][r / 2][r % 2][2]
-                    float2 *dst = reinterpret_cast<float2 *>(vb) + gi * GB + r;
+                float *dst = vb + gi * GB + r;
 #pragma unroll
-                    for (int t = 0; t < TAPS; ++t) dst[(o + t) * kG] = make_float2(w[t], w[t]);
+                for (int t = 0; t < TAPS; ++t) dst[(o + t) * kG] = w[t];
 #pragma unroll
-                    for (int z = 0; z < 3; ++z) dst[(z < o ? z : z + TAPS) * kG] = make_float2(0.f, 0.f);
-                } else {
-                    float *dst = vb + gi * GB + r;
-#pragma unroll
-                    for (int t = 0; t < TAPS; ++t) dst[(o + t) * kG] = w[t];
-#pragma unroll
-                    for (int z = 0; z < 3; ++z) dst[(z < o ? z : z + TAPS) * kG] = 0.f;
-                }
+                for (int z = 0; z < 3; ++z) dst[(z < o ? z : z + TAPS) * kG] = 0.f;
             }
             for (int gi = lane; gi < n; gi += 32) vr[gi] = vis[gi] & 0xffffff;
             // the staging area was read: the next copy into it (async proxy) comes after
@@ -432,21 +413,14 @@ __global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_co
         };
         for (int k = 0; k < nblk && ok; ++k) {
             const int s = k % NI;
-            if (k >= NI && !warp_wait(&empty_in[s], uint32_t((k / NI - 1) & 1), abort_flag, p.err)) {
-                ok = false;
-                break;
-            }
-            if (lane == 0) {
-                fused::mbar_arrive_expect_tx(&full_in[s], blk_bytes);
-                fused::tma_load_2d(slot_in(s), &tmap, &full_in[s], xs, r_lo + k * kRB);
-                if (p.offB)
-                    fused::tma_load_2d(slot_in(s) + kRB * P, &tmap, &full_in[s], xs + p.offB, r_lo + k * kRB);
-                if (p.pf && k + NI < nblk) {
-                    fused::tma_prefetch_2d(&tmap, xs, r_lo + (k + NI) * kRB);
-                    if (p.offB) fused::tma_prefetch_2d(&tmap, xs + p.offB, r_lo + (k + NI) * kRB);
+            if (k >= NI) { // (the first NI blocks were issued before the set-up)
+                if (!warp_wait(&empty_in[s], uint32_t((k / NI - 1) & 1), abort_flag, p.err)) {
+                    ok = false;
+                    break;
                 }
+                if (lane == 0) issue_in(k);
+                ki = k + 1;
             }
-            ki = k + 1;
             if (k >= 1 && !build(k - 1)) {
                 ok = false;
                 break;
@@ -563,7 +537,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_co
                     const int rows = rem_rows < kG ? int(rem_rows) : kG;
                     const int nsamp = rem_samp < 4 ? int(rem_samp) : 4;
                     if (nsamp > 0)
-                        v_band<T, TAPS, VP>(hring + ch * Q + hs0, vbs + gi * (VB / 4),
+                        v_band<T, TAPS>(hring + ch * Q + hs0, vbs + gi * (GB / 4),
                                             static_cast<T *>(p.out) + y0 * p.out_stride + sx, p.out_stride, rows,
                                             nsamp, vec_ok);
                 }
@@ -575,26 +549,26 @@ __global__ void __launch_bounds__(kMaxThreads, 2) xstream_kernel(const __grid_co
     }
 }
 
-// Instantiated kernels: storage type x channels x taps per output x packed
-// vertical pass.
-template <typename T, int C, int TAPS> const void *kernel_vp(int vp)
+// Instantiated kernels: storage type x channels x taps per output x the
+// launch-bounds variant (big: more than kSmallWarps warps).
+template <typename T, int C, int TAPS> const void *kernel_big(int big)
 {
-    return vp ? reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 1>)
-              : reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 0>);
+    return big ? reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 1>)
+               : reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 0>);
 }
-template <typename T> const void *kernel_table(int C, int taps, int vp)
+template <typename T> const void *kernel_table(int C, int taps, int big)
 {
-    if (C == 1 && taps == 4) return kernel_vp<T, 1, 4>(vp);
-    if (C == 1 && taps == 6) return kernel_vp<T, 1, 6>(vp);
-    if (C == 3 && taps == 4) return kernel_vp<T, 3, 4>(vp);
-    if (C == 3 && taps == 6) return kernel_vp<T, 3, 6>(vp);
+    if (C == 1 && taps == 4) return kernel_big<T, 1, 4>(big);
+    if (C == 1 && taps == 6) return kernel_big<T, 1, 6>(big);
+    if (C == 3 && taps == 4) return kernel_big<T, 3, 4>(big);
+    if (C == 3 && taps == 6) return kernel_big<T, 3, 6>(big);
     return nullptr;
 }
 
 // defined in rs_xstream_f32.cu, rs_xstream_f16.cu, rs_xstream_bf16.cu
-const void *kernel_f32(int C, int taps, int vp);
-const void *kernel_f16(int C, int taps, int vp);
-const void *kernel_bf16(int C, int taps, int vp);
+const void *kernel_f32(int C, int taps, int big);
+const void *kernel_f16(int C, int taps, int big);
+const void *kernel_bf16(int C, int taps, int big);
 
 } // namespace xstream
 } // namespace rs

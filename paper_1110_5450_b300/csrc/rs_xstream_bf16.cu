@@ -5,7 +5,7 @@
 namespace rs {
 namespace xstream {
 
-const void *kernel_bf16(int C, int taps, int vp) { return kernel_table<__nv_bfloat16>(C, taps, vp); }
+const void *kernel_bf16(int C, int taps, int big) { return kernel_table<__nv_bfloat16>(C, taps, big); }
 
 } // namespace xstream
 } // namespace rs

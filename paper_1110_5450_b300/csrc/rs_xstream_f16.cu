@@ -5,7 +5,7 @@
 namespace rs {
 namespace xstream {
 
-const void *kernel_f16(int C, int taps, int vp) { return kernel_table<__half>(C, taps, vp); }
+const void *kernel_f16(int C, int taps, int big) { return kernel_table<__half>(C, taps, big); }
 
 } // namespace xstream
 } // namespace rs

@@ -5,7 +5,7 @@
 namespace rs {
 namespace xstream {
 
-const void *kernel_f32(int C, int taps, int vp) { return kernel_table<float>(C, taps, vp); }
+const void *kernel_f32(int C, int taps, int big) { return kernel_table<float>(C, taps, big); }
 
 } // namespace xstream
 } // namespace rs

@@ -6,8 +6,8 @@ bench.py tunes them) on sampled rows.
 Forms: the band kernel with alternating phases (2 or 3 staged blocks), the
 band kernel with warps specialised on the passes (3, 4 or 5 horizontal warps x
 2 or 3 staged blocks), and the pipelined kernel (1 to 4 horizontal warps, 2
-or 3 staged blocks, with and without the L2 prefetch and the packed vertical
-pass), each at the cost
+or 3 staged blocks, 3 to 8 vertical warps -- CTAs of more than 12 warps take
+a whole SM --, with and without the L2 prefetch), each at the cost
 model's strip width and at explicit narrow and wide widths.  Tolerances FP32
 2e-6, FP16 2e-3, BF16 1e-2 (max-abs on [0, 1] data, the oracle fed the same
 quantised input).
@@ -33,12 +33,13 @@ def rs():
     return rs
 
 
-# (kind, horizontal warps, staged blocks, prefetch, packed)
+# (kind, horizontal warps, staged blocks, prefetch, vertical warps of kind 2)
 FORMS = [(0, 0, 2, 0, 0), (0, 0, 3, 0, 0),
          (1, 3, 2, 0, 0), (1, 3, 3, 0, 0), (1, 4, 2, 0, 0), (1, 4, 3, 0, 0), (1, 5, 2, 0, 0), (1, 5, 3, 0, 0),
-         (2, 1, 2, 0, 0), (2, 2, 2, 0, 0), (2, 3, 2, 0, 0), (2, 3, 3, 0, 0), (2, 4, 2, 0, 0), (2, 3, 2, 1, 0),
-         (2, 2, 2, 0, 1), (2, 3, 3, 1, 1)]
-FORM_IDS = ["k%d-h%d-s%d%s%s" % (k, h, s, "-pf" if pf else "", "-pk" if pk else "") for k, h, s, pf, pk in FORMS]
+         (2, 1, 2, 0, 0), (2, 2, 2, 0, 0), (2, 3, 2, 0, 0), (2, 3, 3, 0, 0), (2, 4, 2, 0, 4), (2, 3, 2, 1, 0),
+         (2, 4, 2, 0, 3), (2, 7, 2, 0, 8), (2, 5, 3, 1, 6)]
+FORM_IDS = ["k%d-h%d-s%d%s%s" % (k, h, s, "-pf" if pf else "", "-v%d" % vw if vw else "")
+            for k, h, s, pf, vw in FORMS]
 
 # (every input row a whole number of 16-byte words: the streaming kernels stage rows by TMA)
 SHAPES = [((96, 132), (131, 181)),    # ~x1.37
@@ -54,21 +55,23 @@ def _resample_with_form(rs, t, OH, OW, kernel, boundary, param, form, width):
     cannot take the form at this strip width."""
     import torch
 
-    kind, hw, ns, pf, pk = form
+    kind, hw, ns, pf, vw = form
     H, W, C = t.shape
     x = t.to("cuda").contiguous()
     p = rs.Plan(H, W, C, OH, OW, kernel=kernel, param=param, boundary=boundary, dtype=x.dtype)
     try:
         try:
             rs.rs_plan_set_stream_form(p.handle, kind, hw, ns, width, pf,
-                                       torch.cuda.current_stream().cuda_stream, pk)
+                                       torch.cuda.current_stream().cuda_stream, vw)
         except rs.RSError as e:
             assert e.status == rs.RS_ERR_UNSUPPORTED, e
             return None
         p.info = rs.rs_plan_get_info(p.handle)
         assert p.info.path == 3
         got_form = rs.rs_plan_get_stream_form(p.handle)
-        assert (got_form.kind, got_form.prefetch, got_form.packed) == (kind, pf, pk)
+        assert (got_form.kind, got_form.prefetch) == (kind, pf)
+        if kind == 2 and vw:
+            assert got_form.v_warps == vw
         if width:
             assert got_form.strip_width == width
         y = p(x)
@@ -118,8 +121,9 @@ def test_exact_form_kernels_and_boundaries(rs, form, boundary, kernel, param):
 
 
 @pytest.mark.parametrize("dt", ["f16", "bf16"])
-@pytest.mark.parametrize("form", [(0, 0, 2, 0, 0), (1, 4, 3, 0, 0), (2, 3, 2, 0, 0), (2, 2, 3, 1, 1)],
-                         ids=["k0", "k1", "k2", "k2-pf-pk"])
+@pytest.mark.parametrize("form", [(0, 0, 2, 0, 0), (1, 4, 3, 0, 0), (2, 3, 2, 0, 0), (2, 2, 3, 1, 5),
+                                  (2, 7, 2, 0, 8)],
+                         ids=["k0", "k1", "k2", "k2-pf", "k2-big"])
 @pytest.mark.parametrize("C", [1, 3])
 def test_forms_16bit(rs, dt, form, C):
     img = synth.uniform(96, 136, C, seed=9 + C)
