@@ -289,21 +289,30 @@ RS_API rs_status rs_plan_get_tables(const rs_plan *plan, int axis, int32_t *h_jl
  * synchronises the whole device).  The paper has no counterpart of this entry
  * point; it is a deployment convenience.
  *
- * Same descriptor and buffers as rs_plan_create + rs_resample, but no plan:
- * each call computes the weight tables and runs the separate H-then-V pass
- * kernels with the tables and the intermediate placed in one library-owned
- * static device array of RS_STATIC_SCRATCH_BYTES (32 MiB), which every GPU
- * that loads the library holds until the process exits.  No cudaMalloc,
- * cudaFree or other allocating call is made.  A request whose tables plus
- * intermediate (in_h * out_w * channels * 4 bytes, 8 for RS_F64) exceed the
- * array returns RS_ERR_BUDGET with the sizes in rs_last_error().
+ * Same descriptor (checked exactly as rs_plan_create checks it) and buffers as
+ * rs_plan_create + rs_resample, but no plan: each call computes the weight
+ * tables and runs the separate H-then-V pass kernels with the tables and the
+ * intermediate placed in one library-owned static device array of
+ * RS_STATIC_SCRATCH_BYTES (32 MiB).  No cudaMalloc, cudaFree or other
+ * allocating call is made on the caller's behalf.  The only flag it takes is
+ * RS_NO_ANTIALIAS (any other: RS_ERR_UNSUPPORTED).  A request whose tables
+ * plus intermediate (in_h * out_w * channels * 4 bytes, 8 for RS_F64) exceed
+ * the array returns RS_ERR_BUDGET with the sizes in rs_last_error().
  *
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array and it keeps the previous call's
- * contents; calls whose GPU work overlaps (different streams or host threads)
- * race on it, so issue them on one stream.  Asynchronous on `stream`; device
- * errors of the table kernel are not reported by this entry point. */
+ * The array comes into existence when the CUDA runtime loads the library's
+ * device code that holds it: with lazy module loading (the CUDA default) at
+ * the first call of this entry point on a device, with eager loading
+ * (CUDA_MODULE_LOADING=EAGER) when the device's context is created; the
+ * device keeps it until the process exits.  Make the first call on each
+ * device at start-up, before the application's allocator takes the device
+ * memory (if the device has no room left then, it returns RS_ERR_OOM) and
+ * outside any stream capture.  Every call looks the array's device address up
+ * again (cudaGetSymbolAddress: no allocation once it exists), so a call after
+ * a device reset uses the re-created array.  All calls share the array and it
+ * keeps the previous call's contents; calls whose GPU work overlaps (different
+ * streams or host threads) race on it, so issue them on one stream.
+ * Asynchronous on `stream`; device errors of the table kernel are not reported
+ * by this entry point. */
 #define RS_STATIC_SCRATCH_BYTES (32u << 20)
 RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in, void *d_out, void *stream);
 

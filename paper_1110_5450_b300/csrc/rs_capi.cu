@@ -168,6 +168,45 @@ int64_t derive_out(int32_t given, int64_t n, double scale)
     return std::max<int64_t>(1, int64_t(v));
 }
 
+// Checks a descriptor the way every entry point that takes one does, derives
+// the output size from the scale where it is 0 and the packed row strides
+// where they are 0; on failure sets the error message.
+rs_status validate_desc(const rs_plan_desc &in, rs_plan_desc *out)
+{
+    rs_plan_desc d = in;
+    if (d.in_h < 1 || d.in_w < 1 || d.in_h > kMaxSide || d.in_w > kMaxSide)
+        return fail(RS_ERR_INVALID_ARG, "input size out of range");
+    if (d.channels < 1 || d.channels > 64) return fail(RS_ERR_INVALID_ARG, "channels must be 1..64");
+    if (d.out_h < 0 || d.out_w < 0) return fail(RS_ERR_INVALID_ARG, "negative output size");
+    if (d.kernel < RS_K_LINEAR || d.kernel > RS_K_GAUSSIAN) return fail(RS_ERR_INVALID_ARG, "unknown kernel");
+    if (d.boundary < RS_B_CLAMP || d.boundary > RS_B_TRUNCATE) return fail(RS_ERR_INVALID_ARG, "unknown boundary");
+    if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.out_dtype < RS_F64 || d.out_dtype > RS_BF16)
+        return fail(RS_ERR_INVALID_ARG, "unknown dtype");
+    if (d.in_dtype != d.out_dtype) return fail(RS_ERR_UNSUPPORTED, "in_dtype and out_dtype must be equal");
+    if (d.flags & ~uint32_t(0x1ff)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
+    if ((d.flags & RS_PREFILTER) &&
+        (d.kernel != RS_K_BSPLINE3 || d.boundary == RS_B_TRUNCATE || (d.in_dtype != RS_F32 && d.in_dtype != RS_F64)))
+        return fail(RS_ERR_UNSUPPORTED, "RS_PREFILTER needs RS_K_BSPLINE3, FP32 or FP64 storage and the clamp, "
+                                        "mirror or reflect101 boundary");
+    if (support_radius(d.kernel, d.param) == 0)
+        return fail(RS_ERR_INVALID_ARG, "kernel parameter out of range (Lanczos: an integer R in 1..16; "
+                                        "Mitchell-Netravali: B in [0, 1]; Gaussian: sigma in (0, 4])");
+    if (d.kernel == RS_K_CUBIC && !std::isfinite(d.param)) return fail(RS_ERR_INVALID_ARG, "cubic a not finite");
+    const int64_t oh = derive_out(d.out_h, d.in_h, d.scale_h);
+    const int64_t ow = derive_out(d.out_w, d.in_w, d.scale_w);
+    if (oh < 1 || ow < 1 || oh > kMaxSide || ow > kMaxSide)
+        return fail(RS_ERR_INVALID_ARG, "output size out of range (scale must be finite and > 0)");
+    d.out_h = int32_t(oh);
+    d.out_w = int32_t(ow);
+    if (d.in_row_stride == 0) d.in_row_stride = int64_t(d.in_w) * d.channels;
+    if (d.out_row_stride == 0) d.out_row_stride = int64_t(d.out_w) * d.channels;
+    if (d.in_row_stride < int64_t(d.in_w) * d.channels || d.out_row_stride < int64_t(d.out_w) * d.channels)
+        return fail(RS_ERR_INVALID_ARG, "row stride smaller than a row");
+
+    *out = d;
+    return RS_OK;
+}
+
 // Weight-table launch for both axes; when the axes are identical the column
 // tables alias the row tables and only the rows are computed.
 cudaError_t launch_plan_weights(rs_plan *p, cudaStream_t s);
@@ -819,33 +858,8 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
     const int64_t ef = env_plan_flags();
     if (ef < 0) return fail(RS_ERR_INVALID_ARG, "RS_PLAN_FLAGS names an unknown flag");
     d.flags |= uint32_t(ef);
-    if (d.in_h < 1 || d.in_w < 1 || d.in_h > kMaxSide || d.in_w > kMaxSide)
-        return fail(RS_ERR_INVALID_ARG, "input size out of range");
-    if (d.channels < 1 || d.channels > 64) return fail(RS_ERR_INVALID_ARG, "channels must be 1..64");
-    if (d.out_h < 0 || d.out_w < 0) return fail(RS_ERR_INVALID_ARG, "negative output size");
-    if (d.kernel < RS_K_LINEAR || d.kernel > RS_K_GAUSSIAN) return fail(RS_ERR_INVALID_ARG, "unknown kernel");
-    if (d.boundary < RS_B_CLAMP || d.boundary > RS_B_TRUNCATE) return fail(RS_ERR_INVALID_ARG, "unknown boundary");
-    if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.out_dtype < RS_F64 || d.out_dtype > RS_BF16)
-        return fail(RS_ERR_INVALID_ARG, "unknown dtype");
-    if (d.in_dtype != d.out_dtype) return fail(RS_ERR_UNSUPPORTED, "in_dtype and out_dtype must be equal");
-    if (d.flags & ~uint32_t(0x1ff)) return fail(RS_ERR_INVALID_ARG, "unknown flag bits");
-    if ((d.flags & RS_PREFILTER) &&
-        (d.kernel != RS_K_BSPLINE3 || d.boundary == RS_B_TRUNCATE || (d.in_dtype != RS_F32 && d.in_dtype != RS_F64)))
-        return fail(RS_ERR_UNSUPPORTED, "RS_PREFILTER needs RS_K_BSPLINE3, FP32 or FP64 storage and the clamp, "
-                                        "mirror or reflect101 boundary");
-    if (support_radius(d.kernel, d.param) == 0)
-        return fail(RS_ERR_INVALID_ARG, "Lanczos needs an integer R in 1..16");
-    if (d.kernel == RS_K_CUBIC && !std::isfinite(d.param)) return fail(RS_ERR_INVALID_ARG, "cubic a not finite");
-    const int64_t oh = derive_out(d.out_h, d.in_h, d.scale_h);
-    const int64_t ow = derive_out(d.out_w, d.in_w, d.scale_w);
-    if (oh < 1 || ow < 1 || oh > kMaxSide || ow > kMaxSide)
-        return fail(RS_ERR_INVALID_ARG, "output size out of range (scale must be finite and > 0)");
-    d.out_h = int32_t(oh);
-    d.out_w = int32_t(ow);
-    if (d.in_row_stride == 0) d.in_row_stride = int64_t(d.in_w) * d.channels;
-    if (d.out_row_stride == 0) d.out_row_stride = int64_t(d.out_w) * d.channels;
-    if (d.in_row_stride < int64_t(d.in_w) * d.channels || d.out_row_stride < int64_t(d.out_w) * d.channels)
-        return fail(RS_ERR_INVALID_ARG, "row stride smaller than a row");
+    const rs_status vs = validate_desc(d, &d);
+    if (vs != RS_OK) return vs;
 
     rs_plan *p = new (std::nothrow) rs_plan();
     if (!p) return fail(RS_ERR_OOM, "host allocation failed");

@@ -114,4 +114,13 @@ cudaError_t launch_two_pass(const TwoPassArgs &a, cudaStream_t s);
 // Thread-local last-error string.
 void set_error(const std::string &msg);
 
+// Checks a descriptor as rs_plan_create does (sizes, channels, kernel and
+// parameter, boundary, dtypes, flag bits, strides), derives the output size
+// where out_h / out_w are 0 and the packed strides where they are 0; on
+// failure sets the error message and returns its status.
+rs_status validate_desc(const rs_plan_desc &in, rs_plan_desc *out);
+// The geometry of one axis of a validated descriptor (false with a reason when
+// it needs more than kMaxTaps taps per output).
+bool axis_setup(AxisGeom &g, int64_t n_in, int64_t n_out, const rs_plan_desc &d, std::string &why);
+
 } // namespace rs

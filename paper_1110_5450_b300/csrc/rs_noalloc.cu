@@ -9,12 +9,18 @@
 //
 // How: the weight tables and the intermediate of the separate H-then-V pass
 // kernels live in one file-scope static device array of
-// RS_STATIC_SCRATCH_BYTES.  Every GPU that loads this library holds that
-// array until the process exits.  Host code cannot use the array's name as an
-// address (on the host it is only a stand-in symbol), so the first call on
-// each device looks the device address up with cudaGetSymbolAddress while
-// that device is current and caches it; that first call should therefore
-// happen before any stream capture.
+// RS_STATIC_SCRATCH_BYTES.  The array is created when the CUDA runtime loads
+// this file's device code on a device: with lazy module loading (the CUDA
+// default) that is the first call of this entry point on the device, with
+// eager loading (CUDA_MODULE_LOADING=EAGER) the creation of the device's
+// context.  From then on the device holds it until the process exits.  Host
+// code cannot use the array's name as an address (on the host it is only a
+// stand-in symbol), so every call looks the device address up with
+// cudaGetSymbolAddress while the device is current (no allocation once the
+// array exists; the address stays right if the context was reset and the
+// array re-created).  The first call on a device therefore belongs at
+// start-up -- before the host application's allocator takes the device
+// memory, and outside any stream capture.
 //
 // All calls share the one array and it keeps whatever the last call left in
 // it: the error word is cleared on every call, and the weight-table kernel
@@ -23,7 +29,6 @@
 // them on one stream, one after another.
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "rs_internal.h"
 
@@ -32,64 +37,20 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[RS_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the static array on the current device (set-up on first use).
+// Device address of the static array on the current device.  The lookup
+// loads this file's device code on first use (which creates the array:
+// cudaErrorMemoryAllocation then means the device had no room left for it).
 rs_status static_scratch(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error(std::string("rs_resample_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
-        return RS_ERR_CUDA;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        set_error(std::string("rs_resample_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("rs_resample_noalloc: device ordinal beyond 63");
-        return RS_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            set_error(std::string("rs_resample_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            return RS_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return RS_OK;
-}
-
-int radius(int kernel, double param)
-{
-    switch (kernel) {
-    case RS_K_LINEAR: return 1;
-    case RS_K_CUBIC: return 2;
-    case RS_K_BSPLINE3: return 2;
-    case RS_K_LANCZOS:
-        if (!(param >= 1.0 && param <= 16.0) || param != std::floor(param)) return 0;
-        return int(param);
-    case RS_K_MITCHELL:
-        if (!(param >= 0.0 && param <= 1.0)) return 0;
-        return 2;
-    case RS_K_GAUSSIAN:
-        if (!(param > 0.0 && param <= 4.0)) return 0;
-        return int(std::ceil(3.0 * param));
-    }
-    return 0;
-}
-
-int64_t out_len(int32_t given, int64_t n, double scale)
-{
-    if (given > 0) return given;
-    if (!(scale > 0.0) || !std::isfinite(scale)) return -1;
-    const double v = std::floor(double(n) * scale + 0.5);
-    if (!(v < double(kMaxSide) + 1.0)) return -1;
-    return v < 1.0 ? 1 : int64_t(v);
 }
 
 rs_status bad(rs_status s, const char *msg)
@@ -108,24 +69,15 @@ using namespace rs;
 extern "C" rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in, void *d_out, void *stream_v)
 {
     if (!desc || !d_in || !d_out) return bad(RS_ERR_INVALID_ARG, "NULL descriptor or buffer");
-    rs_plan_desc d = *desc;
-    if (d.in_h < 1 || d.in_w < 1 || d.in_h > kMaxSide || d.in_w > kMaxSide)
-        return bad(RS_ERR_INVALID_ARG, "input size out of range");
-    if (d.channels < 1 || d.channels > 64) return bad(RS_ERR_INVALID_ARG, "channels must be 1..64");
-    if (d.out_h < 0 || d.out_w < 0) return bad(RS_ERR_INVALID_ARG, "negative output size");
-    if (d.kernel < RS_K_LINEAR || d.kernel > RS_K_GAUSSIAN) return bad(RS_ERR_INVALID_ARG, "unknown kernel");
-    if (d.boundary < RS_B_CLAMP || d.boundary > RS_B_TRUNCATE) return bad(RS_ERR_INVALID_ARG, "unknown boundary");
-    if (d.in_dtype < RS_F64 || d.in_dtype > RS_BF16 || d.in_dtype != d.out_dtype)
-        return bad(RS_ERR_INVALID_ARG, "dtype unknown or in_dtype != out_dtype");
-    if (d.flags & ~uint32_t(0xff)) return bad(RS_ERR_INVALID_ARG, "unknown flag bits");
-    const int R = radius(d.kernel, d.param);
-    if (R == 0) return bad(RS_ERR_INVALID_ARG, "Lanczos needs an integer R in 1..16");
-    const int64_t oh = out_len(d.out_h, d.in_h, d.scale_h), ow = out_len(d.out_w, d.in_w, d.scale_w);
-    if (oh < 1 || ow < 1 || oh > kMaxSide || ow > kMaxSide) return bad(RS_ERR_INVALID_ARG, "output size out of range");
-    const int64_t in_stride = d.in_row_stride ? d.in_row_stride : int64_t(d.in_w) * d.channels;
-    const int64_t out_stride = d.out_row_stride ? d.out_row_stride : ow * d.channels;
-    if (in_stride < int64_t(d.in_w) * d.channels || out_stride < ow * d.channels)
-        return bad(RS_ERR_INVALID_ARG, "row stride smaller than a row");
+    // the same checks, output size and strides as rs_plan_create
+    rs_plan_desc d;
+    const rs_status vs = validate_desc(*desc, &d);
+    if (vs != RS_OK) return bad(vs, rs_last_error());
+    // this path always runs the two-pass kernels: no kernel choice to make
+    if (d.flags & ~uint32_t(RS_NO_ANTIALIAS))
+        return bad(RS_ERR_UNSUPPORTED, "only RS_NO_ANTIALIAS applies (this path always runs the two-pass kernels)");
+    const int64_t oh = d.out_h, ow = d.out_w;
+    const int64_t in_stride = d.in_row_stride, out_stride = d.out_row_stride;
 
     const bool dbl = d.in_dtype == RS_F64;
     const size_t wsz = dbl ? 8 : 4;
@@ -134,17 +86,8 @@ extern "C" rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d
     size_t need = up256(16);
     for (int ax = 0; ax < 2; ++ax) {
         AxisGeom &g = a[ax].g;
-        g.n_in = n_in[ax];
-        g.n_out = n_out[ax];
-        g.R = R;
-        g.D = (!(d.flags & RS_NO_ANTIALIAS) && g.n_in > g.n_out) ? 2 * g.n_in : 2 * g.n_out;
-        const int64_t traw = (g.R * g.D + g.n_out - 1) / g.n_out;
-        if (traw > kMaxTaps) return bad(RS_ERR_UNSUPPORTED, "more than 256 taps per output on one axis");
-        g.t_raw = int32_t(traw);
-        g.t_eff = int32_t(traw < g.n_in ? traw : g.n_in);
-        g.kernel = d.kernel;
-        g.boundary = d.boundary;
-        g.param = d.param;
+        std::string why;
+        if (!axis_setup(g, n_in[ax], n_out[ax], d, why)) return bad(RS_ERR_UNSUPPORTED, why.c_str());
         need += 3 * up256(size_t(g.n_out) * 4) + up256(size_t(g.n_out) * g.t_eff * 8) +
                 up256(size_t(g.n_out) * g.t_eff * wsz);
     }
