@@ -119,7 +119,7 @@ typedef enum {
  * (wide antialiasing); with RS_FORCE_TC a plan that cannot take it fails with
  * RS_ERR_UNSUPPORTED.  Batches and the server always run the SIMT kernel. */
 #define RS_TWO_PASS 0x08u     /* separate H-then-V kernels through an HBM buffer  */
-#define RS_CHECK 0x10u        /* device bounds checks that set an error word      */
+#define RS_CHECK 0x10u        /* device table checks before every resample (below) */
 #define RS_NO_STREAM 0x20u    /* never pick the row-streaming kernel              */
 #define RS_FORCE_STREAM 0x40u /* pick the row-streaming kernel (FP32/FP16/BF16, 1 or 3
                                  channels; bands of 4 outputs of at most 40 / 32
@@ -442,9 +442,40 @@ RS_API rs_status rs_server_destroy(rs_server *server);
 RS_API rs_status rs_tc_selftest(int32_t m, int32_t n, int32_t k, int32_t a_mn, int32_t b_mn, int32_t variant,
                                 int32_t bf16, const uint16_t *h_a, const uint16_t *h_b, float *h_d);
 
+/* RS_CHECK.  A plan created with RS_CHECK runs a table check on the device
+ * before every resample (on the same stream): per output of both axes, the
+ * stored window lies in the input (0 <= h_start <= n_in - table entries) and
+ * its working-precision weights are finite and sum to one within 1e-5 (FP32,
+ * FP16, BF16 storage) or 1e-12 (FP64).  These are what every pass kernel
+ * relies on when it reads a window; a failure sets the plan's error word
+ * (rs_plan_check then returns RS_ERR_DEVICE) and the resample still runs. */
+
 /* Synchronise the device and report any device-side error word the plan's
- * kernels set (RS_CHECK builds and bounded waits); clears the word. */
+ * kernels set; clears the word.  RS_ERR_TIMEOUT: a bounded device wait ran
+ * out (every wait of every kernel gives up after 2 s); RS_ERR_DEVICE: any
+ * other device-side check (the weight-table kernel's tap and sum checks, a
+ * band that does not fit its staged tile, RS_CHECK). */
 RS_API rs_status rs_plan_check(rs_plan *plan);
+
+/* Replace one axis' working-precision weights (axis 0 = rows, 1 = columns)
+ * with the caller's: h_wwork holds n_out x (table entries) values, row-major,
+ * laid out as rs_plan_get_tables returns h_wwork; they are rounded to the
+ * working precision.  The windows (h_start) stay the plan's, so every read
+ * stays inside the input whatever the weights are; they are used as given
+ * (RS_CHECK checks them before each resample).  The band tables of the
+ * kernels that have them are rebuilt on `stream`; rs_plan_recompute restores
+ * the computed weights.  RS_ERR_UNSUPPORTED when both axes share one table
+ * (identical geometry).  Synchronises `stream` for FP32 / FP16 / BF16 plans. */
+RS_API rs_status rs_plan_set_weights(rs_plan *plan, int32_t axis, const double *h_wwork, void *stream);
+
+/* Bounded-wait self-test: enqueues on `stream` a one-warp kernel that runs the
+ * same bounded mbarrier wait as every kernel of the library on a barrier
+ * nobody arrives on, with a limit of limit_us microseconds (1 .. 2,000,000).
+ * The wait gives up, sets the plan's error word to the timeout code and the
+ * kernel returns, so the next rs_plan_check reports RS_ERR_TIMEOUT and the
+ * context stays usable.  The paper has no counterpart: this checks the
+ * library's failure path without stopping a GPU. */
+RS_API rs_status rs_plan_wait_selftest(rs_plan *plan, int32_t limit_us, void *stream);
 
 /* ------------------------------------------------------------------------
  * Affine warps with elliptical weighted average filtering (non-separable):

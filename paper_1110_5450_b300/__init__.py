@@ -148,6 +148,10 @@ _lib.rs_plan_set_stream_form.restype = ctypes.c_int
 _lib.rs_plan_set_stream_form.argtypes = [_vp, ctypes.POINTER(rs_stream_form), _vp]
 _lib.rs_plan_get_stream_form.restype = ctypes.c_int
 _lib.rs_plan_get_stream_form.argtypes = [_vp, ctypes.POINTER(rs_stream_form)]
+_lib.rs_plan_set_weights.restype = ctypes.c_int
+_lib.rs_plan_set_weights.argtypes = [_vp, ctypes.c_int32, _dp, _vp]
+_lib.rs_plan_wait_selftest.restype = ctypes.c_int
+_lib.rs_plan_wait_selftest.argtypes = [_vp, ctypes.c_int32, _vp]
 _lib.rs_resample_noalloc.restype = ctypes.c_int
 _lib.rs_resample_noalloc.argtypes = [ctypes.POINTER(rs_plan_desc), _vp, _vp, _vp]
 RS_STATIC_SCRATCH_BYTES = 32 << 20
@@ -194,7 +198,8 @@ EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "
            "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
            "rs_batch_submit", "rs_batch_poll", "rs_server_release", "rs_server_drain", "rs_server_get_stats",
            "rs_server_destroy", "rs_tc_selftest", "rs_cluster_create", "rs_cluster_run", "rs_cluster_destroy",
-           "rs_warp", "rs_plan_set_stream_form", "rs_plan_get_stream_form"]
+           "rs_warp", "rs_plan_set_stream_form", "rs_plan_get_stream_form", "rs_plan_set_weights",
+           "rs_plan_wait_selftest"]
 
 
 class RSError(RuntimeError):
@@ -296,6 +301,21 @@ def rs_plan_get_tables(plan: int, axis: int):
 
 def rs_plan_check(plan: int) -> None:
     _check(_lib.rs_plan_check(_vp(plan)), "rs_plan_check")
+
+
+def rs_plan_set_weights(plan: int, axis: int, wwork, stream: int = 0) -> None:
+    """Replace one axis' working-precision window weights ((n_out, entries)
+    float64 array, as rs_plan_get_tables returns them)."""
+    import numpy as np
+
+    w = np.ascontiguousarray(wwork, dtype=np.float64)
+    _check(_lib.rs_plan_set_weights(_vp(plan), int(axis), w.ctypes.data_as(_dp), _vp(stream)),
+           "rs_plan_set_weights")
+
+
+def rs_plan_wait_selftest(plan: int, limit_us: int, stream: int = 0) -> None:
+    """A bounded device wait that must run out after limit_us (see include/rs.h)."""
+    _check(_lib.rs_plan_wait_selftest(_vp(plan), int(limit_us), _vp(stream)), "rs_plan_wait_selftest")
 
 
 def _ptr_array(ptrs):

@@ -1020,6 +1020,10 @@ rs_status rs_resample(rs_plan *p, const void *d_in, void *d_out, void *stream_v)
         if (ps != RS_OK) return ps;
         d_in = p->coef;
     }
+    if (d.flags & RS_CHECK) {
+        e = launch_table_check(p, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "table check launch");
+    }
     if (p->use_vfirst) return vfirst::launch(p, d_in, d_out, stream);
     if (p->path == 0) {
         fused::Params fp = p->fp;
@@ -1487,10 +1491,52 @@ rs_status rs_plan_check(rs_plan *p)
     if (e == cudaSuccess && herr) e = cudaMemset(p->d_err, 0, 4);
     if (e != cudaSuccess) return cuda_fail(e, "checking the device error word");
     if (herr) {
-        char buf[64];
-        std::snprintf(buf, sizeof buf, "device error word %d", herr);
-        return fail(RS_ERR_DEVICE, buf);
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "device error word %d%s", herr,
+                      herr == fused::kErrTimeout ? " (a bounded device wait ran out)"
+                      : herr == fused::kErrCheck ? " (RS_CHECK: a table window or its weights)"
+                                                 : "");
+        return fail(herr == fused::kErrTimeout ? RS_ERR_TIMEOUT : RS_ERR_DEVICE, buf);
     }
+    return RS_OK;
+}
+
+rs_status rs_plan_set_weights(rs_plan *p, int32_t axis, const double *h_wwork, void *stream_v)
+{
+    if (!p || !h_wwork || (axis != 0 && axis != 1)) return fail(RS_ERR_INVALID_ARG, "bad plan, axis or weights");
+    if (p->axes_alias) return fail(RS_ERR_UNSUPPORTED, "the plan's two axes share one table (identical geometry)");
+    const AxisGeom &g = axis == 0 ? p->gy : p->gx;
+    const AxisTables &t = axis == 0 ? p->ty : p->tx;
+    const size_t n = size_t(g.n_out) * size_t(g.t_eff);
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    cudaError_t e = cudaSuccess;
+    if (p->work_double) {
+        e = cudaMemcpyAsync(t.wwork, h_wwork, n * 8, cudaMemcpyHostToDevice, stream);
+    } else {
+        std::vector<float> w(n);
+        for (size_t i = 0; i < n; ++i) w[i] = float(h_wwork[i]);
+        e = cudaMemcpyAsync(t.wwork, w.data(), n * 4, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream); // w is released on return
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copying weights");
+    // the kernels that read bands of these weights get them rebuilt
+    if (p->vfirst_ok) {
+        const rs_status s = vfirst::rebuild(p, stream);
+        if (s != RS_OK) return s;
+    }
+    if (p->stream_ok) {
+        const rs_status s = stream::rebuild(p, stream);
+        if (s != RS_OK) return s;
+    }
+    p->tile_bands_stale = 1;
+    return RS_OK;
+}
+
+rs_status rs_plan_wait_selftest(rs_plan *p, int32_t limit_us, void *stream_v)
+{
+    if (!p || limit_us < 1 || limit_us > 2000000) return fail(RS_ERR_INVALID_ARG, "bad plan or limit (1 us .. 2 s)");
+    const cudaError_t e = launch_wait_selftest(p->d_err, uint64_t(limit_us) * 1000ull, static_cast<cudaStream_t>(stream_v));
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test launch");
     return RS_OK;
 }
 

@@ -45,6 +45,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kErrBounds = 201;  // a band would read outside the staged tile
 constexpr int kErrTimeout = 202; // an mbarrier wait ran out
+constexpr int kErrCheck = 203;   // an RS_CHECK table check failed
 constexpr int kOffCache = 2048;  // batch tile prefix sums kept in shared memory
 constexpr int kPrefetch = 2;     // tiles ahead whose input is prefetched into L2
 
@@ -317,7 +318,10 @@ __host__ __device__ inline Layout layout(size_t elem, size_t acc, int box_h, int
 }
 
 // Bounded wait that also honours the CTA abort flag; false on timeout/abort.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err)
+// limit_ns: wall time before giving up (2 s in every kernel; the wait
+// self-test passes a shorter one).
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                              uint64_t limit_ns = 2000000000ull)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
@@ -325,7 +329,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 3u) == 3u) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > 2000000000ull) {
+            if (global_ns() - t0 > limit_ns) {
                 flag(err, kErrTimeout);
                 *abort_flag = 1;
                 return false;

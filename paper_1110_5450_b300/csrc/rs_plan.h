@@ -127,6 +127,10 @@ struct rs_plan {
 namespace rs {
 
 rs_status fail(rs_status s, const std::string &msg);
+// RS_CHECK: the plan's tables checked on the device (rs_check.cu).
+cudaError_t launch_table_check(const rs_plan *p, cudaStream_t s);
+// The bounded-wait self-test kernel (rs_check.cu).
+cudaError_t launch_wait_selftest(int *err, uint64_t limit_ns, cudaStream_t s);
 // Instantiated fused kernel for (dtype, channels, group size), or nullptr.
 const fused::Variant *find_variant(int dtype, int C, int G);
 // Support radius of a kernel (0 for an invalid Lanczos parameter).
