@@ -80,6 +80,19 @@ def parse():
                     help="input side (profiling runs only; the benchmark workload is 4096)")
     ap.add_argument("--scales", type=str, default="1.37,0.3",
                     help="comma-separated scales (profiling runs only)")
+    ap.add_argument("--case", action="store_true",
+                    help="profiling: run one plan (--size, first of --scales, --case-*) --case-launches times "
+                         "and print its configuration; no timing, no JSON line")
+    ap.add_argument("--case-dtype", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--case-channels", type=int, default=3)
+    ap.add_argument("--case-kernel", default="lanczos")
+    ap.add_argument("--case-param", type=float, default=3.0)
+    ap.add_argument("--case-boundary", default="mirror")
+    ap.add_argument("--case-flags", default="", help="comma-separated RS_* plan flag names without the prefix")
+    ap.add_argument("--case-form", default="",
+                    help="streaming form kind,h_warps,v_warps,staged_blocks,strip_width,row_ranges "
+                         "(rs_plan_set_stream_form; zeros: defaults)")
+    ap.add_argument("--case-launches", type=int, default=4)
     a = ap.parse_args()
     global N_IN, SCALES
     N_IN = a.size
@@ -105,8 +118,17 @@ def max_over_ranks(ms, device):
     return float(t.item())
 
 
-def out_sizes():
-    return [max(1, int(math.floor(N_IN * s + 0.5))) for s in SCALES]
+def out_sizes(reference: bool = False):
+    """Output sides of the workload's scales: the library's rule (our arm; host
+    only) or the oracle's own (the reference arm runs the oracle alone)."""
+    if reference:
+        import oracle
+
+        return [oracle.out_size(N_IN, s) for s in SCALES]
+    import paper_1110_5450_b300 as rs
+
+    return [rs.rs_desc_out_size(rs.make_desc(N_IN, N_IN, C, 0, 0, s, s, kernel="lanczos", param=3.0,
+                                             boundary="mirror"))[0] for s in SCALES]
 
 
 def measured_peaks():
@@ -194,7 +216,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def cpu_baseline(img, budget_s: float):
+def cpu_baseline(img, budget_s: float, outs):
     """The FP64 oracle on the host cores, on a band of output rows of both
     scales sized to about ``budget_s`` seconds; returns (Mpixel/s, cores, text)."""
     import oracle
@@ -202,7 +224,6 @@ def cpu_baseline(img, budget_s: float):
     import numpy as np
 
     o = oracle.default()
-    outs = out_sizes()
     img = np.ascontiguousarray(img, dtype=np.float64)  # exact upcast, once, outside the timing
     # grow a central band of output rows per scale until it has taken its
     # share of the budget (per-call set-up makes tiny samples unrepresentative)
@@ -242,7 +263,89 @@ def cpu_baseline(img, budget_s: float):
     return value, o.default_threads(), sample
 
 
-def batched_section(args, dev, stream):
+def sample_rows(n: int, k: int = 6, seed: int = 17):
+    """Rows checked against the oracle: both edges, the middle, k random."""
+    import numpy as np
+
+    g = np.random.default_rng(seed)
+    return sorted(r for r in set([0, 1, n // 2, n - 2, n - 1]) | set(int(v) for v in g.integers(0, n, k))
+                  if 0 <= r < n)
+
+
+def accuracy_item(group, dtype, path, make_input, oh, ow, kernel, param, boundary, rows, gpu, tol):
+    """One result to check against the oracle: the device output on `rows`
+    (None: every row) and how to rebuild its exact (quantised) input."""
+    return {"group": group, "dtype": dtype, "path": path, "input": make_input, "oh": oh, "ow": ow,
+            "kernel": kernel, "param": param, "boundary": boundary, "rows": rows, "gpu": gpu, "tol": tol}
+
+
+def oracle_accuracy(items):
+    """Part of the CPU-baseline leg: the FP64 oracle on the sampled rows of
+    every collected result, fed the same quantised input; per result group the
+    largest absolute error and the RMS error."""
+    import numpy as np
+
+    import oracle
+
+    groups = {}
+    for it in items:
+        exact = it["input"]()
+        if it["rows"] is None:
+            want = oracle.resample(exact, it["oh"], it["ow"], it["kernel"], it["boundary"], param=it["param"])
+        else:
+            want = np.concatenate([oracle.resample(exact, it["oh"], it["ow"], it["kernel"], it["boundary"],
+                                                   param=it["param"], rows=(r, r + 1)) for r in it["rows"]])
+        d = np.abs(np.asarray(it["gpu"], dtype=np.float64).reshape(want.shape) - want)
+        g = groups.setdefault(it["group"], {"result": it["group"], "dtype": it["dtype"], "path": it["path"],
+                                            "max_abs": 0.0, "sq": 0.0, "n": 0, "rows": 0, "tol": it["tol"]})
+        g["max_abs"] = max(g["max_abs"], float(d.max()))
+        g["sq"] += float((d * d).sum())
+        g["n"] += d.size
+        g["rows"] += want.shape[0]
+        if it["path"] != g["path"]:
+            g["path"] = "mixed"
+    out = []
+    for g in groups.values():
+        out.append({"result": g["result"], "dtype": g["dtype"], "path": g["path"], "max_abs": g["max_abs"],
+                    "rms": math.sqrt(g["sq"] / max(1, g["n"])), "rows_checked": g["rows"], "tol": g["tol"],
+                    "within_tol": g["max_abs"] <= g["tol"]})
+    return out
+
+
+def run_case(args):
+    """--case: one plan, a few launches, for profilers (no timing)."""
+    import torch
+
+    import paper_1110_5450_b300 as rs
+    import synth
+
+    dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.case_dtype]
+    flags = 0
+    for name in filter(None, args.case_flags.split(",")):
+        flags |= getattr(rs, "RS_" + name.strip().upper())
+    img = synth.sinusoids(N_IN, N_IN, args.case_channels, seed=synth.SEED_C2)
+    x = torch.from_numpy(img).to(dt).cuda()
+    p = rs.Plan(N_IN, N_IN, args.case_channels, scale=SCALES[0], kernel=args.case_kernel, param=args.case_param,
+                boundary=args.case_boundary, dtype=dt, flags=flags)
+    y = torch.empty(p.out_shape, dtype=dt, device="cuda")
+    if args.tune_cache:
+        p.autotune(x, y, cache_path=args.tune_cache)
+    if args.case_form:
+        kind, hw, vw, ns, sw, nr = [int(v) for v in args.case_form.split(",")]
+        rs.rs_plan_set_stream_form(p.handle, kind, hw, ns, sw, 0, torch.cuda.current_stream().cuda_stream,
+                                   vw, nr)
+        p.info = rs.rs_plan_get_info(p.handle)
+    for _ in range(args.case_launches):
+        p(x, out=y)
+    torch.cuda.synchronize()
+    p.check()
+    i = p.info
+    print("path", p.path, "tile", [i.tile_h, i.tile_w], "group", i.group_h, "band", [i.span_h, i.span_w],
+          "stages", i.stages, "warps_pass1", i.warps_pass1, "smem", i.smem_bytes, "ctas_per_sm", i.ctas_per_sm)
+    p.close()
+
+
+def batched_section(args, dev, stream, acc=None):
     """Uneven batch (512 single-channel FP16 images, sides U{64..2048}, scale
     logU[1/4, 4], kernel U{tent, Keys -1/2, Lanczos-3}, mirror) in one
     persistent launch replayed as a CUDA graph, against the plain per-image
@@ -272,9 +375,8 @@ def batched_section(args, dev, stream):
         batch = rs.Batch(bspecs, channels=1, dtype=tdt, in_pitches=pitches, stream=stream)
     create_s = time.perf_counter() - t0
     outs16 = []
-    for sp, d in zip(specs, batch.descs):
-        oh = rs.out_size(sp.in_h, sp.scale)
-        ow = rs.out_size(sp.in_w, sp.scale)
+    for d in batch.descs:
+        oh, ow = rs.rs_desc_out_size(d)
         outs16.append(torch.empty((oh, ow, 1), dtype=tdt, device=dev))
     t0 = time.perf_counter()
     if not args.no_tune:
@@ -315,9 +417,19 @@ def batched_section(args, dev, stream):
     b.record(stream)
     torch.cuda.synchronize()
     ms_plain = a.elapsed_time(b) / 3
-    # FP16 batch against the per-image FP32 path (the error against the FP64
-    # oracle is measured by tests/precision_report.py)
+    # FP16 batch against the per-image FP32 path; every 64th image's sampled
+    # rows go to the oracle leg
     diff = max(float((o16.float() - o32).abs().max()) for o16, o32 in zip(outs16, outs32))
+    if acc is not None:
+        for k in range(0, len(specs), 64):
+            sp, y = specs[k], outs16[k]
+            rows = sample_rows(y.shape[0], 2, seed=k)
+            acc.append(accuracy_item(
+                "C4 batch of %d FP16 images (every 64th)" % len(specs), "f16", "batch",
+                (lambda sp=sp: torch.from_numpy(synth.sinusoids(sp.in_h, sp.in_w, 1, seed=sp.seed))
+                 .to(tdt).to(torch.float64).numpy()),
+                y.shape[0], y.shape[1], sp.kernel, sp.param, "mirror", rows,
+                y[rows].double().cpu().numpy(), 2e-3))
     for pl in plans:
         pl.close()
     batch.close()
@@ -338,15 +450,16 @@ def batched_section(args, dev, stream):
                        "tiles": info.total_tiles}}
 
 
-def tc_section(args, dev, stream):
+def tc_section(args, dev, stream, acc=None):
     """Precision form: the 4096x4096x3 sinusoid image stored in BF16 and FP16
     (FP32 accumulation), Lanczos-3 mirror, x1.37, x0.3 and x0.125.  Per dtype
     and scale: the autotuned plan ("auto": the fastest of the kernels below),
     then each kernel forced where it applies -- the tensor-core vertical pass
     (tcgen05, the default for the wide antialiased downscales), the SIMT tile
     kernel and the row-streaming kernel; kernel time, HBM fraction, and the
-    largest difference from the FP32 path on the same input (errors against
-    the FP64 oracle: tests/precision_report.py)."""
+    largest difference from the FP32 path on the same input (the autotuned
+    results' errors against the FP64 oracle: the line's
+    accuracy_vs_fp64_oracle)."""
     import torch
 
     import paper_1110_5450_b300 as rs
@@ -394,6 +507,13 @@ def tc_section(args, dev, stream):
                 us = a.elapsed_time(b) / reps * 1e3
                 alg = x.numel() * 2 + y.numel() * 2
                 info = p.info
+                if acc is not None and label == "auto":
+                    rows = sample_rows(y.shape[0])
+                    acc.append(accuracy_item(
+                        "C3 4096x4096x3 x%g %s" % (sc, name.upper()), name, rs.PATHS[info.path],
+                        (lambda tdt=tdt: torch.from_numpy(img).to(tdt).to(torch.float64).numpy()),
+                        y.shape[0], y.shape[1], "lanczos", 3.0, "mirror", rows, y[rows].double().cpu().numpy(),
+                        1e-2 if name == "bf16" else 2e-3))
                 res["runs"].append({
                     "dtype": name, "scale": sc, "variant": label, "path": rs.PATHS[info.path], "us": us,
                     "GBps": alg / (us / 1e6) / 1e9, "hbm_frac": alg / (us / 1e6) / 1e9 / peak,
@@ -406,7 +526,7 @@ def tc_section(args, dev, stream):
     return res
 
 
-def c1_section(dev, stream):
+def c1_section(dev, stream, acc=None):
     """C1: 256x256x1 FP64 U[0,1) -> 512x512, Keys a = -1/2, clamp, FP64
     accumulation.  2.6 MB move in 0.4 us at full HBM bandwidth, so there is
     no meaningful roofline: after autotuning, the device time of one call
@@ -448,6 +568,11 @@ def c1_section(dev, stream):
         rt.append((time.perf_counter() - t0) * 1e6)
     p.check()
     info = p.info
+    if acc is not None:
+        host = img.cpu().numpy()
+        acc.append(accuracy_item("C1 256x256x1 FP64 x2 Keys (whole output)", "f64", rs.PATHS[info.path],
+                                 lambda: host, 512, 512, "cubic", -0.5, "clamp", None,
+                                 y.cpu().numpy(), 1e-12))
     p.close()
     rt.sort()
     return {"workload": "C1 256x256x1 FP64 U[0,1) -> 512x512, Keys -1/2, clamp",
@@ -611,16 +736,16 @@ def run_reference(args, rank, world):
 
     img = synth.sinusoids(N_IN, N_IN, C, seed=synth.SEED_C2)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    outs = out_sizes(reference=True)
     for _ in range(args.warmup):
-        cpu_baseline(img, min(per_step, 2.0))
+        cpu_baseline(img, min(per_step, 2.0), outs)
     vals, cores, sample = [], 0, ""
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, cores, sample = cpu_baseline(img, per_step)
+        v, cores, sample = cpu_baseline(img, per_step, outs)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
-    outs = out_sizes()
     mpx_step = sum(n * n for n in outs) / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mpx_step / value * 1e3,
@@ -637,6 +762,9 @@ def main():
     rank, world, local = dist_info()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case:
+        run_case(args)
         return
 
     import torch
@@ -818,25 +946,40 @@ def main():
 
     for p in plans:
         p.check()
+    # the timed step's outputs on sampled rows, for the oracle leg
+    acc = [] if rank == 0 and not args.no_cpu_baseline else None
+    if acc is not None:
+        import numpy as np
+
+        img64 = img.astype(np.float64)
+        for sc, p, y in zip(SCALES, plans, ys):
+            rows = sample_rows(y.shape[0])
+            acc.append(accuracy_item("C2 %dx%dx%d x%g FP32 (timed step)" % (N_IN, N_IN, C, sc), "f32",
+                                     rs.PATHS[p.info.path], lambda: img64, y.shape[0], y.shape[1], "lanczos",
+                                     3.0, "mirror", rows, y[rows].double().cpu().numpy(), 2e-6))
 
     batched = None
     if not args.no_batch:
-        batched = batched_section(args, dev, stream)
+        batched = batched_section(args, dev, stream, acc)
     clustering = None
     if not args.no_cluster and rank == 0:
         clustering = cluster_section(args, dev, stream)
-    c1 = c1_section(dev, stream) if rank == 0 and not args.no_c1 else None
+    c1 = c1_section(dev, stream, acc) if rank == 0 and not args.no_c1 else None
     tc16 = None
     if not args.no_tc and rank == 0:
-        tc16 = tc_section(args, dev, stream)
+        tc16 = tc_section(args, dev, stream, acc)
     serving = None
     if not args.no_serve and rank == 0:
         serving = serving_section(args, dev)
 
+    # the CPU-baseline leg: the FP64 oracle timed on the host cores, and the
+    # error of every collected result against it
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline(img, args.cpu_sample_s)
+        v, cores, sample = cpu_baseline(img, args.cpu_sample_s, outs)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        accuracy = oracle_accuracy(acc)
 
     if rank == 0:
         line = {
@@ -862,6 +1005,7 @@ def main():
             "gpu_launches": launches_per_step * args.steps + args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "accuracy_vs_fp64_oracle": accuracy,
             "batched": batched,
             "clustering": clustering,
             "c1_latency": c1,

@@ -176,6 +176,11 @@ typedef struct {
 
 typedef struct rs_plan rs_plan;
 
+/* The output size a descriptor derives (out_h / out_w as given, or
+ * max(1, floor(n s + 1/2)) from scale_h / scale_w where they are 0), after the
+ * same checks as rs_plan_create.  Host only: no device work, no allocation. */
+RS_API rs_status rs_desc_out_size(const rs_plan_desc *desc, int32_t *out_h, int32_t *out_w);
+
 /* Create a plan: validates the descriptor, derives the output size, allocates
  * the weight tables on the current device and enqueues the FP64 weight-table
  * kernel on `stream`, then synchronises that stream once to read back the

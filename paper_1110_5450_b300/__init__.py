@@ -122,6 +122,8 @@ _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _dp = ctypes.POINTER(ctypes.c_double)
 
+_lib.rs_desc_out_size.restype = ctypes.c_int
+_lib.rs_desc_out_size.argtypes = [ctypes.POINTER(rs_plan_desc), _i32p, _i32p]
 _lib.rs_plan_create.restype = ctypes.c_int
 _lib.rs_plan_create.argtypes = [ctypes.POINTER(rs_plan_desc), _vp, ctypes.POINTER(_vp)]
 _lib.rs_resample.restype = ctypes.c_int
@@ -192,7 +194,7 @@ _lib.rs_server_destroy.restype = ctypes.c_int
 _lib.rs_server_destroy.argtypes = [_vp]
 
 # Every symbol include/rs.h declares (checked by the CPU test suite).
-EXPORTS = ["rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
+EXPORTS = ["rs_desc_out_size", "rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
            "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version",
            "rs_resample_noalloc", "rs_plan_autotune", "rs_batch_create", "rs_batch_run",
            "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
@@ -403,9 +405,11 @@ def rs_server_destroy(server: int) -> None:
     _check(_lib.rs_server_destroy(_vp(server)), "rs_server_destroy")
 
 
-def out_size(n: int, scale: float) -> int:
-    """Output length the library derives from a scale: max(1, floor(n s + 1/2))."""
-    return max(1, int(math.floor(n * scale + 0.5)))
+def rs_desc_out_size(desc: rs_plan_desc):
+    """(out_h, out_w) the library derives for a descriptor (host only)."""
+    oh, ow = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.rs_desc_out_size(ctypes.byref(desc), ctypes.byref(oh), ctypes.byref(ow)), "rs_desc_out_size")
+    return int(oh.value), int(ow.value)
 
 
 # ------------------------------------------------------------ torch helper

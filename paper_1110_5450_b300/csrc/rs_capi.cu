@@ -848,6 +848,17 @@ const char *rs_last_error(void) { return g_last_error.c_str(); }
 
 int32_t rs_version(void) { return 1; }
 
+rs_status rs_desc_out_size(const rs_plan_desc *desc, int32_t *out_h, int32_t *out_w)
+{
+    if (!desc || !out_h || !out_w) return fail(RS_ERR_INVALID_ARG, "NULL argument");
+    rs_plan_desc d;
+    const rs_status s = validate_desc(*desc, &d);
+    if (s != RS_OK) return s;
+    *out_h = d.out_h;
+    *out_w = d.out_w;
+    return RS_OK;
+}
+
 rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out)
 {
     const Range range("rs_plan_create");
