@@ -60,8 +60,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the model-chosen kernel configuration")
     ap.add_argument("--batch-n", type=int, default=512, help="images in the batched section")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the serving trace")
-    ap.add_argument("--serve-plain-n", type=int, default=300, help="requests of the plain FP32 comparison")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the serving trace")
+    ap.add_argument("--serve-plain-seconds", type=float, default=5.0,
+                    help="arrivals of the trace replayed through the plain FP32 path")
+    ap.add_argument("--serve-plain-cap", type=float, default=60.0,
+                    help="wall seconds after which the plain FP32 replay stops")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving section")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched section")
@@ -625,9 +628,17 @@ def serving_section(args, dev):
     U{Keys -1/2, Lanczos-3}, mirror), continuous batching under a 40 GB budget.
     Inputs are crops of two resident 4096x4096 base images; outputs are
     allocated by the server and released as soon as each request completes.
-    Latency = completion (host callback) - submission.  The plain FP32 path
-    (one plan + one resample per request, back to back) runs on a prefix of
-    the same trace for comparison."""
+    Latency = completion (host callback) - arrival time in the trace.
+
+    The comparator replays the first --serve-plain-seconds of the SAME trace
+    open loop through the plain FP32 path: one worker takes the requests in
+    arrival order, each one (plan creation + resample + synchronise + destroy)
+    starting at its arrival or when the previous one ends, whichever is later;
+    its latency is completion - arrival too.  The replay stops after
+    --serve-plain-cap seconds; requests not finished by then are counted with
+    the latency they had reached (a lower bound) and reported as unfinished.
+    The server's latencies over the same prefix of arrivals are reported
+    beside it."""
     import numpy as np
     import torch
 
@@ -649,13 +660,14 @@ def serving_section(args, dev):
     srv = rs.rs_server_create(40 << 30, max_inflight=4, max_batch=256)
     torch.cuda.synchronize()
     outstanding = {}
-    lat, out_px, batch_sizes = [], 0, []
-    t0 = time.perf_counter()
+    lat = np.full(len(trace), np.nan)
+    out_px, batch_sizes = 0, []
+    t0_ns = time.monotonic_ns()       # the server stamps with the same (steady) clock
     i = 0
     n = len(trace)
     lag = []
     while i < n or outstanding:
-        now = time.perf_counter() - t0
+        now = (time.monotonic_ns() - t0_ns) * 1e-9
         # submit everything whose arrival time has come
         first = i
         while i < n and trace[i].arrival_s <= now:
@@ -672,8 +684,9 @@ def serving_section(args, dev):
             st = rs.rs_batch_poll(srv, tk)
             if st.status == rs.RS_ERR_BUSY:
                 continue
+            k = outstanding[tk]
             if st.status == rs.RS_OK:
-                lat.append((st.t_done_ns - st.t_submit_ns) / 1e6)
+                lat[k] = (st.t_done_ns - t0_ns) / 1e6 - trace[k].arrival_s * 1e3
                 out_px += st.out_h * st.out_w
                 batch_sizes.append(st.batch_size)
             rs.rs_server_release(srv, tk)
@@ -682,50 +695,69 @@ def serving_section(args, dev):
             del outstanding[tk]
         if not done and i < n:
             time.sleep(0.0002)
-    wall = time.perf_counter() - t0
+    wall = (time.monotonic_ns() - t0_ns) * 1e-9
     stats = rs.rs_server_get_stats(srv)
     rs.rs_server_drain(srv)
     rs.rs_server_destroy(srv)
-    lat = np.array(lat)
-    # plain per-request FP32 path on a prefix of the trace (back to back)
-    m = min(len(trace), args.serve_plain_n)
-    t1 = time.perf_counter()
-    svc, px32 = [], 0
+    ok = ~np.isnan(lat)
+
+    # the plain FP32 path, open loop on the first seconds of the same trace
+    m = sum(1 for r in trace if r.arrival_s < args.serve_plain_seconds)
+    dd = []
     for r in trace[:m]:
         sp = r.spec
-        ts = time.perf_counter()
-        pl = rs.Plan(sp.in_h, sp.in_w, sp.channels, scale=sp.scale, kernel=sp.kernel, param=sp.param,
-                     boundary="mirror", dtype=torch.float32)
-        y = torch.empty(pl.out_shape, dtype=torch.float32, device=dev)
-        d = pl.desc
-        h = pl.handle
-        # the crop of the resident FP32 base (row pitch 4096*C) through the C ABI
-        dd = rs.make_desc(sp.in_h, sp.in_w, sp.channels, pl.info.out_h, pl.info.out_w, kernel=sp.kernel,
-                          param=sp.param, boundary="mirror", dtype=torch.float32,
-                          in_row_stride=4096 * sp.channels)
-        pl.close()
-        hh = rs.rs_plan_create(dd, 0)
-        rs.rs_resample(hh, bases32[sp.channels].data_ptr(), y.data_ptr(), 0)
+        d = rs.make_desc(sp.in_h, sp.in_w, sp.channels, scale_h=sp.scale, scale_w=sp.scale, kernel=sp.kernel,
+                         param=sp.param, boundary="mirror", dtype=torch.float32, in_row_stride=4096 * sp.channels)
+        oh, ow = rs.rs_desc_out_size(d)
+        dd.append((d, oh * ow * sp.channels))
+    y = torch.empty(max([e for _, e in dd] + [1]), dtype=torch.float32, device=dev)   # reused output
+    torch.cuda.synchronize()
+    plat, px32 = np.zeros(m), 0
+    t1_ns = time.monotonic_ns()
+    cap_ns = int(args.serve_plain_cap * 1e9)
+    served = 0
+    for k in range(m):
+        arr = t1_ns + int(trace[k].arrival_s * 1e9)
+        while time.monotonic_ns() < arr:
+            pass
+        h = rs.rs_plan_create(dd[k][0], 0)
+        rs.rs_resample(h, bases32[trace[k].spec.channels].data_ptr(), y.data_ptr(), 0)
         torch.cuda.synchronize()
-        rs.rs_destroy(hh)
-        svc.append((time.perf_counter() - ts) * 1e3)
-        px32 += y.shape[0] * y.shape[1]
-        del y, d, h
-    plain_wall = time.perf_counter() - t1
-    svc = np.array(svc)
+        rs.rs_destroy(h)
+        t = time.monotonic_ns()
+        plat[k] = (t - arr) / 1e6
+        px32 += dd[k][1] // trace[k].spec.channels
+        served = k + 1
+        if t - t1_ns > cap_ns:
+            break
+    stop_ns = time.monotonic_ns()
+    for k in range(served, m):          # still waiting when the replay stopped: a lower bound
+        plat[k] = max(0.0, (stop_ns - t1_ns) / 1e6 - trace[k].arrival_s * 1e3)
+    plain_wall = (stop_ns - t1_ns) * 1e-9
+    del y
+    pre = ok[:m]
     return {"workload": "Poisson %d req/s for %.0f s, square BF16, side logU[32,4096], C in {1,3}, "
                         "scale logU[1/8,8], kernel U{Keys -1/2, Lanczos-3}, mirror; 40 GB budget"
                         % (2000, args.serve_seconds),
-            "requests": int(len(lat)), "rejected": int(stats.rejected), "launches": int(stats.launches),
+            "requests": int(ok.sum()), "rejected": int(stats.rejected), "launches": int(stats.launches),
+            "streamed_launches": int(stats.streamed),
             "value": out_px / wall / 1e6, "unit": UNIT, "wall_s": wall,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms": float(np.percentile(lat[ok], 50)), "p99_ms": float(np.percentile(lat[ok], 99)),
+            "latency": "completion (host callback) - arrival in the trace",
             "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
             "max_bytes_in_use": int(stats.max_bytes_in_use),
             "submit_lag_p99_ms": float(np.percentile(lag, 99) * 1e3) if lag else 0.0,
-            "plain_fp32_per_request": {"requests": m, "value": px32 / plain_wall / 1e6, "unit": UNIT,
-                                       "p50_ms": float(np.percentile(svc, 50)),
-                                       "p99_ms": float(np.percentile(svc, 99)),
-                                       "how": "closed loop, one plan + resample + sync per request"}}
+            "same_prefix": {"arrivals_s": args.serve_plain_seconds, "requests": m,
+                            "server_p50_ms": float(np.percentile(lat[:m][pre], 50)) if pre.any() else None,
+                            "server_p99_ms": float(np.percentile(lat[:m][pre], 99)) if pre.any() else None,
+                            "plain_fp32_open_loop": {
+                                "served": served, "unfinished": m - served,
+                                "p50_ms": float(np.percentile(plat, 50)) if m else None,
+                                "p99_ms": float(np.percentile(plat, 99)) if m else None,
+                                "value": px32 / plain_wall / 1e6, "unit": UNIT, "wall_s": plain_wall,
+                                "how": "one worker, arrival order, rs_plan_create + rs_resample + sync + "
+                                       "rs_destroy per request, FP32, one reused output buffer; "
+                                       "latency = completion - arrival (unfinished: lower bound at the cap)"}}}
 
 
 def run_reference(args, rank, world):

@@ -380,11 +380,16 @@ RS_API rs_status rs_batch_destroy(rs_batch *batch);
  * device arena allocated once -- plans each one without any host
  * synchronisation, and launches everything admitted since the previous launch
  * as one persistent fused launch per (channels, dtype, group size, TMA)
- * class, on up to max_inflight streams at once.  Requests arriving while
+ * class, on up to max_inflight streams at once.  A request of at least 2^20
+ * output pixels (16-byte row pitches, not RS_F64, not RS_NO_STREAM) runs
+ * alone on the row-streaming kernels in their untuned form, its window
+ * starts computed on the host in closed form; when no streaming form takes
+ * it, it runs on the tile kernel like the rest.  Requests arriving while
  * others run are admitted as memory frees and run concurrently with them.
  * Completion is timestamped (host steady clock) by a host callback queued
  * behind each launch.  Every request's result is bit-identical to the same
- * resample run alone (rs_resample of the same descriptor).
+ * resample run alone: on the tile kernel (RS_FORCE_SIMT | RS_NO_STREAM), or
+ * for a large request on the plan's untuned streaming form.
  * ---------------------------------------------------------------------- */
 typedef struct rs_server rs_server;
 
@@ -410,12 +415,17 @@ typedef struct {
     int32_t out_h, out_w;
     int64_t out_row_stride; /* elements                                                 */
     void *d_out;            /* the result (device), valid once status == RS_OK          */
-    uint64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns;
+    uint64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns; /* host steady clock */
+    /* GPU clock (%globaltimer, ns) when the launch that ran the request started
+     * and finished its work on the device (one-thread stamp kernels on its
+     * stream around it): launches whose intervals intersect ran concurrently */
+    uint64_t t_gpu_start_ns, t_gpu_end_ns;
 } rs_request_state;
 
 typedef struct {
     uint64_t completed, rejected, launches, out_pixels, pending;
     uint64_t bytes_in_use, max_bytes_in_use, max_batch;
+    uint64_t streamed; /* launches of one large request on the row-streaming kernels */
 } rs_server_stats;
 
 RS_API rs_status rs_server_create(const rs_server_desc *desc, rs_server **out);

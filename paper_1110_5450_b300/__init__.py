@@ -110,12 +110,13 @@ class rs_request_state(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("launch_id", ctypes.c_int32), ("batch_size", ctypes.c_int32),
                 ("out_h", ctypes.c_int32), ("out_w", ctypes.c_int32), ("out_row_stride", ctypes.c_int64),
                 ("d_out", ctypes.c_void_p), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
-                ("t_launch_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+                ("t_launch_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64),
+                ("t_gpu_start_ns", ctypes.c_uint64), ("t_gpu_end_ns", ctypes.c_uint64)]
 
 
 class rs_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("completed", "rejected", "launches", "out_pixels", "pending",
-                                               "bytes_in_use", "max_bytes_in_use", "max_batch")]
+                                               "bytes_in_use", "max_bytes_in_use", "max_batch", "streamed")]
 
 
 _vp = ctypes.c_void_p

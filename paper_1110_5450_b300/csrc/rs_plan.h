@@ -111,6 +111,15 @@ struct rs_plan {
     int x_on = 0;
     rs::xstream::Params xp{};
     rs::DeviceBuf xbufs;
+    // external placement of the streaming kernels' tables (a serving
+    // arena): when ext_base is set, the streaming set-up carves its band or
+    // descriptor tables out of [ext_base, ext_base + ext_bytes) instead of
+    // allocating, and uploads host data through ext_staging (pinned) with
+    // copies on its stream, never synchronising
+    char *ext_base = nullptr;
+    size_t ext_bytes = 0;
+    unsigned char *ext_staging = nullptr;
+    size_t ext_staging_bytes = 0;
     // interpolating cubic B-spline: coefficients of the input (RS_PREFILTER)
     int prefilter = 0;
     rs::DeviceBuf pbufs;
@@ -219,6 +228,8 @@ int widths(rs_plan *p, const Opts &o, int *out, int n);
 // Rebuilds its band tables from the plan's weight tables (after a recompute).
 rs_status rebuild(rs_plan *p, cudaStream_t s);
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
+// Row-range counts the configuration searches model (ascending).
+std::vector<int> range_counts(int n_strips, int64_t slots, int max_nr);
 } // namespace stream
 
 namespace xstream {
@@ -226,10 +237,10 @@ namespace xstream {
 // channels, a 16-byte row pitch, 4 or 6 taps per output on both axes, window
 // starts that advance by 0 or 1 per output: an upscale or scale 1).
 bool eligible(const rs_plan *p);
-// Configures it (o.hw horizontal warps, o.ni_min staged blocks, o.sw strip
+// Configures it on `s` (o.hw horizontal warps, o.ni_min staged blocks, o.sw strip
 // width, o.pf, o.vw, o.nr; zeros choose the defaults); RS_ERR_UNSUPPORTED when the plan
 // is not eligible.  The kernel reads the plan's weight tables directly.
-rs_status setup(rs_plan *p, const stream::Opts &o);
+rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o);
 // Strip widths it admits, best first by the cost model (at most n).
 int widths(rs_plan *p, const stream::Opts &o, int *out, int n);
 } // namespace xstream

@@ -13,6 +13,12 @@
 //     persistent fused launch per (channels, dtype, group size, TMA) class,
 //     on one of several streams, so that requests arriving while others run
 //     are admitted as memory frees and their work overlaps on the device;
+//   * runs every large request (2^20 output pixels or more, a 16-byte row
+//     pitch) alone on the row-streaming kernels -- the same kernels a plan
+//     picks untuned -- through a plan object whose tables, band tables and
+//     group descriptors all live in the request's arena block (window starts
+//     from their closed form on the host, uploads through the slot's pinned
+//     staging), so large requests no longer queue behind the tile kernel;
 //   * timestamps completion in a host callback queued behind each launch,
 //     which also returns the request's tables to the arena.
 // All device waits inside the kernels are bounded; the server never runs an
@@ -98,6 +104,7 @@ struct Req {
     rs_request r{};
     uint64_t ticket = 0;
     uint64_t t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
+    uint64_t t_gpu_start = 0, t_gpu_end = 0;
     int32_t status = RS_ERR_BUSY;
     int32_t launch_id = -1, batch_size = 0;
     // device placement (arena offsets)
@@ -111,6 +118,11 @@ struct Req {
     fused::Params P{};
     int G = 0, use_tma = 0, cls = 0;
     fused::Work regions{};
+    // large requests: run alone on the row-streaming kernels through a plan
+    // object over the request's arena block (sx: the streaming tables' part)
+    bool big = false;
+    rs_plan *sp = nullptr;
+    size_t sx_off = 0, sx_bytes = 0;
 };
 
 struct Slot {
@@ -124,8 +136,17 @@ struct Slot {
     DeviceBuf dparams, dmaps, doff;
     void *host = nullptr;
     size_t cap = 0;
+    unsigned char *xstage = nullptr; // pinned staging of a large request's streaming descriptors
+    // GPU clock (%globaltimer, ns) when the launch's work started and ended on
+    // the device: written by one-thread kernels around it, copied to the
+    // pinned hstamp before the completion callback
+    DeviceBuf dstamp;
+    uint64_t *hstamp = nullptr;
     struct rs_server *owner = nullptr;
 };
+
+constexpr size_t kXStage = 256 * 1024;       // bytes of that staging per slot
+constexpr int64_t kBigPixels = int64_t(1) << 20; // output pixels from which a request streams
 
 } // namespace
 
@@ -149,6 +170,7 @@ struct rs_server {
     int launches = 0;
     // statistics
     uint64_t completed = 0, rejected = 0, out_pixels = 0, max_batch_seen = 0, max_in_use = 0;
+    std::atomic<uint64_t> streamed{0}; // launches that ran on the row-streaming kernels
     std::string error;
     ~rs_server()
     {
@@ -156,6 +178,8 @@ struct rs_server {
         for (int k = 0; k < nslots; ++k) {
             if (slots[k].stream) cudaStreamDestroy(slots[k].stream);
             if (slots[k].host) cudaFreeHost(slots[k].host);
+            if (slots[k].xstage) cudaFreeHost(slots[k].xstage);
+            if (slots[k].hstamp) cudaFreeHost(slots[k].hstamp);
         }
         if (arena_base) cudaFree(arena_base);
     }
@@ -174,6 +198,35 @@ struct FastPlan {
 };
 
 int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int64_t floor_div64(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Window starts of an axis in closed form (what the weight-table kernel
+// stores): the first raw tap j_lo = floor(((2i+1) n_in - R D - n_out) /
+// (2 n_out)) + 1, moved into [0, n_in - t_eff] -- for every boundary rule the
+// smallest input a window's taps map to is j_lo if j_lo >= 0, else 0, and
+// the stored window starts there or at the last full window.
+void host_starts(const AxisGeom &g, std::vector<int32_t> &st)
+{
+    st.resize(size_t(g.n_out));
+    const int64_t RD = g.R * g.D;
+    for (int64_t i = 0; i < g.n_out; ++i) {
+        const int64_t jlo = floor_div64((2 * i + 1) * g.n_in - RD - g.n_out, 2 * g.n_out) + 1;
+        st[size_t(i)] = int32_t(std::min<int64_t>(std::max<int64_t>(jlo, 0), g.n_in - g.t_eff));
+    }
+}
+
+// Bytes the row-streaming kernels' tables of a request may take at most:
+// the band kernels' bases and bands (at most 40 taps x 4 outputs across, 32
+// taps x 8 floats down per group of 4 rows) or the pipelined kernel's group
+// descriptors, whichever is larger.
+size_t stream_space(const AxisGeom &gy, const AxisGeom &gx)
+{
+    const size_t gxn = size_t((gx.n_out + 3) / 4), gyn = size_t((gy.n_out + 3) / 4);
+    const size_t band = up256(gxn * 4) + up256(gxn * 40 * 4 * 4) + up256((gyn + 4) * 4) + up256(gyn * 32 * 8 * 4);
+    const size_t desc = up256(gxn * 4) + up256((gyn + 8) * 4);
+    return std::max(band, desc) + 256;
+}
 
 // Geometry and kernel configuration of a request from closed-form bounds
 // (no device readback).  Fills r->gy/gx/G/P (except pointers) and the byte
@@ -299,8 +352,15 @@ FastPlan fast_plan(rs_server *S, Req *q)
                     const int64_t slots =
                         a == 0 ? groups : (groups + ngx - 1) / ngx * fused::pair_slots(ngx);
                     tb += 3 * up256(size_t(g.n_out) * 4) + up256(size_t(g.n_out) * g.t_eff * 8) +
-                          up256(size_t(g.n_out) * g.t_eff * asz) + up256(size_t(groups) * 4) +
+                          up256(size_t(g.n_out + 4) * g.t_eff * asz) + up256(size_t(groups) * 4) +
                           up256(size_t(slots) * js * asz);
+                }
+                // a large request streams (the tile plan above stays its fallback)
+                q->big = oh * ow >= kBigPixels && q->use_tma && d.in_dtype != RS_F64 && !(d.flags & RS_NO_STREAM);
+                if (q->big) {
+                    q->sx_off = tb;
+                    q->sx_bytes = stream_space(q->gy, q->gx);
+                    tb += up256(q->sx_bytes);
                 }
                 q->tab_bytes = tb;
                 q->own_out = q->r.d_out == nullptr;
@@ -341,7 +401,7 @@ void place_tables(rs_server *S, Req *q)
         t.cnt = reinterpret_cast<int32_t *>(take(size_t(g.n_out) * 4));
         t.start = reinterpret_cast<int32_t *>(take(size_t(g.n_out) * 4));
         t.w64 = reinterpret_cast<double *>(take(size_t(g.n_out) * g.t_eff * 8));
-        t.wwork = take(size_t(g.n_out) * g.t_eff * asz);
+        t.wwork = take(size_t(g.n_out + 4) * g.t_eff * asz); // 4 spare rows (zeroed before a streamed launch)
         t.band_base = reinterpret_cast<int32_t *>(take(size_t(groups) * 4));
         t.band_w = take(size_t(band_slots(t)) * js * asz);
     }
@@ -356,15 +416,103 @@ void place_tables(rs_server *S, Req *q)
 
 void on_launch_done(void *arg);
 
-// Launches one class's group on a reserved slot.  Called WITHOUT the server
-// mutex: the group and the slot belong to the scheduler until the launch's
-// completion callback fires.  Returns an error message or an empty string.
+// One thread: the GPU clock into *t (the start or end of a launch's work).
+__global__ void stamp_kernel(uint64_t *t)
+{
+    uint64_t v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    *t = v;
+}
+
+// After a launch's work on the slot's stream: the end stamp, the copy of both
+// stamps to the host, then the completion callback.  Returns an error message
+// or an empty string.
+std::string finish_launch(Slot &slot)
+{
+    cudaStream_t st = slot.stream;
+    std::string err;
+    stamp_kernel<<<1, 1, 0, st>>>(static_cast<uint64_t *>(slot.dstamp.p) + 1);
+    cudaMemcpyAsync(slot.hstamp, slot.dstamp.p, 16, cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaLaunchHostFunc(st, on_launch_done, &slot);
+    if (e != cudaSuccess) {
+        // no callback will come: complete the slot from here
+        err = std::string("server callback: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        cudaStreamSynchronize(st);
+        slot.t_done.store(now_ns());
+        slot.done.store(true, std::memory_order_release);
+    }
+    return err;
+}
+
+// A large request alone on the row-streaming kernels (its weight tables are
+// computed on the slot's stream first).  False if no streaming configuration
+// takes it (the caller then runs its tile plan).
+bool launch_streamed(rs_server *S, Slot &slot, Req *q)
+{
+    cudaStream_t st = slot.stream;
+    const int dt = q->r.desc.in_dtype;
+    const size_t asz = dt == RS_F64 ? 8 : 4;
+    WeightArgs a0, a1;
+    a0.g = q->gy;
+    a0.t = q->ty;
+    a1.g = q->gx;
+    a1.t = q->tx;
+    a0.work_is_double = a1.work_is_double = 0;
+    a0.err = a1.err = static_cast<int *>(S->derr.p);
+    launch_weights(a0, a1, st);
+    for (const auto &at : {a0, a1}) // the spare rows that groups of 4 read past the last output
+        cudaMemsetAsync(static_cast<char *>(at.t.wwork) + size_t(at.g.n_out) * at.g.t_eff * asz, 0,
+                        size_t(4) * at.g.t_eff * asz, st);
+    rs_plan *p = new (std::nothrow) rs_plan();
+    if (!p) return false;
+    p->desc = q->r.desc;
+    p->device = S->device;
+    p->num_sms = S->num_sms;
+    p->gy = q->gy;
+    p->gx = q->gx;
+    p->ty = q->ty;
+    p->tx = q->tx;
+    p->d_err = static_cast<int *>(S->derr.p);
+    p->path = 0;
+    host_starts(q->gy, p->host_start_y);
+    host_starts(q->gx, p->host_start_x);
+    p->ext_base = static_cast<char *>(S->arena_base) + q->tab_off + q->sx_off;
+    p->ext_bytes = q->sx_bytes;
+    p->ext_staging = slot.xstage;
+    p->ext_staging_bytes = kXStage;
+    if (stream::setup(p, st, stream::Opts()) != RS_OK) {
+        cudaGetLastError();
+        delete p;
+        return false;
+    }
+    p->use_stream = 1;
+    if (stream::launch(p, q->r.d_in, q->d_out, st) != RS_OK) {
+        cudaGetLastError();
+        delete p;
+        return false;
+    }
+    q->sp = p; // released when the launch has completed
+    S->streamed.fetch_add(1, std::memory_order_relaxed);
+    return true;
+}
+
+// Launches one class's group (or one large request) on a reserved slot.
+// Called WITHOUT the server mutex: the group and the slot belong to the
+// scheduler until the launch's completion callback fires.  Returns an error
+// message or an empty string.
 std::string launch(rs_server *S, Slot &slot, std::vector<Req *> &group)
 {
     const int n = int(group.size());
     const Req *q0 = group[0];
     const int C = q0->r.desc.channels, dt = q0->r.desc.in_dtype;
     cudaStream_t st = slot.stream;
+    stamp_kernel<<<1, 1, 0, st>>>(static_cast<uint64_t *>(slot.dstamp.p));
+    bool tables_done = false;
+    if (n == 1 && group[0]->big) {
+        if (launch_streamed(S, slot, group[0])) return finish_launch(slot);
+        tables_done = true; // the weight tables are on the stream already
+    }
     // weight and band tables of every request (asynchronous, in stream order)
     for (Req *q : group) {
         WeightArgs a0, a1;
@@ -374,7 +522,7 @@ std::string launch(rs_server *S, Slot &slot, std::vector<Req *> &group)
         a1.t = q->tx;
         a0.work_is_double = a1.work_is_double = dt == RS_F64 ? 1 : 0;
         a0.err = a1.err = static_cast<int *>(S->derr.p);
-        launch_weights(a0, a1, st);
+        if (!tables_done) launch_weights(a0, a1, st);
         launch_band(a0, a1, st);
     }
     // launch arrays: parameters, tensor maps, tile prefix sums
@@ -444,16 +592,8 @@ std::string launch(rs_server *S, Slot &slot, std::vector<Req *> &group)
         err = std::string("server launch: ") + cudaGetErrorString(e);
         cudaGetLastError();
     }
-    e = cudaLaunchHostFunc(st, on_launch_done, &slot);
-    if (e != cudaSuccess) {
-        // no callback will come: complete the slot from here
-        err = std::string("server callback: ") + cudaGetErrorString(e);
-        cudaGetLastError();
-        cudaStreamSynchronize(st);
-        slot.t_done.store(now_ns());
-        slot.done.store(true, std::memory_order_release);
-    }
-    return err;
+    const std::string fin = finish_launch(slot);
+    return err.empty() ? fin : err;
 }
 
 // Completion callback (driver thread): never blocks and calls no CUDA API --
@@ -476,7 +616,11 @@ void collect(rs_server *S)
         const uint64_t t = slot.t_done.load(std::memory_order_relaxed);
         for (Req *q : slot.reqs) {
             q->t_done = t;
+            q->t_gpu_start = slot.hstamp[0];
+            q->t_gpu_end = slot.hstamp[1];
             q->status = S->error.empty() ? RS_OK : RS_ERR_CUDA;
+            delete q->sp; // a streamed request's plan object (no device memory of its own)
+            q->sp = nullptr;
             S->arena.release(q->tab_off, q->tab_bytes);
             ++S->completed;
             S->out_pixels += uint64_t(q->P.out_h) * uint64_t(q->P.out_w);
@@ -521,10 +665,15 @@ void scheduler(rs_server *S)
         for (int k = 0; k < S->nslots && !S->ready.empty(); ++k) {
             Slot &slot = S->slots[k];
             if (slot.busy) continue;
-            const int cls = S->ready.front()->cls;
+            const Req *first = S->ready.front();
+            const int cls = first->cls;
             std::vector<Req *> group, rest;
             for (Req *q : S->ready) {
-                if (q->cls == cls && int(group.size()) < S->d.max_batch)
+                // a large request runs alone (on the streaming kernels); the
+                // others group by class
+                const bool take = first->big ? group.empty() && q == first
+                                             : !q->big && q->cls == cls && int(group.size()) < S->d.max_batch;
+                if (take)
                     group.push_back(q);
                 else
                     rest.push_back(q);
@@ -597,6 +746,9 @@ rs_status rs_server_create(const rs_server_desc *desc, rs_server **out)
         if (e == cudaSuccess) e = cudaMalloc(&s.dmaps.p, sizeof(CUtensorMap) * nb);
         if (e == cudaSuccess) e = cudaMalloc(&s.doff.p, 4 * (nb + 1));
         if (e == cudaSuccess) e = cudaHostAlloc(&s.host, host, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s.xstage), kXStage, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc(&s.dstamp.p, 16);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s.hstamp), 16, cudaHostAllocDefault);
     }
     if (e != cudaSuccess) {
         delete S;
@@ -663,6 +815,8 @@ rs_status rs_batch_poll(rs_server *S, uint64_t ticket, rs_request_state *st)
     st->t_admit_ns = q->t_admit;
     st->t_launch_ns = q->t_launch;
     st->t_done_ns = q->t_done;
+    st->t_gpu_start_ns = q->t_gpu_start;
+    st->t_gpu_end_ns = q->t_gpu_end;
     st->launch_id = q->launch_id;
     st->batch_size = q->batch_size;
     return RS_OK;
@@ -721,6 +875,7 @@ rs_status rs_server_get_stats(rs_server *S, rs_server_stats *st)
     st->bytes_in_use = uint64_t(S->arena.in_use);
     st->max_bytes_in_use = S->max_in_use;
     st->max_batch = S->max_batch_seen;
+    st->streamed = S->streamed.load(std::memory_order_relaxed);
     return RS_OK;
 }
 

@@ -79,6 +79,28 @@ struct Strip {
 // per-block barriers, waits and task rounding, fitted to measured widths --
 // times the rows of its range plus the band and the pipeline fill); cheapest
 // first.
+} // namespace
+
+// Row-range counts worth modelling: the cost of a configuration depends on
+// its waves of CTAs (or CTAs per SM) and on its rows per range, which fall as
+// ranges are added, so for each count of waves only the largest range count
+// that still fits it can be best; plus the first few counts.  Ascending.
+std::vector<int> range_counts(int n_strips, int64_t slots, int max_nr)
+{
+    std::vector<int> c;
+    for (int nr = 1; nr <= 8 && nr <= max_nr; ++nr) c.push_back(nr);
+    for (int64_t w = 1; w <= 64; ++w) {
+        const int64_t v = w * slots / std::max(1, n_strips);
+        for (int64_t x = v - 1; x <= v + 1; ++x)
+            if (x >= 1 && x <= max_nr) c.push_back(int(x));
+    }
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    return c;
+}
+
+namespace {
+
 std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, const std::vector<int32_t> &hb,
                           int JH, int JV, int GV, int WP, const std::vector<int32_t> &vb, int pairs)
 {
@@ -151,7 +173,7 @@ std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, 
         const int n_strips = (groups_x + c.sw / kG - 1) / (c.sw / kG);
         const int64_t slots = int64_t(c.occ) * p->num_sms;
         c.cost = 1e300;
-        for (int nr = 1; nr <= 1024; ++nr) {
+        for (const int nr : range_counts(n_strips, slots, 1024)) {
             const int cand = (pairs + nr - 1) / nr;
             if (cand < 8 && nr > 1) break;
             if (!blocks_ok(cand)) continue;
@@ -251,7 +273,7 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
     p->stream_ok = 0;
     // the exact-window form where it applies (or when asked for)
     if (opts.ex != 0) {
-        const rs_status xs = xstream::setup(p, opts);
+        const rs_status xs = xstream::setup(p, s, opts);
         if (xs == RS_OK || opts.ex > 0) return xs;
     }
     p->x_on = 0;
@@ -285,14 +307,20 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
     const size_t o_hw = cv.take(size_t(groups_x) * JH * kG * 4);
     const size_t o_vb = cv.take(size_t((pairs + 3) & ~3) * 4); // the kernel copies whole 16-byte words
     const size_t o_vw = cv.take(size_t(pairs) * JV * vtap_floats(GV) * 4);
-    if (p->sbufs.p) {
-        cudaFree(p->sbufs.p);
-        p->sbufs.p = nullptr;
+    char *base = nullptr;
+    if (p->ext_base) {
+        if (cv.off > p->ext_bytes) return fail(RS_ERR_BUDGET, "streaming tables exceed their reserved space");
+        base = p->ext_base;
+    } else {
+        if (p->sbufs.p) {
+            cudaFree(p->sbufs.p);
+            p->sbufs.p = nullptr;
+        }
+        e = cudaMalloc(&p->sbufs.p, cv.off);
+        if (e != cudaSuccess) return cuda_fail(e, "allocating stream tables");
+        p->sbufs.n = cv.off;
+        base = static_cast<char *>(p->sbufs.p);
     }
-    e = cudaMalloc(&p->sbufs.p, cv.off);
-    if (e != cudaSuccess) return cuda_fail(e, "allocating stream tables");
-    p->sbufs.n = cv.off;
-    char *base = static_cast<char *>(p->sbufs.p);
     Params &sp = p->sp;
     std::memset(&sp, 0, sizeof sp);
     sp.in_h = gy.n_in;

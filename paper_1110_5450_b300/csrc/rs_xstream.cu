@@ -156,7 +156,9 @@ std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nth
             if (!P) continue;
         }
         Choice best;
-        for (int nr = nr_force > 0 ? nr_force : 1; nr <= (nr_force > 0 ? nr_force : 4096); ++nr) {
+        const std::vector<int> nrs =
+            nr_force > 0 ? std::vector<int>{nr_force} : stream::range_counts(n_strips, p->num_sms, 4096);
+        for (const int nr : nrs) {
             const int gpr = (g.groups_y + nr - 1) / nr;
             if (gpr < 8 && nr > 1 && nr_force <= 0) break;
             const int ranges = (g.groups_y + gpr - 1) / gpr;
@@ -235,7 +237,7 @@ int widths(rs_plan *p, const stream::Opts &o, int *out, int n)
     return k;
 }
 
-rs_status setup(rs_plan *p, const stream::Opts &o)
+rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
 {
     p->x_on = 0;
     Geometry g;
@@ -263,16 +265,28 @@ rs_status setup(rs_plan *p, const stream::Opts &o)
     std::vector<int32_t> host(cv.off / 4, 0);
     std::memcpy(host.data() + o_h / 4, g.hinfo.data(), g.hinfo.size() * 4);
     std::memcpy(host.data() + o_v / 4, g.vinfo.data(), g.vinfo.size() * 4);
-    if (p->xbufs.p) {
-        cudaFree(p->xbufs.p);
-        p->xbufs.p = nullptr;
+    char *base = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (p->ext_base) {
+        // the caller's space, uploaded through its pinned staging on `s`
+        if (cv.off > p->ext_bytes || cv.off > p->ext_staging_bytes)
+            return fail(RS_ERR_BUDGET, "pipelined-kernel descriptors exceed their reserved space");
+        std::memcpy(p->ext_staging, host.data(), cv.off);
+        e = cudaMemcpyAsync(p->ext_base, p->ext_staging, cv.off, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "uploading pipelined-kernel descriptors");
+        base = p->ext_base;
+    } else {
+        if (p->xbufs.p) {
+            cudaFree(p->xbufs.p);
+            p->xbufs.p = nullptr;
+        }
+        e = cudaMalloc(&p->xbufs.p, cv.off);
+        if (e != cudaSuccess) return cuda_fail(e, "allocating pipelined-kernel descriptors");
+        p->xbufs.n = cv.off;
+        e = cudaMemcpy(p->xbufs.p, host.data(), cv.off, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "uploading pipelined-kernel descriptors");
+        base = static_cast<char *>(p->xbufs.p);
     }
-    cudaError_t e = cudaMalloc(&p->xbufs.p, cv.off);
-    if (e != cudaSuccess) return cuda_fail(e, "allocating exact-window descriptors");
-    p->xbufs.n = cv.off;
-    e = cudaMemcpy(p->xbufs.p, host.data(), cv.off, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "uploading exact-window descriptors");
-    char *base = static_cast<char *>(p->xbufs.p);
     Params &xp = p->xp;
     std::memset(&xp, 0, sizeof xp);
     xp.in_h = p->gy.n_in;
