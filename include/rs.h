@@ -426,6 +426,8 @@ typedef struct {
     uint64_t completed, rejected, launches, out_pixels, pending;
     uint64_t bytes_in_use, max_bytes_in_use, max_batch;
     uint64_t streamed; /* launches of one large request on the row-streaming kernels */
+    uint64_t launch_host_ns; /* scheduler time spent issuing launches (host work + API calls) */
+    uint64_t stream_host_ns; /* of which issuing the large requests' launches              */
 } rs_server_stats;
 
 RS_API rs_status rs_server_create(const rs_server_desc *desc, rs_server **out);

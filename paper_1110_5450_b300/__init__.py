@@ -116,7 +116,8 @@ class rs_request_state(ctypes.Structure):
 
 class rs_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("completed", "rejected", "launches", "out_pixels", "pending",
-                                               "bytes_in_use", "max_bytes_in_use", "max_batch", "streamed")]
+                                               "bytes_in_use", "max_bytes_in_use", "max_batch", "streamed",
+                                               "launch_host_ns", "stream_host_ns")]
 
 
 _vp = ctypes.c_void_p

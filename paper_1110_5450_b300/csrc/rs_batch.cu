@@ -191,12 +191,9 @@ rs_status build_launch(rs_batch *b, cudaStream_t stream)
               fused::batch_extra(n);
     if (b->smem > 227 * 1024) return fail(RS_ERR_UNSUPPORTED, "batch: shared memory of the largest tiles too big");
     b->variant = b->plans[0]->variant;
-    cudaError_t e = cudaFuncSetAttribute(b->variant->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    int occ = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->variant->fn, fused::kThreads, b->smem);
-    if (e != cudaSuccess) return cuda_fail(e, "batch: occupancy");
+    const int occ = occupancy(b->variant->fn, fused::kThreads, b->smem);
     if (occ < 1) return fail(RS_ERR_UNSUPPORTED, "batch: kernel does not fit on an SM");
+    cudaError_t e = cudaSuccess;
     b->ctas = occ;
     b->grid = int(std::max<int64_t>(1, std::min<int64_t>(b->total_tiles, int64_t(occ) * b->plans[0]->num_sms)));
 

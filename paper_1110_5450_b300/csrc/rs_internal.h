@@ -88,6 +88,9 @@ struct WeightArgs {
 cudaError_t launch_weights(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s);
 // Band tables for the fused kernel (both axes, one launch).
 cudaError_t launch_band(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s);
+// Loads the weight-table and band kernels now rather than at their first
+// launch (lazy module loading).
+void preload_weights();
 
 // Element type code shared by the pass launchers.
 enum class Dt : int { F64 = RS_F64, F32 = RS_F32, F16 = RS_F16, BF16 = RS_BF16 };
@@ -122,5 +125,13 @@ rs_status validate_desc(const rs_plan_desc &in, rs_plan_desc *out);
 // The geometry of one axis of a validated descriptor (false with a reason when
 // it needs more than kMaxTaps taps per output).
 bool axis_setup(AxisGeom &g, int64_t n_in, int64_t n_out, const rs_plan_desc &d, std::string &why);
+
+// Resident CTAs per SM of kernel `fn` launched with `nthreads` threads and
+// `smem` bytes of dynamic shared memory on the current device, the kernel's
+// dynamic shared-memory limit raised to 227 KB.  The first call for a
+// (device, kernel, block size) tabulates where the count drops (the runtime's
+// occupancy query, bisected); later calls make no CUDA call.  0 when the
+// kernel cannot run so (or the queries failed).  Thread-safe.
+int occupancy(const void *fn, int nthreads, size_t smem);
 
 } // namespace rs

@@ -230,9 +230,15 @@ rs_status rebuild(rs_plan *p, cudaStream_t s);
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 // Row-range counts the configuration searches model (ascending).
 std::vector<int> range_counts(int n_strips, int64_t slots, int max_nr);
+// Loads every band-kernel instantiation of `dtype` (lazy module loading
+// would otherwise load each on its first launch, in the middle of a stream's
+// work) and tabulates its occupancy.
+void preload(int dtype);
 } // namespace stream
 
 namespace xstream {
+// As stream::preload, for the pipelined kernel.
+void preload(int dtype);
 // Whether the plan can run the pipelined kernel (FP32/FP16/BF16, 1 or 3
 // channels, a 16-byte row pitch, 4 or 6 taps per output on both axes, window
 // starts that advance by 0 or 1 per output: an upscale or scale 1).

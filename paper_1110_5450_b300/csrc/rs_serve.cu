@@ -171,6 +171,7 @@ struct rs_server {
     // statistics
     uint64_t completed = 0, rejected = 0, out_pixels = 0, max_batch_seen = 0, max_in_use = 0;
     std::atomic<uint64_t> streamed{0}; // launches that ran on the row-streaming kernels
+    uint64_t launch_host_ns = 0, stream_host_ns = 0; // host time issuing launches (all; streamed ones)
     std::string error;
     ~rs_server()
     {
@@ -576,9 +577,7 @@ std::string launch(rs_server *S, Slot &slot, std::vector<Req *> &group)
     const size_t smem = fused::layout_of(w.tin_bytes, w.wy_bytes, w.wx_bytes, w.tt_bytes, w.rec2_bytes, 1).total +
                         fused::batch_extra(n);
     const fused::Variant *var = find_variant(dt, C, q0->G);
-    cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var->fn, fused::kThreads, smem);
+    const int occ = occupancy(var->fn, fused::kThreads, smem);
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(w.total_tiles, int64_t(std::max(occ, 1)) * S->num_sms)));
     fused::Params p0;
     std::memset(&p0, 0, sizeof p0);
@@ -700,11 +699,19 @@ void scheduler(rs_server *S)
         // CUDA calls happen without the mutex
         lock.unlock();
         std::string err;
+        uint64_t t_all = 0, t_big = 0;
         for (auto &w : work) {
+            const uint64_t t0 = now_ns();
+            const bool big = w.second.size() == 1 && w.second[0]->big;
             std::string e = launch(S, *w.first, w.second);
             if (!e.empty()) err = e;
+            const uint64_t dt = now_ns() - t0;
+            t_all += dt;
+            t_big += big ? dt : 0;
         }
         lock.lock();
+        S->launch_host_ns += t_all;
+        S->stream_host_ns += t_big;
         if (!err.empty()) S->error = err;
         S->cv.notify_all();
     }
@@ -753,6 +760,22 @@ rs_status rs_server_create(const rs_server_desc *desc, rs_server **out)
     if (e != cudaSuccess) {
         delete S;
         return cuda_fail(e, "server: slots");
+    }
+    // load every kernel a launch may use now: under lazy module loading the
+    // first launch of each would otherwise stall a request by milliseconds
+    preload_weights();
+    {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, stamp_kernel) != cudaSuccess) cudaGetLastError();
+    }
+    for (const int dt : {int(RS_F64), int(RS_F32), int(RS_F16), int(RS_BF16)}) {
+        for (const int C : {1, 3})
+            for (const int G : {1, 2, 4, 8})
+                if (const fused::Variant *v = find_variant(dt, C, G)) occupancy(v->fn, fused::kThreads, 0);
+        if (dt != RS_F64) {
+            stream::preload(dt);
+            xstream::preload(dt);
+        }
     }
     S->th = std::thread(scheduler, S);
     *out = S;
@@ -876,6 +899,8 @@ rs_status rs_server_get_stats(rs_server *S, rs_server_stats *st)
     st->max_bytes_in_use = S->max_in_use;
     st->max_batch = S->max_batch_seen;
     st->streamed = S->streamed.load(std::memory_order_relaxed);
+    st->launch_host_ns = S->launch_host_ns;
+    st->stream_host_ns = S->stream_host_ns;
     return RS_OK;
 }
 

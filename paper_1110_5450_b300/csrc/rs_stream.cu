@@ -27,6 +27,21 @@ const void *kernel_for(int dtype, int C, int jv, int gv, bool ws)
     return nullptr;
 }
 
+} // namespace
+
+void preload(int dtype)
+{
+    for (const int C : {1, 3})
+        for (const bool ws : {false, true}) {
+            for (const int jv : kJV8)
+                if (const void *fn = kernel_for(dtype, C, jv, 8, ws)) occupancy(fn, kThreads, 0);
+            for (const int jv : kJV4)
+                if (const void *fn = kernel_for(dtype, C, jv, 4, ws)) occupancy(fn, kThreads, 0);
+        }
+}
+
+namespace {
+
 // Vertical taps of groups of GV output rows, rounded up to an instantiated
 // width (0 if none is wide enough).
 int vertical_taps(const std::vector<int32_t> &sy, int t_eff, int GV)
@@ -84,12 +99,15 @@ struct Strip {
 // Row-range counts worth modelling: the cost of a configuration depends on
 // its waves of CTAs (or CTAs per SM) and on its rows per range, which fall as
 // ranges are added, so for each count of waves only the largest range count
-// that still fits it can be best; plus the first few counts.  Ascending.
+// that still fits it can be best; plus the first few counts.  Beyond a few
+// waves more ranges only trade rows for waves one for one while adding each
+// range's pipeline fill, so waves stop at 8 (which also keeps the search
+// cheap enough for a server to run per request).  Ascending.
 std::vector<int> range_counts(int n_strips, int64_t slots, int max_nr)
 {
     std::vector<int> c;
     for (int nr = 1; nr <= 8 && nr <= max_nr; ++nr) c.push_back(nr);
-    for (int64_t w = 1; w <= 64; ++w) {
+    for (int64_t w = 1; w <= 8; ++w) {
         const int64_t v = w * slots / std::max(1, n_strips);
         for (int64_t x = v - 1; x <= v + 1; ++x)
             if (x >= 1 && x <= max_nr) c.push_back(int(x));
@@ -165,11 +183,8 @@ std::vector<Strip> strips(rs_plan *p, const Opts &opts_in, int C, int groups_x, 
     std::vector<Strip> ok;
     for (Strip c : out) {
         const void *fn = kernel_for(dtype, C, JV, GV, c.NW != 0);
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, fn, kThreads, c.smem) != cudaSuccess || c.occ < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        c.occ = rs::occupancy(fn, kThreads, c.smem);
+        if (c.occ < 1) continue;
         const int n_strips = (groups_x + c.sw / kG - 1) / (c.sw / kG);
         const int64_t slots = int64_t(c.occ) * p->num_sms;
         c.cost = 1e300;

@@ -513,6 +513,13 @@ static AxisConst axis_const(const AxisGeom &g)
     return k;
 }
 
+void preload_weights()
+{
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, weights_kernel) != cudaSuccess) cudaGetLastError();
+    if (cudaFuncGetAttributes(&a, band_kernel) != cudaSuccess) cudaGetLastError();
+}
+
 cudaError_t launch_weights(const WeightArgs &a0, const WeightArgs &a1, cudaStream_t s)
 {
     const int64_t h0 = (a0.g.n_out + 1) / 2, h1 = (a1.g.n_out + 1) / 2;

@@ -26,6 +26,19 @@ const void *kernel_for(int dtype, int C, int taps, int big)
     return nullptr;
 }
 
+} // namespace
+
+void preload(int dtype)
+{
+    for (const int C : {1, 3})
+        for (const int taps : {4, 6})
+            for (const int big : {0, 1})
+                if (const void *fn = kernel_for(dtype, C, taps, big))
+                    occupancy(fn, 32 * (big ? kMaxWarps : kSmallWarps), 0);
+}
+
+namespace {
+
 // Staged pitch >= n samples: whole 16-byte words, odd in 16-byte words (lanes
 // on consecutive rows reading 16 bytes hit distinct banks).
 int pad_pitch(int n, int es)
@@ -115,22 +128,7 @@ std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nth
     const int C = g.C, es = g.es;
     const int HR = 2 * kRB + g.JV, M = g.JV - 1, Q = (HR + M) | 1;
     const void *fn = kernel_for(p->desc.in_dtype, C, g.T, nthreads > 32 * kSmallWarps ? 1 : 0);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess) {
-        cudaGetLastError();
-        return out;
-    }
-    std::map<size_t, int> occ_of;
-    auto occupancy = [&](size_t smem) {
-        auto it = occ_of.find(smem);
-        if (it != occ_of.end()) return it->second;
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nthreads, smem) != cudaSuccess) {
-            cudaGetLastError();
-            occ = 0;
-        }
-        occ_of[smem] = occ;
-        return occ;
-    };
+    if (rs::occupancy(fn, nthreads, 0) < 1) return out;
     const int sw_max = C == 1 ? 252 : 128;
     for (int sw = 8; sw <= sw_max; sw += 4) {
         const int ngx = sw / kG, nch = sw * C / 4;
@@ -170,7 +168,7 @@ std::vector<Choice> choices(const rs_plan *p, const Geometry &g, int NI, int nth
             const int nblk = (rows + kRB - 1) / kRB;
             if (nblk <= 512) {
                 const size_t smem = layout(NI, P, Q, nch, ngx, g.T, g.WP, nblk, offB != 0, es).total;
-                const int occ = smem <= 227 * 1024 ? occupancy(smem) : 0;
+                const int occ = rs::occupancy(fn, nthreads, smem);
                 if (occ >= 1) {
                     const int64_t grid = int64_t(n_strips) * ranges;
                     const int64_t per_sm = (grid + p->num_sms - 1) / p->num_sms;
