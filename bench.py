@@ -144,28 +144,46 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-def kernel_source_hash():
+# the sources that define the dominant kernel (the pipelined streaming
+# kernel) and how it is configured: a change to any of them voids a recorded
+# traffic figure
+TRAFFIC_SOURCES = ("rs_xstream.cuh", "rs_xstream.cu", "rs_xstream_f32.cu", "rs_plan.h", "rs_stream.cu",
+                   "rs_weights.cu")
+
+
+def kernel_source_hash(files=TRAFFIC_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1110_5450_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "rs.h"), "rb").read())
+    for f in sorted(files):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(form=None):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, only if it was taken on the current kernel sources."""
+    summary, only if it was taken on the current kernel sources and, when
+    `form` (the streaming form tuple in use) is given, on that form."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("source_hash") == kernel_source_hash():
-            return float(d["dram_bytes_per_launch"])
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        if form is not None and list(d.get("form", [])) != list(form):
+            return None
+        return float(d["dram_bytes_per_launch"])
     except Exception:
-        pass
-    return None
+        return None
+
+
+def stream_form(rs, plan):
+    """(kind, h_warps, v_warps, staged_blocks, strip_width, row_ranges) of a
+    streaming plan, else None."""
+    if plan.path not in ("stream", "tcstream"):
+        return None
+    f = rs.rs_plan_get_stream_form(plan.handle)
+    return [f.kind, f.h_warps, f.v_warps, f.staged_blocks, f.strip_width, f.row_ranges]
 
 
 class ClockSampler:
@@ -344,7 +362,8 @@ def run_case(args):
     p.check()
     i = p.info
     print("path", p.path, "tile", [i.tile_h, i.tile_w], "group", i.group_h, "band", [i.span_h, i.span_w],
-          "stages", i.stages, "warps_pass1", i.warps_pass1, "smem", i.smem_bytes, "ctas_per_sm", i.ctas_per_sm)
+          "stages", i.stages, "warps_pass1", i.warps_pass1, "smem", i.smem_bytes, "ctas_per_sm", i.ctas_per_sm,
+          "form", stream_form(rs, p))
     p.close()
 
 
@@ -457,12 +476,14 @@ def tc_section(args, dev, stream, acc=None):
     """Precision form: the 4096x4096x3 sinusoid image stored in BF16 and FP16
     (FP32 accumulation), Lanczos-3 mirror, x1.37, x0.3 and x0.125.  Per dtype
     and scale: the autotuned plan ("auto": the fastest of the kernels below),
-    then each kernel forced where it applies -- the tensor-core vertical pass
-    (tcgen05, the default for the wide antialiased downscales), the SIMT tile
-    kernel and the row-streaming kernel; kernel time, HBM fraction, and the
-    largest difference from the FP32 path on the same input (the autotuned
-    results' errors against the FP64 oracle: the line's
-    accuracy_vs_fp64_oracle)."""
+    then each kernel forced where it applies -- the tensor-core streaming
+    downscale (stream form 3: the horizontal pass as a tcgen05 GEMM), the
+    fused tiles with the tcgen05 vertical pass, the SIMT tile kernel and the
+    SIMT row-streaming kernels (untuned form); kernel time (CUDA events per
+    launch, L2 flushed before each: the 16-bit input, 101 MB, would fit the
+    126 MB L2), HBM fraction, and the largest difference from the FP32 path
+    on the same input (the autotuned results' errors against the FP64
+    oracle: the line's accuracy_vs_fp64_oracle)."""
     import torch
 
     import paper_1110_5450_b300 as rs
@@ -470,13 +491,14 @@ def tc_section(args, dev, stream, acc=None):
 
     img = synth.sinusoids(4096, 4096, 3, seed=synth.SEED_C2)
     x32 = torch.from_numpy(img).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peak, _ = measured_peaks()
     res = {"workload": "4096x4096x3 sinusoids+noise, Lanczos-3 mirror, BF16/FP16 storage, FP32 accumulation",
-           "runs": []}
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    variants = (("auto", 0), ("tcgen05", rs.RS_FORCE_TC), ("tile", rs.RS_FORCE_SIMT | rs.RS_NO_STREAM),
-                ("stream", rs.RS_FORCE_STREAM))
+           "l2": "256 MB buffer written before each timed launch", "runs": []}
+    # (label, plan flags, stream form forced after creation or None, autotune)
+    variants = (("auto", 0, None, True), ("tcstream", 0, 3, False), ("tcgen05", rs.RS_FORCE_TC, None, True),
+                ("tile", rs.RS_FORCE_SIMT | rs.RS_NO_STREAM, None, True), ("stream", rs.RS_FORCE_STREAM, -1, False))
+    s = stream.cuda_stream
     for tdt, name in ((torch.bfloat16, "bf16"), (torch.float16, "f16")):
         x = x32.to(tdt)
         for sc in (1.37, 0.3, 0.125):
@@ -484,30 +506,43 @@ def tc_section(args, dev, stream, acc=None):
                 p32 = rs.Plan(4096, 4096, 3, scale=sc, kernel="lanczos", param=3.0, boundary="mirror",
                               dtype=torch.float32, stream=stream)
                 y32 = p32(x32, stream=stream)
-            for label, flags in variants:
+            for label, flags, form, tune in variants:
                 try:
                     with torch.cuda.stream(stream):
                         p = rs.Plan(4096, 4096, 3, scale=sc, kernel="lanczos", param=3.0, boundary="mirror",
                                     dtype=tdt, flags=flags, stream=stream)
-                except RuntimeError as e:
+                    if form == 3:
+                        rs.rs_plan_set_stream_form(p.handle, 3, 0, 0, 0, 0, s)
+                        p.info = rs.rs_plan_get_info(p.handle)
+                    elif form == -1 and p.path == "tcstream":
+                        # the SIMT streaming kernels: the band kernel's untuned form
+                        rs.rs_plan_set_stream_form(p.handle, 1, 0, 0, 0, 0, s)
+                        p.info = rs.rs_plan_get_info(p.handle)
+                except (RuntimeError, rs.RSError) as e:
                     if "unsupported" not in str(e):
                         raise
                     continue  # this kernel does not apply to this scale
                 with torch.cuda.stream(stream):
                     y = torch.empty(p.out_shape, dtype=tdt, device=dev)
-                    if not args.no_tune:
+                    if tune and not args.no_tune:
                         p.autotune(x, out=y, stream=stream, cache_path=args.tune_cache)
                     for _ in range(3):
                         p(x, out=y, stream=stream)
                 torch.cuda.synchronize()
-                reps = 20
-                a.record(stream)
-                for _ in range(reps):
-                    p(x, out=y, stream=stream)
-                b.record(stream)
+                reps = 10
+                ev = []
+                with torch.cuda.stream(stream):
+                    for _ in range(reps):
+                        flush.fill_(1)
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        p(x, out=y, stream=stream)
+                        b.record(stream)
+                        ev.append((a, b))
                 torch.cuda.synchronize()
                 p.check()
-                us = a.elapsed_time(b) / reps * 1e3
+                us = sum(a.elapsed_time(b) for a, b in ev) / reps * 1e3
                 alg = x.numel() * 2 + y.numel() * 2
                 info = p.info
                 if acc is not None and label == "auto":
@@ -517,13 +552,16 @@ def tc_section(args, dev, stream, acc=None):
                         (lambda tdt=tdt: torch.from_numpy(img).to(tdt).to(torch.float64).numpy()),
                         y.shape[0], y.shape[1], "lanczos", 3.0, "mirror", rows, y[rows].double().cpu().numpy(),
                         1e-2 if name == "bf16" else 2e-3))
-                res["runs"].append({
+                run = {
                     "dtype": name, "scale": sc, "variant": label, "path": rs.PATHS[info.path], "us": us,
                     "GBps": alg / (us / 1e6) / 1e9, "hbm_frac": alg / (us / 1e6) / 1e9 / peak,
                     "out_mpx_s": y.shape[0] * y.shape[1] / us,
                     "max_abs_diff_vs_fp32_path": float((y.float() - y32).abs().max()),
                     "tile": [info.tile_h, info.tile_w], "group": info.group_h, "band": info.span_h,
-                    "smem": info.smem_bytes, "ctas_per_sm": info.ctas_per_sm})
+                    "smem": info.smem_bytes, "ctas_per_sm": info.ctas_per_sm}
+                if info.path in (3, 5):
+                    run["form"] = stream_form(rs, p)
+                res["runs"].append(run)
                 p.close()
             p32.close()
     return res
@@ -1030,7 +1068,8 @@ def main():
                                            "smem": pl.info.smem_bytes, "ctas_per_sm": pl.info.ctas_per_sm}
                                  for sc, pl in zip(SCALES, plans)}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(),
+                         "frac": achieved / peak, "traffic": recorded_traffic(stream_form(rs, plans[0])),
+                         "form": stream_form(rs, plans[0]),
                          "kernel": "resample x1.37 (%s kernel)" % rs.PATHS[plans[0].info.path], "algorithmic_bytes": alg,
                          "avg_kernel_ms": k_avg_s * 1e3, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
             "e2e": e2e,

@@ -956,7 +956,9 @@ rs_status rs_plan_create(const rs_plan_desc *desc, void *stream_v, rs_plan **out
         // streaming kernel is forced; the autotuner times both)
         const rs_status ss = stream::setup(p, stream);
         if (ss == RS_OK) {
-            p->use_stream = (!p->chosen.tc || (d.flags & RS_FORCE_STREAM)) ? 1 : 0;
+            // (the tensor-core downscale form is itself a tensor-core kernel)
+            p->use_stream =
+                (!p->chosen.tc || (d.flags & RS_FORCE_STREAM) || (p->tcs_on && !(d.flags & RS_FORCE_TC))) ? 1 : 0;
         } else if (ss != RS_ERR_UNSUPPORTED) {
             delete p;
             return ss;
@@ -1197,18 +1199,21 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
         double us_tile = 0;
         s = time_plan(p, d_in, d_out, stream, &us_tile);
         if (s != RS_OK) return s;
-        // {pipelined kernel, warp-specialised, horizontal warps, staged blocks, L2 prefetch, unused,
-        //  vertical warps of the pipelined kernel}
+        // {form (0 band kernels, 1 pipelined, 2 tensor-core downscale), warp-specialised,
+        //  horizontal warps, staged blocks (chunks), L2 prefetch, unused, vertical warps}
         const int cands_s[][7] = {{0, 0, 0, 3, 0, 0, 0}, {0, 0, 0, 2, 0, 0, 0}, {0, 1, 4, 3, 0, 0, 0},
                                   {0, 1, 4, 2, 0, 0, 0}, {0, 1, 3, 3, 0, 0, 0}, {0, 1, 5, 3, 0, 0, 0},
                                   {0, 1, 5, 2, 0, 0, 0}, {1, 0, 4, 2, 0, 0, 4}, {1, 0, 4, 2, 0, 0, 3},
                                   {1, 0, 5, 2, 0, 0, 4}, {1, 0, 4, 2, 0, 0, 5}, {1, 0, 3, 2, 0, 0, 4},
-                                  {1, 0, 4, 3, 0, 0, 4}, {1, 0, 7, 2, 0, 0, 8}, {1, 0, 8, 2, 0, 0, 7}};
-        const bool x_ok = xstream::eligible(p);
+                                  {1, 0, 4, 3, 0, 0, 4}, {1, 0, 7, 2, 0, 0, 8}, {1, 0, 8, 2, 0, 0, 7},
+                                  {2, 0, 0, 4, 0, 0, 4}, {2, 0, 0, 4, 0, 0, 6}, {2, 0, 0, 4, 0, 0, 8},
+                                  {2, 0, 0, 4, 0, 0, 10}, {2, 0, 0, 3, 0, 0, 6}, {2, 0, 0, 6, 0, 0, 6},
+                                  {2, 0, 0, 4, 1, 0, 8}, {2, 0, 0, 4, 1, 0, 10}};
+        const bool x_ok = xstream::eligible(p), t_ok = tcstream::eligible(p);
         double best_s = 1e300;
         int best_code = 0;
         for (const auto &c : cands_s) {
-            if (c[0] && !x_ok) continue;
+            if ((c[0] == 1 && !x_ok) || (c[0] == 2 && !t_ok)) continue;
             stream::Opts o;
             o.ex = c[0];
             o.ws = c[1];
@@ -1314,7 +1319,14 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
 rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *stream_v)
 {
     if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
-    if (f->kind < 0 || f->kind > 2 || f->h_warps < 0 || f->h_warps > 8 || (f->kind != 2 && f->h_warps > 6) ||
+    if (f->kind == 3) {
+        // the tensor-core downscale: staged chunks (2..6) and vertical warps (1..8); no other choice
+        if (f->h_warps || (f->prefetch != 0 && f->prefetch != 1) || f->row_ranges || f->strip_width ||
+            f->staged_blocks < 0 ||
+            f->staged_blocks == 1 || f->staged_blocks > tcstream::kMaxNA || f->v_warps < 0 ||
+            f->v_warps > tcstream::kMaxVW)
+            return fail(RS_ERR_INVALID_ARG, "malformed streaming form");
+    } else if (f->kind < 0 || f->kind > 2 || f->h_warps < 0 || f->h_warps > 8 || (f->kind != 2 && f->h_warps > 6) ||
         f->v_warps < 0 || f->v_warps > 12 || (f->v_warps && f->kind != 2) || f->h_warps + f->v_warps > 15 ||
         f->row_ranges < 0 || f->row_ranges > 255 ||
         (f->row_ranges && f->kind != 2) || f->staged_blocks < 0 ||
@@ -1325,11 +1337,11 @@ rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *str
     if (p->path != 0 || p->prefilter)
         return fail(RS_ERR_UNSUPPORTED, "the plan has no fused path for the streaming kernel");
     stream::Opts o;
-    o.ex = f->kind == 2 ? 1 : 0;
+    o.ex = f->kind == 3 ? 2 : f->kind == 2 ? 1 : 0;
     o.ws = f->kind == 1 ? 1 : 0;
     o.hw = f->h_warps;
     if (f->kind == 1 && f->h_warps == 1) return fail(RS_ERR_INVALID_ARG, "kind 1 takes 2..6 horizontal warps");
-    o.ni_min = f->staged_blocks ? f->staged_blocks : (f->kind == 2 ? 2 : 3);
+    o.ni_min = f->staged_blocks ? f->staged_blocks : (f->kind == 2 ? 2 : f->kind == 3 ? 0 : 3);
     o.sw = f->strip_width;
     o.pf = f->prefetch;
     o.vw = f->v_warps;
@@ -1353,6 +1365,16 @@ rs_status rs_plan_get_stream_form(const rs_plan *p, rs_stream_form *f)
     if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
     if (!p->stream_ok) return fail(RS_ERR_UNSUPPORTED, "the plan has no streaming configuration");
     const stream::Opts o = stream::Opts::decode(p->stream_code);
+    if (p->tcs_on) {
+        f->kind = 3;
+        f->h_warps = 0;
+        f->staged_blocks = p->tcp.NA;
+        f->strip_width = p->tcp.NP;
+        f->prefetch = p->tcp.pf ? 1 : 0;
+        f->v_warps = p->tcp.VW;
+        f->row_ranges = 0;
+        return RS_OK;
+    }
     f->kind = o.ex > 0 ? 2 : (o.ws > 0 ? 1 : 0);
     f->h_warps = p->x_on ? p->xp.HW : (o.ws > 0 ? p->sp.HW : 0);
     f->staged_blocks = p->x_on ? p->xp.NI : p->sp.NI;
@@ -1431,6 +1453,18 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
         info->stages = 0;
         info->smem_bytes = 0;
         info->ctas_per_sm = 0;
+    } else if (p->path == 0 && p->use_stream && p->tcs_on) {
+        info->path = 5;
+        info->tile_h = tcstream::kM;   // input rows per tensor-core block
+        info->tile_w = p->tcp.NP;      // output pixels per strip
+        info->group_h = 1;
+        info->group_w = p->tcp.NP;
+        info->span_h = p->tcp.Ty;
+        info->span_w = p->tcp.Kc / p->desc.channels; // staged input pixels per strip
+        info->warps_pass1 = 0;
+        info->stages = p->tcp.NA;
+        info->smem_bytes = int32_t(p->s_smem);
+        info->ctas_per_sm = p->s_ctas;
     } else if (p->path == 0 && p->use_stream && p->x_on) {
         info->path = 3;
         info->tile_h = xstream::kRB;

@@ -12,6 +12,7 @@
 #include "rs_fused.cuh"
 #include "rs_internal.h"
 #include "rs_stream.cuh"
+#include "rs_tcstream.cuh"
 #include "rs_xstream.cuh"
 
 namespace rs {
@@ -111,6 +112,12 @@ struct rs_plan {
     int x_on = 0;
     rs::xstream::Params xp{};
     rs::DeviceBuf xbufs;
+    // the tensor-core downscale form (16-bit downscales): when tcs_on, s_fn /
+    // s_block / s_smem / s_grid describe it, tcp holds its parameters and
+    // tcbufs its per-strip weight matrices; stmap is its 3-D input map
+    int tcs_on = 0;
+    rs::tcstream::Params tcp{};
+    rs::DeviceBuf tcbufs;
     // external placement of the streaming kernels' tables (a serving
     // arena): when ext_base is set, the streaming set-up carves its band or
     // descriptor tables out of [ext_base, ext_base + ext_bytes) instead of
@@ -187,8 +194,11 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 
 namespace stream {
 // Choices of a streaming configuration: ex = 1 the pipelined kernel
-// (rs_xstream.cuh), 0 the band kernels of rs_stream.cuh, -1 the pipelined
-// kernel where it applies with its default choices, else the band kernels; ws = 1
+// (rs_xstream.cuh), 2 the tensor-core downscale (rs_tcstream.cuh), 0 the band
+// kernels of rs_stream.cuh, -1 the pipelined kernel where it applies with its
+// default choices, else the tensor-core downscale where it applies, else the
+// band kernels (ni_min and vw give the tensor-core kernel's staged chunks and
+// vertical warps when ex = 2); ws = 1
 // warp-specialised band kernel, 0 phase-alternating, -1 either
 // (warp-specialised first); hw = warps on the horizontal pass (0: the form's
 // default); ni_min = fewest staged input blocks of a narrow strip (the
@@ -202,8 +212,8 @@ struct Opts {
     int nr = 0; // pipelined kernel: row ranges (0: the cost model's choice), < 256
     int code() const
     {
-        return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4) + (ex > 0 ? 32768 : 0) + (pf ? 65536 : 0) +
-               (vw << 18) + (nr << 22);
+        return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4) + (ex == 1 ? 32768 : 0) +
+               (pf ? 65536 : 0) + (ex == 2 ? 131072 : 0) + (vw << 18) + (nr << 22);
     }
     static Opts decode(int c)
     {
@@ -212,7 +222,7 @@ struct Opts {
         o.hw = (c >> 2) & 15;
         o.ni_min = (c >> 6) & 7;
         o.sw = ((c >> 9) & 63) * 4;
-        o.ex = (c >> 15) & 1;
+        o.ex = ((c >> 17) & 1) ? 2 : (c >> 15) & 1;
         o.pf = (c >> 16) & 1;
         o.vw = (c >> 18) & 15;
         o.nr = (c >> 22) & 255;
@@ -235,6 +245,24 @@ std::vector<int> range_counts(int n_strips, int64_t slots, int max_nr);
 // work) and tabulates its occupancy.
 void preload(int dtype);
 } // namespace stream
+
+namespace tcstream {
+// Whether the plan can run the tensor-core downscale (FP16/BF16, 1 or 3
+// channels, both axes downscaled, in_w * channels a multiple of 8, a 16-byte
+// row pitch, at most 128 vertical taps).
+bool eligible(const rs_plan *p);
+// Configures it on `s` (o.ni_min staged chunks and o.vw vertical warps when
+// o.ex = 2; else the defaults): the strips' weight matrices are built on the
+// device from the plan's tables.  RS_ERR_UNSUPPORTED when not eligible.
+rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o);
+// Rebuilds the weight matrices from the plan's weight tables (after a recompute).
+rs_status rebuild(rs_plan *p, cudaStream_t s);
+rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
+// Bytes of its device tables at most, for external placement (a serving arena).
+size_t space_bound(const AxisGeom &gx, int C);
+// As stream::preload.
+void preload(int dtype);
+} // namespace tcstream
 
 namespace xstream {
 // As stream::preload, for the pipelined kernel.

@@ -219,14 +219,16 @@ void host_starts(const AxisGeom &g, std::vector<int32_t> &st)
 
 // Bytes the row-streaming kernels' tables of a request may take at most:
 // the band kernels' bases and bands (at most 40 taps x 4 outputs across, 32
-// taps x 8 floats down per group of 4 rows) or the pipelined kernel's group
-// descriptors, whichever is larger.
-size_t stream_space(const AxisGeom &gy, const AxisGeom &gx)
+// taps x 8 floats down per group of 4 rows), the pipelined kernel's group
+// descriptors or the tensor-core downscale's per-strip weight matrices,
+// whichever is largest.
+size_t stream_space(const AxisGeom &gy, const AxisGeom &gx, int C)
 {
     const size_t gxn = size_t((gx.n_out + 3) / 4), gyn = size_t((gy.n_out + 3) / 4);
     const size_t band = up256(gxn * 4) + up256(gxn * 40 * 4 * 4) + up256((gyn + 4) * 4) + up256(gyn * 32 * 8 * 4);
     const size_t desc = up256(gxn * 4) + up256((gyn + 8) * 4);
-    return std::max(band, desc) + 256;
+    const size_t tcs = gx.n_out < gx.n_in ? tcstream::space_bound(gx, C) : 0;
+    return std::max(std::max(band, desc), tcs) + 256;
 }
 
 // Geometry and kernel configuration of a request from closed-form bounds
@@ -360,7 +362,7 @@ FastPlan fast_plan(rs_server *S, Req *q)
                 q->big = oh * ow >= kBigPixels && q->use_tma && d.in_dtype != RS_F64 && !(d.flags & RS_NO_STREAM);
                 if (q->big) {
                     q->sx_off = tb;
-                    q->sx_bytes = stream_space(q->gy, q->gx);
+                    q->sx_bytes = stream_space(q->gy, q->gx, C);
                     tb += up256(q->sx_bytes);
                 }
                 q->tab_bytes = tb;

@@ -274,6 +274,11 @@ rs_status bands_of(const rs_plan *p, Bands &b)
 
 int widths(rs_plan *p, const Opts &opts, int *out, int n)
 {
+    if (opts.ex == 2) {
+        if (!tcstream::eligible(p) || n < 1) return 0;
+        out[0] = tcstream::kN / p->desc.channels; // one strip width
+        return 1;
+    }
     if (opts.ex > 0) return xstream::widths(p, opts, out, n);
     Bands b;
     if (bands_of(p, b) != RS_OK) return 0;
@@ -286,12 +291,22 @@ int widths(rs_plan *p, const Opts &opts, int *out, int n)
 rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
 {
     p->stream_ok = 0;
+    if (opts.ex == 2) return tcstream::setup(p, s, opts);
     // the exact-window form where it applies (or when asked for)
     if (opts.ex != 0) {
         const rs_status xs = xstream::setup(p, s, opts);
         if (xs == RS_OK || opts.ex > 0) return xs;
+        // then the tensor-core downscale where it applies and the horizontal
+        // windows are wide (12 or more taps: it was measured slower than the
+        // band kernels at x0.6 Lanczos-3, 10 taps, and 1.6-2.8x faster at
+        // x0.3 and x0.125)
+        if (p->gx.t_eff >= 12) {
+            const rs_status ts = tcstream::setup(p, s, opts);
+            if (ts != RS_ERR_UNSUPPORTED) return ts;
+        }
     }
     p->x_on = 0;
+    p->tcs_on = 0;
     Bands bd;
     const rs_status bst = bands_of(p, bd);
     if (bst != RS_OK) return bst;
@@ -387,6 +402,7 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
 
 rs_status rebuild(rs_plan *p, cudaStream_t s)
 {
+    if (p->tcs_on) return tcstream::rebuild(p, s);
     if (p->x_on) return RS_OK; // the exact-window kernel reads the weight tables directly
     // both bands in one launch of the band kernel:
     //  * vertical: groups of 4 rows, every weight twice -> per tap (w0, w0, .., w3, w3);
@@ -424,6 +440,7 @@ rs_status rebuild(rs_plan *p, cudaStream_t s)
 
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s)
 {
+    if (p->tcs_on) return tcstream::launch(p, d_in, d_out, s);
     const rs_plan_desc &d = p->desc;
     if (p->stmap_ptr != d_in) {
         cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};

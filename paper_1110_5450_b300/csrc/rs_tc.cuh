@@ -32,6 +32,18 @@ __host__ __device__ inline uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
+// The same for a K-major operand in the 128-byte swizzled layout (rows of 128
+// bytes of K, 16-byte chunks permuted by row % 8 as a TMA copy with
+// CU_TENSOR_MAP_SWIZZLE_128B lands them, from a 1024-byte aligned base): sbo =
+// distance between groups of 8 rows; the leading offset is unused; advancing
+// K within a row adds to the start address.
+__host__ __device__ inline uint64_t smem_desc_sw128(uint32_t addr, uint32_t sbo)
+{
+    uint64_t d = smem_desc(addr, 16u, sbo);
+    d |= uint64_t(2) << 61; // swizzling mode: 128-byte
+    return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulators, A and B of the
 // same 16-bit type (bf16 = true: BF16, else FP16), major-ness of A and B
 // (1 = MN-major), shape M x N.

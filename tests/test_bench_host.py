@@ -20,5 +20,13 @@ def test_traffic_only_for_the_measured_sources(monkeypatch):
         rec = json.load(f)
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["source_hash"])
     assert bench.recorded_traffic() == float(rec["dram_bytes_per_launch"])
+    assert bench.recorded_traffic(rec["form"]) == float(rec["dram_bytes_per_launch"])
+    other = list(rec["form"])
+    other[4] += 4        # another strip width: not the measured configuration
+    assert bench.recorded_traffic(other) is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.recorded_traffic() is None
+
+
+def test_traffic_sources_exist():
+    assert len(bench.kernel_source_hash()) == 16

@@ -146,7 +146,7 @@ def test_form_is_reported_and_refused_cleanly(rs):
     assert e.value.status == rs.RS_ERR_UNSUPPORTED
     assert rs.rs_plan_get_info(p.handle).path == before
     with pytest.raises(rs.RSError) as e:      # malformed
-        rs.rs_plan_set_stream_form(p.handle, 3, 0, 0, 0, 0, s)
+        rs.rs_plan_set_stream_form(p.handle, 4, 0, 0, 0, 0, s)
     assert e.value.status == rs.RS_ERR_INVALID_ARG
     with pytest.raises(rs.RSError) as e:
         rs.rs_plan_set_stream_form(p.handle, 1, 0, 0, 18, 0, s)  # width not a multiple of 4

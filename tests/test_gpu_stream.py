@@ -220,14 +220,17 @@ def test_stream_parity_16bit(rs, dt, shape, kernel, param, boundary, C):
     img = synth.uniform(H, W, C, seed=(H * 37 + W * 11 + C) & 0xffff)
     t, exact = quantise(img, dt)
     want = oracle.resample(exact, OH, OW, kernel, boundary, param=param)
-    try:
-        got, info = run_gpu(t, OH, OW, kernel, boundary, param, rs.RS_FORCE_STREAM)
-    except RuntimeError as e:
-        assert "unsupported" in str(e) and OH < H, e
-        return
-    assert info.path == 3
-    err = np.abs(got - want).max()
-    assert err <= TOL[dt], (err, info.tile_w)
+    # forced streaming (a wide 16-bit downscale takes the tensor-core form, path
+    # 5), and the SIMT streaming kernels alone (RS_FORCE_SIMT)
+    for flags in (rs.RS_FORCE_STREAM, rs.RS_FORCE_STREAM | rs.RS_FORCE_SIMT):
+        try:
+            got, info = run_gpu(t, OH, OW, kernel, boundary, param, flags)
+        except RuntimeError as e:
+            assert "unsupported" in str(e) and OH < H, e
+            continue
+        assert info.path == 3 or (info.path == 5 and not flags & rs.RS_FORCE_SIMT and OH < H), info.path
+        err = np.abs(got - want).max()
+        assert err <= TOL[dt], (err, info.tile_w, flags)
 
 
 @pytest.mark.parametrize("dt", ["bf16", "f16"])
@@ -251,23 +254,30 @@ def test_stream_is_default_for_16bit_upscale(rs):
         p = rs.Plan(4096, 4096, 3, scale=1.37, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt)
         assert p.path == "stream", (dt, p.path)
         p.close()
-        # the wide antialiasing downscale keeps its tensor-core tiles unless forced
+        # the wide antialiasing downscale takes the tensor-core streaming form,
+        # forced streaming too; without the tensor cores the SIMT streaming kernel
         p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt)
-        assert p.path == "tcgen05", (dt, p.path)
+        assert p.path == "tcstream", (dt, p.path)
         p.close()
         p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt,
                     flags=rs.RS_FORCE_STREAM)
+        assert p.path == "tcstream", (dt, p.path)
+        p.close()
+        p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt,
+                    flags=rs.RS_FORCE_STREAM | rs.RS_FORCE_SIMT)
         assert p.path == "stream", (dt, p.path)
         p.close()
 
 
 @pytest.mark.parametrize("dt", ["bf16", "f16"])
-@pytest.mark.parametrize("scale,out", [(1.37, 5612), (0.3, 1229)])
-def test_stream_16bit_full_size_sampled_rows(rs, dt, scale, out):
-    """4096x4096x3 16-bit on the streaming kernel: sampled rows against the oracle."""
+@pytest.mark.parametrize("scale,out,simt", [(1.37, 5612, 0), (0.3, 1229, 0), (0.3, 1229, 1)])
+def test_stream_16bit_full_size_sampled_rows(rs, dt, scale, out, simt):
+    """4096x4096x3 16-bit on the streaming kernels (x0.3: the tensor-core form,
+    and the SIMT band kernel): sampled rows against the oracle."""
     t, exact = quantise(synth.sinusoids(4096, 4096, 3, seed=synth.SEED_C2), dt)
-    got, info = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_STREAM, scale=scale)
-    assert info.path == 3 and (info.out_h, info.out_w) == (out, out)
+    flags = rs.RS_FORCE_STREAM | (rs.RS_FORCE_SIMT if simt else 0)
+    got, info = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, flags, scale=scale)
+    assert info.path == (5 if scale < 1 and not simt else 3) and (info.out_h, info.out_w) == (out, out)
     g = np.random.default_rng(7)
     rows = sorted(set([0, 1, out // 2, out - 2, out - 1]) | set(int(r) for r in g.integers(0, out, 8)))
     err = 0.0

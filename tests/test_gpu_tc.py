@@ -111,7 +111,12 @@ def test_tc_chosen_automatically_for_wide_16bit(rs):
 
     for dt in (torch.bfloat16, torch.float16):
         for s in (0.3, 0.125):
+            # the tensor-core streaming downscale; its fused tiles when forced
             p = rs.Plan(4096, 4096, 3, scale=s, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt)
+            assert p.path == "tcstream", (dt, s, p.path)
+            p.close()
+            p = rs.Plan(4096, 4096, 3, scale=s, kernel="lanczos", param=3.0, boundary="mirror", dtype=dt,
+                        flags=rs.RS_FORCE_TC)
             assert p.path == "tcgen05", (dt, s, p.path)
             p.close()
         # narrow: the SIMT streaming kernel
@@ -161,7 +166,7 @@ def test_tc_matches_simt_path(rs, dt):
     t, exact = quantise(img, dt)
     a, ia = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, 0, scale=0.3)
     b, ib = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_SIMT | rs.RS_NO_STREAM, scale=0.3)
-    assert (ia.path, ib.path) == (2, 0)
+    assert (ia.path, ib.path) == (5, 0)
     assert np.abs(a - b).max() <= TOL[dt]
     want = oracle.resample(exact, ia.out_h, ia.out_w, "lanczos", "mirror", param=3.0)
     assert np.abs(a - want).max() <= TOL[dt]
@@ -184,7 +189,7 @@ def test_tc_autotune_keeps_parity(rs, tmp_path, forced):
     for _ in range(2):
         p = rs.Plan(600, 800, 3, scale=0.125, kernel="lanczos", param=3.0, boundary="mirror",
                     dtype=torch.bfloat16, flags=flags)
-        assert p.path == "tcgen05"
+        assert p.path == ("tcgen05" if forced else "tcstream")
         out = torch.empty((p.info.out_h, p.info.out_w, 3), dtype=torch.bfloat16, device="cuda")
         p.autotune(x, out, cache_path=cache)
         paths.append(p.path)
