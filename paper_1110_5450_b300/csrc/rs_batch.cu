@@ -1,9 +1,12 @@
 // rs_batch.cu -- batches of uneven images in one persistent fused launch.
 //
-// Images of at least kStreamMinOut output pixels that the row-streaming kernel
-// takes (TMA-planned batches) leave the tile list and run on it, one launch
-// each after the persistent kernel: on large upscales it is 2-4x faster than
-// the tile kernel, and a launch that large fills the GPU by itself.
+// Images of at least kStreamMinOut output pixels that the row-streaming
+// kernels take (TMA-planned batches) leave the tile list and run on them,
+// beside the persistent kernel: on large upscales they are 2-4x faster than
+// the tile kernel.  The pipelined kernel's images go into one multi-image
+// launch per kernel kind (their CTAs in one grid, each image's parameters and
+// tensor map read from device arrays); the band kernels' images run one launch
+// each.
 //
 // Each image gets an ordinary plan (exact taps, FP64 weight tables); the batch
 // then re-plans every image's fused configuration under one launch-wide
@@ -29,8 +32,28 @@ using namespace rs;
 constexpr int64_t kStreamMinOut = int64_t(1) << 20;
 constexpr int kAux = 4; // side streams the streamed images are spread over
 
+// Streamed images on one multi-image pipelined kernel (xstream_multi_kernel):
+// one launch over all their CTAs.  dev holds [Params][tensor maps][CTA
+// offsets]; each run stages them in host[k] (pinned) and copies them up on the
+// group's side stream before the launch.
+struct MultiGroup {
+    const void *fn = nullptr;
+    int block = 0;
+    size_t smem = 0;
+    int total = 0; // CTAs
+    int aux = 0;   // side stream
+    std::vector<int> imgs;
+    std::vector<int32_t> off;
+    size_t o_maps = 0, o_off = 0, bytes = 0;
+    DeviceBuf dev;
+    unsigned char *host[2] = {nullptr, nullptr};
+    std::vector<const void *> st_in[2];
+    std::vector<void *> st_out[2];
+};
+
 struct rs_batch {
     std::vector<rs_plan *> plans;
+    std::vector<MultiGroup> groups; // streamed upscales, one launch per kind
     std::vector<char> streamed; // image i runs on the row-streaming kernel
     int n_streamed = 0;
     std::vector<int> stream_order; // streamed images, largest output first
@@ -70,6 +93,9 @@ struct rs_batch {
             if (aux[k]) cudaStreamDestroy(aux[k]);
         }
         if (fork) cudaEventDestroy(fork);
+        for (MultiGroup &g : groups)
+            for (int k = 0; k < 2; ++k)
+                if (g.host[k]) cudaFreeHost(g.host[k]);
         for (rs_plan *p : plans) rs_destroy(p);
     }
 };
@@ -324,7 +350,8 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
         if (b->use_tma && p->stream_ok && int64_t(p->gy.n_out) * p->gx.n_out >= kStreamMinOut) {
             b->streamed[i] = 1;
             ++b->n_streamed;
-            p->sp.err = static_cast<int *>(b->derr.p); // one error word for the whole batch
+            // one error word for the whole batch
+            p->sp.err = p->xp.err = p->tcp.err = static_cast<int *>(b->derr.p);
             b->stream_order.push_back(i);
         }
     }
@@ -332,6 +359,55 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
         return int64_t(b->plans[x]->gy.n_out) * b->plans[x]->gx.n_out >
                int64_t(b->plans[y]->gy.n_out) * b->plans[y]->gx.n_out;
     });
+    // the streamed upscales on the pipelined kernel: one multi-image launch per
+    // (kernel, block size), their CTAs in order of the images (largest first)
+    {
+        std::vector<int> rest;
+        for (const int i : b->stream_order) {
+            rs_plan *p = b->plans[i];
+            const void *fn = xstream::multi_kernel(p);
+            if (!fn) {
+                rest.push_back(i);
+                continue;
+            }
+            MultiGroup *g = nullptr;
+            for (MultiGroup &h : b->groups)
+                if (h.fn == fn && h.block == p->s_block) g = &h;
+            if (!g) {
+                b->groups.emplace_back();
+                g = &b->groups.back();
+                g->fn = fn;
+                g->block = p->s_block;
+                g->off.push_back(0);
+            }
+            g->imgs.push_back(i);
+            g->smem = std::max(g->smem, p->s_smem);
+            g->total += p->s_grid;
+            g->off.push_back(g->total);
+        }
+        b->stream_order.swap(rest);
+        for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+            MultiGroup &g = b->groups[gi];
+            const size_t m = g.imgs.size();
+            g.aux = int(gi % kAux);
+            g.o_maps = (sizeof(xstream::Params) * m + 127) / 128 * 128;
+            g.o_off = g.o_maps + sizeof(CUtensorMap) * m;
+            g.bytes = g.o_off + sizeof(int32_t) * (m + 1);
+            if (occupancy(g.fn, g.block, g.smem) < 1) {
+                delete b;
+                return fail(RS_ERR_UNSUPPORTED, "batch: multi-image streaming kernel does not fit an SM");
+            }
+            e = cudaMalloc(&g.dev.p, g.bytes);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                e = cudaHostAlloc(reinterpret_cast<void **>(&g.host[k]), g.bytes, cudaHostAllocDefault);
+                if (e == cudaSuccess) {
+                    std::memcpy(g.host[k] + g.o_off, g.off.data(), sizeof(int32_t) * (m + 1));
+                    g.st_in[k].assign(m, nullptr);
+                    g.st_out[k].assign(m, nullptr);
+                }
+            }
+        }
+    }
     if (e == cudaSuccess && b->n_streamed) {
         e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
         for (int k = 0; k < kAux && e == cudaSuccess; ++k) {
@@ -428,9 +504,38 @@ rs_status rs_batch_run(rs_batch *b, const void *const *d_in, void *const *d_out,
     e = cudaGraphLaunch(b->exec[k], stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch: graph launch");
     if (b->n_streamed) {
+        for (MultiGroup &g : b->groups) {
+            const size_t m = g.imgs.size();
+            xstream::Params *hp = reinterpret_cast<xstream::Params *>(g.host[k]);
+            CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(g.host[k] + g.o_maps);
+            for (size_t j = 0; j < m; ++j) {
+                const int i = g.imgs[j];
+                if (g.st_in[k][j] == d_in[i] && g.st_out[k][j] == d_out[i]) continue;
+                xstream::Params xp = b->plans[i]->xp;
+                xp.in = d_in[i];
+                xp.out = d_out[i];
+                xp.err = static_cast<int *>(b->derr.p);
+                hp[j] = xp;
+                const rs_status st = stream::encode_input_map(b->plans[i], d_in[i], &hm[j]);
+                if (st != RS_OK) return st;
+                g.st_in[k][j] = d_in[i];
+                g.st_out[k][j] = d_out[i];
+            }
+            cudaStream_t as = b->aux[g.aux];
+            e = cudaMemcpyAsync(g.dev.p, g.host[k], g.bytes, cudaMemcpyHostToDevice, as);
+            xstream::Multi mu;
+            mu.ps = static_cast<const xstream::Params *>(g.dev.p);
+            mu.maps = reinterpret_cast<const CUtensorMap *>(static_cast<char *>(g.dev.p) + g.o_maps);
+            mu.cta_off = reinterpret_cast<const int32_t *>(static_cast<char *>(g.dev.p) + g.o_off);
+            mu.n = int32_t(m);
+            void *args[1] = {&mu};
+            if (e == cudaSuccess) e = cudaLaunchKernel(g.fn, dim3(g.total), dim3(g.block), args, g.smem, as);
+            if (e != cudaSuccess) return cuda_fail(e, "batch: multi-image streaming launch");
+        }
         for (size_t j = 0; j < b->stream_order.size(); ++j) {
             const int i = b->stream_order[j];
-            const rs_status st = stream::launch(b->plans[i], d_in[i], d_out[i], b->aux[j % kAux]);
+            const rs_status st =
+                stream::launch(b->plans[i], d_in[i], d_out[i], b->aux[(j + b->groups.size()) % kAux]);
             if (st != RS_OK) return st;
         }
         for (int a = 0; a < kAux && e == cudaSuccess; ++a) {

@@ -238,6 +238,8 @@ int widths(rs_plan *p, const Opts &o, int *out, int n);
 // Rebuilds its band tables from the plan's weight tables (after a recompute).
 rs_status rebuild(rs_plan *p, cudaStream_t s);
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
+// The input tensor map of a band or pipelined streaming configuration for d_in.
+rs_status encode_input_map(const rs_plan *p, const void *d_in, CUtensorMap *map);
 // Row-range counts the configuration searches model (ascending).
 std::vector<int> range_counts(int n_strips, int64_t slots, int max_nr);
 // Loads every band-kernel instantiation of `dtype` (lazy module loading
@@ -267,6 +269,9 @@ void preload(int dtype);
 namespace xstream {
 // As stream::preload, for the pipelined kernel.
 void preload(int dtype);
+// The multi-image variant (xstream_multi_kernel) of the plan's configured
+// pipelined kernel, or nullptr.
+const void *multi_kernel(const rs_plan *p);
 // Whether the plan can run the pipelined kernel (FP32/FP16/BF16, 1 or 3
 // channels, a 16-byte row pitch, 4 or 6 taps per output on both axes, window
 // starts that advance by 0 or 1 per output: an upscale or scale 1).

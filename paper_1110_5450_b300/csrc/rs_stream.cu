@@ -438,23 +438,30 @@ rs_status rebuild(rs_plan *p, cudaStream_t s)
     return RS_OK;
 }
 
+rs_status encode_input_map(const rs_plan *p, const void *d_in, CUtensorMap *map)
+{
+    const rs_plan_desc &d = p->desc;
+    cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};
+    const int es = dt_size(d.in_dtype);
+    cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * es)};
+    cuuint32_t box[2] = {cuuint32_t(p->x_on ? p->xp.P : p->sp.P), cuuint32_t(kRB)};
+    cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType ty = d.in_dtype == RS_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : d.in_dtype == RS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = encode_fn()(map, ty, 2, const_cast<void *>(d_in), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(RS_ERR_CUDA, "stream tensor map encoding failed");
+    return RS_OK;
+}
+
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s)
 {
     if (p->tcs_on) return tcstream::launch(p, d_in, d_out, s);
-    const rs_plan_desc &d = p->desc;
     if (p->stmap_ptr != d_in) {
-        cuuint64_t dims[2] = {cuuint64_t(p->gx.n_in * d.channels), cuuint64_t(p->gy.n_in)};
-        const int es = dt_size(d.in_dtype);
-        cuuint64_t strides[1] = {cuuint64_t(d.in_row_stride * es)};
-        cuuint32_t box[2] = {cuuint32_t(p->x_on ? p->xp.P : p->sp.P), cuuint32_t(kRB)};
-        cuuint32_t estr[2] = {1, 1};
-        const CUtensorMapDataType ty = d.in_dtype == RS_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                       : d.in_dtype == RS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-        CUresult r = encode_fn()(&p->stmap, ty, 2, const_cast<void *>(d_in), dims,
-                                 strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(RS_ERR_CUDA, "stream tensor map encoding failed");
+        const rs_status st = encode_input_map(p, d_in, &p->stmap);
+        if (st != RS_OK) return st;
         p->stmap_ptr = d_in;
     }
     Params sp = p->sp;

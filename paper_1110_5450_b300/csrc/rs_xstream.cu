@@ -37,6 +37,13 @@ void preload(int dtype)
                     occupancy(fn, 32 * (big ? kMaxWarps : kSmallWarps), 0);
 }
 
+const void *multi_kernel(const rs_plan *p)
+{
+    if (!p->x_on) return nullptr;
+    const int big = p->s_block > 32 * kSmallWarps ? 1 : 0;
+    return kernel_for(p->desc.in_dtype, p->desc.channels, int(p->gx.t_eff), 2 + big);
+}
+
 namespace {
 
 // Staged pitch >= n samples: whole 16-byte words, odd in 16-byte words (lanes

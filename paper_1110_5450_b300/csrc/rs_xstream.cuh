@@ -247,12 +247,21 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
     return __all_sync(0xffffffffu, ok);
 }
 
-// BIG = 0: up to kSmallWarps warps, two CTAs per SM (at most 85 registers a
-// thread); BIG = 1: up to kMaxWarps warps, one CTA per SM.
+// Several images in one launch (a batch): CTA b belongs to image i with
+// cta_off[i] <= b < cta_off[i + 1] and takes that image's CTA b - cta_off[i];
+// ps and maps hold each image's parameters and 64-byte aligned tensor map.
+struct Multi {
+    const Params *ps;
+    const CUtensorMap *maps;
+    const int32_t *cta_off; // [n + 1]
+    int32_t n;
+};
+
+// The work of one CTA: CTA `bid` of the image that `tmap` and `p` describe.
 template <typename T, int C, int TAPS, int BIG>
-__global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ? 1 : 2)
-    xstream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+__device__ __forceinline__ void xstream_cta(const CUtensorMap *tmap_ptr, const Params &p, int bid)
 {
+    const CUtensorMap &tmap = *tmap_ptr;
     constexpr int HB = TAPS + 3; // band width
     constexpr int GB = kG * HB;  // band weights per group
     extern __shared__ unsigned char smem_raw[];
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ?
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int HW = p.HW, VW = p.VW;
-    const int strip = int(blockIdx.x) % p.n_strips, range = int(blockIdx.x) / p.n_strips;
+    const int strip = bid % p.n_strips, range = bid / p.n_strips;
     const int p0 = range * p.gpr;
     const int p1 = min(p.groups_y, p0 + p.gpr);
     if (p0 >= p1) return;
@@ -549,12 +558,43 @@ __global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ?
     }
 }
 
+// BIG = 0: up to kSmallWarps warps, two CTAs per SM (at most 85 registers a
+// thread); BIG = 1: up to kMaxWarps warps, one CTA per SM.
+template <typename T, int C, int TAPS, int BIG>
+__global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ? 1 : 2)
+    xstream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+{
+    xstream_cta<T, C, TAPS, BIG>(&tmap, p, int(blockIdx.x));
+}
+
+// The same kernel over the CTAs of several images (one launch for a batch's
+// streamed upscales of one kind).
+template <typename T, int C, int TAPS, int BIG>
+__global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ? 1 : 2)
+    xstream_multi_kernel(const __grid_constant__ Multi m)
+{
+    const int b = int(blockIdx.x);
+    int lo = 0, hi = m.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(m.cta_off + mid) <= b)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const Params p = m.ps[lo];
+    xstream_cta<T, C, TAPS, BIG>(m.maps + lo, p, b - __ldg(m.cta_off + lo));
+}
+
 // Instantiated kernels: storage type x channels x taps per output x the
-// launch-bounds variant (big: more than kSmallWarps warps).
+// variant (big = 0 / 1: one image, up to kSmallWarps / kMaxWarps warps; 2 / 3:
+// the multi-image kernel with the same launch bounds).
 template <typename T, int C, int TAPS> const void *kernel_big(int big)
 {
-    return big ? reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 1>)
-               : reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 0>);
+    return big == 1   ? reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 1>)
+           : big == 0 ? reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 0>)
+           : big == 3 ? reinterpret_cast<const void *>(&xstream_multi_kernel<T, C, TAPS, 1>)
+                      : reinterpret_cast<const void *>(&xstream_multi_kernel<T, C, TAPS, 0>);
 }
 template <typename T> const void *kernel_table(int C, int taps, int big)
 {
