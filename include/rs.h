@@ -380,6 +380,13 @@ typedef struct {
 
 RS_API rs_status rs_batch_get_info(const rs_batch *batch, rs_batch_info *info);
 
+/* The kernel path image `index` runs on in this batch: 0 the persistent tile
+ * kernel, 3 a row-streaming kernel (the band kernels one launch per image, the
+ * pipelined kernel in a multi-image launch), 5 the tensor-core streaming
+ * downscale; the streamed images run their plan's untuned streaming form.
+ * RS_ERR_INVALID_ARG for a bad index. */
+RS_API rs_status rs_batch_image_path(const rs_batch *batch, int32_t index, int32_t *path);
+
 /* Frees the batch after waiting for its work.  NULL is accepted. */
 RS_API rs_status rs_batch_destroy(rs_batch *batch);
 

@@ -168,6 +168,8 @@ _lib.rs_batch_autotune.restype = ctypes.c_int
 _lib.rs_batch_autotune.argtypes = [_vp, _vpp, _vpp, _vp, ctypes.c_char_p]
 _lib.rs_batch_get_info.restype = ctypes.c_int
 _lib.rs_batch_get_info.argtypes = [_vp, ctypes.POINTER(rs_batch_info)]
+_lib.rs_batch_image_path.restype = ctypes.c_int
+_lib.rs_batch_image_path.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
 _lib.rs_batch_destroy.restype = ctypes.c_int
 _lib.rs_batch_destroy.argtypes = [_vp]
 _lib.rs_warp.restype = ctypes.c_int
@@ -199,7 +201,7 @@ _lib.rs_server_destroy.argtypes = [_vp]
 EXPORTS = ["rs_desc_out_size", "rs_plan_create", "rs_resample", "rs_plan_recompute", "rs_destroy", "rs_plan_get_info",
            "rs_plan_get_tables", "rs_plan_check", "rs_status_string", "rs_last_error", "rs_version",
            "rs_resample_noalloc", "rs_plan_autotune", "rs_batch_create", "rs_batch_run",
-           "rs_batch_autotune", "rs_batch_get_info", "rs_batch_destroy", "rs_server_create",
+           "rs_batch_autotune", "rs_batch_get_info", "rs_batch_image_path", "rs_batch_destroy", "rs_server_create",
            "rs_batch_submit", "rs_batch_poll", "rs_server_release", "rs_server_drain", "rs_server_get_stats",
            "rs_server_destroy", "rs_tc_selftest", "rs_cluster_create", "rs_cluster_run", "rs_cluster_destroy",
            "rs_warp", "rs_plan_set_stream_form", "rs_plan_get_stream_form", "rs_plan_set_weights",
@@ -343,6 +345,13 @@ def rs_batch_autotune(batch: int, d_in, d_out, stream: int = 0, cache_path=None)
     cp = None if cache_path is None else os.fsencode(cache_path)
     _check(_lib.rs_batch_autotune(_vp(batch), _ptr_array(d_in), _ptr_array(d_out), _vp(stream), cp),
            "rs_batch_autotune")
+
+
+def rs_batch_image_path(batch: int, index: int) -> int:
+    """Kernel path of one image of a batch (0 tile, 3 streaming, 5 tensor-core streaming)."""
+    v = ctypes.c_int32()
+    _check(_lib.rs_batch_image_path(_vp(batch), int(index), ctypes.byref(v)), "rs_batch_image_path")
+    return int(v.value)
 
 
 def rs_batch_get_info(batch: int) -> rs_batch_info:

@@ -650,6 +650,15 @@ rs_status rs_batch_autotune(rs_batch *b, const void *const *d_in, void *const *d
     return RS_OK;
 }
 
+rs_status rs_batch_image_path(const rs_batch *b, int32_t index, int32_t *path)
+{
+    if (!b || !path || index < 0 || index >= int32_t(b->plans.size()))
+        return fail(RS_ERR_INVALID_ARG, "batch: bad image index");
+    const rs_plan *p = b->plans[size_t(index)];
+    *path = b->streamed[size_t(index)] ? (p->tcs_on ? 5 : 3) : 0;
+    return RS_OK;
+}
+
 rs_status rs_batch_get_info(const rs_batch *b, rs_batch_info *info)
 {
     if (!b || !info) return fail(RS_ERR_INVALID_ARG, "NULL argument");

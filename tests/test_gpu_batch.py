@@ -74,10 +74,14 @@ def test_batch_matches_oracle_and_single_path(rs, dt, C, aligned):
         want = oracle.resample(exact[i], got.shape[0], got.shape[1], sp["kernel"], sp["boundary"],
                                param=sp["param"])
         assert np.abs(got - want).max() <= TOL[dt], (i, sp)
-        # alone, through the plan path (on the SIMT kernel, as batches), with the same pitch
+        # alone, through the plan path, on the kernel the batch ran it on (the
+        # tile kernel, or a streaming kernel in its untuned form), same pitch
+        path = rs.rs_batch_image_path(b.handle, i)
+        flags = {0: rs.RS_FORCE_SIMT | rs.RS_NO_STREAM, 3: rs.RS_FORCE_STREAM | rs.RS_FORCE_SIMT,
+                 5: rs.RS_FORCE_STREAM}[path]
         d = rs.make_desc(sp["in_h"], sp["in_w"], C, got.shape[0], got.shape[1], kernel=sp["kernel"],
                          param=sp["param"], boundary=sp["boundary"], dtype=ins[i].dtype,
-                         in_row_stride=pitches[i], flags=rs.RS_FORCE_SIMT | rs.RS_NO_STREAM)
+                         in_row_stride=pitches[i], flags=flags)
         h = rs.rs_plan_create(d, 0)
         alone = torch.empty_like(outs[i])
         rs.rs_resample(h, ins[i].data_ptr(), alone.data_ptr(), 0)
