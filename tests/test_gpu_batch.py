@@ -88,6 +88,9 @@ def test_batch_matches_oracle_and_single_path(rs, dt, C, aligned):
         torch.cuda.synchronize()
         rs.rs_destroy(h)
         assert torch.equal(alone, outs[i]), i
+    with pytest.raises(rs.RSError) as e:
+        rs.rs_batch_image_path(b.handle, len(specs))
+    assert e.value.status == rs.RS_ERR_INVALID_ARG
     # replay with other output buffers (the graph re-stages the pointers)
     outs2 = [torch.zeros_like(o) for o in outs]
     b(ins, outs2)
