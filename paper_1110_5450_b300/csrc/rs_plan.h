@@ -261,7 +261,7 @@ rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o);
 rs_status rebuild(rs_plan *p, cudaStream_t s);
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 // Bytes of its device tables at most, for external placement (a serving arena).
-size_t space_bound(const AxisGeom &gx, int C);
+size_t space_bound(const AxisGeom &gx, const AxisGeom &gy, int C);
 // As stream::preload.
 void preload(int dtype);
 } // namespace tcstream

@@ -227,7 +227,7 @@ size_t stream_space(const AxisGeom &gy, const AxisGeom &gx, int C)
     const size_t gxn = size_t((gx.n_out + 3) / 4), gyn = size_t((gy.n_out + 3) / 4);
     const size_t band = up256(gxn * 4) + up256(gxn * 40 * 4 * 4) + up256((gyn + 4) * 4) + up256(gyn * 32 * 8 * 4);
     const size_t desc = up256(gxn * 4) + up256((gyn + 8) * 4);
-    const size_t tcs = gx.n_out < gx.n_in ? tcstream::space_bound(gx, C) : 0;
+    const size_t tcs = gx.n_out < gx.n_in && gy.n_out < gy.n_in ? tcstream::space_bound(gx, gy, C) : 0;
     return std::max(std::max(band, desc), tcs) + 256;
 }
 

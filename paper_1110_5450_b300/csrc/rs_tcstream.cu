@@ -50,8 +50,34 @@ __global__ void build_b_kernel(const int32_t *start_x, const float *wx, int t_x,
     }
 }
 
+// The vertical band of every row group q (output rows 4 q .. 4 q + 3): at
+// union row u (input row sy[4 q] + u) the 4 rows' window weights, zero outside
+// a row's own window and past the image's last row; and per group its first
+// union row and union rows.  Block q fills group q.
+__global__ void build_vband_kernel(const int32_t *sy, const float *wy, int t_y, int out_h, int gpr, int Uv,
+                                   float4 *vband, int2 *vinfo)
+{
+    const int q = blockIdx.x;
+    if (q >= gpr) return;
+    const int i0 = q * kVG, n = min(kVG, out_h - i0);
+    const int s0 = sy[i0];
+    int st[kVG];
+#pragma unroll
+    for (int r = 0; r < kVG; ++r) st[r] = r < n ? sy[i0 + r] - s0 : -1;
+    for (int u = threadIdx.x; u < Uv; u += blockDim.x) {
+        float w[kVG];
+#pragma unroll
+        for (int r = 0; r < kVG; ++r) {
+            const int t = u - st[r];
+            w[r] = (st[r] >= 0 && t >= 0 && t < t_y) ? wy[size_t(i0 + r) * t_y + t] : 0.f;
+        }
+        vband[size_t(q) * Uv + u] = make_float4(w[0], w[1], w[2], w[3]);
+    }
+    if (threadIdx.x == 0) vinfo[q] = make_int2(s0, st[n - 1] + t_y);
+}
+
 struct Geometry {
-    int C = 0, NP = 0, n_strips = 0, Kc = 0, Ty = 0, Uv = 0;
+    int C = 0, NP = 0, n_strips = 0, Kc = 0, Ty = 0, Uv = 0, gpr = 0;
     std::vector<int32_t> g0;
 };
 
@@ -85,10 +111,11 @@ rs_status geometry(const rs_plan *p, Geometry &g)
         need = std::max(need, hi * g.C - 8 * gz);
     }
     g.Kc = (need + kKC - 1) / kKC * kKC;
-    // rows spanned by kVG consecutive vertical windows (a vertical warp's band)
+    // rows spanned by a row group's windows (kVG output rows from a multiple of kVG)
     const std::vector<int32_t> &sy = p->host_start_y;
+    g.gpr = int((sy.size() + kVG - 1) / kVG);
     g.Uv = 0;
-    for (size_t i = 0; i < sy.size(); ++i) {
+    for (size_t i = 0; i < sy.size(); i += kVG) {
         const size_t j = std::min(sy.size() - 1, i + kVG - 1);
         g.Uv = std::max(g.Uv, int(sy[j] - sy[i]) + g.Ty);
     }
@@ -104,14 +131,19 @@ bool eligible(const rs_plan *p)
     return geometry(p, g) == RS_OK;
 }
 
-size_t space_bound(const AxisGeom &gx, int C)
+size_t space_bound(const AxisGeom &gx, const AxisGeom &gy, int C)
 {
     const int64_t np = kN / C;
     const int64_t n_strips = (gx.n_out + np - 1) / np;
     // a strip's windows span at most (np - 1) n_in / n_out + 1 starts plus t_eff inputs
     const int64_t span = ((np - 1) * gx.n_in + gx.n_out - 1) / gx.n_out + 1 + gx.t_eff;
     const int64_t kc = (span * C + 8 + kKC - 1) / kKC * kKC;
-    return size_t(n_strips) * 2 * b_bytes(int(kc)) + ((size_t(n_strips) * 4 + 255) & ~size_t(255)) + 512;
+    // a row group's windows span at most 3 n_in / n_out + 1 starts plus t_eff rows
+    const int64_t gpr = (gy.n_out + kVG - 1) / kVG;
+    const int64_t uv = std::min<int64_t>(kMaxTy, (3 * gy.n_in + gy.n_out - 1) / gy.n_out + 1 + gy.t_eff);
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return size_t(n_strips) * 2 * b_bytes(int(kc)) + up(size_t(n_strips) * 4) + up(size_t(gpr * uv) * 16) +
+           up(size_t(gpr) * 8) + 512;
 }
 
 void preload(int dtype)
@@ -148,6 +180,8 @@ rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
     Carver cv;
     const size_t o_b = cv.take(size_t(g.n_strips) * 2 * b_bytes(g.Kc));
     const size_t o_g = cv.take(size_t(g.n_strips) * 4);
+    const size_t o_vb = cv.take(size_t(g.gpr) * g.Uv * 16);
+    const size_t o_vi = cv.take(size_t(g.gpr) * 8);
     char *base = nullptr;
     cudaError_t e = cudaSuccess;
     if (p->ext_base) {
@@ -179,7 +213,9 @@ rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
     tp.bmat = reinterpret_cast<const unsigned char *>(base + o_b);
     tp.g0 = reinterpret_cast<const int32_t *>(base + o_g);
     tp.sy = p->ty.start;
-    tp.wy = static_cast<const float *>(p->ty.wwork);
+    tp.vband = reinterpret_cast<const float4 *>(base + o_vb);
+    tp.vinfo = reinterpret_cast<const int2 *>(base + o_vi);
+    tp.gpr = g.gpr;
     tp.Kc = g.Kc;
     tp.NP = g.NP;
     tp.n_strips = g.n_strips;
@@ -189,10 +225,10 @@ rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
     tp.NA = NA;
     tp.VW = VW;
     tp.pf = o.ex == 2 && o.pf ? 2 * NA : 0;
-    const int64_t total = int64_t(g.n_strips) * p->gy.n_out;
-    // a CTA per SM; runs of at least 16 output rows (each run re-reads its
+    const int64_t total = int64_t(g.n_strips) * g.gpr;
+    // a CTA per SM; runs of at least 4 row groups (each run re-reads its
     // windows' first rows)
-    tp.per_cta = std::max<int64_t>((total + p->num_sms - 1) / p->num_sms, std::min<int64_t>(16, p->gy.n_out));
+    tp.per_cta = std::max<int64_t>((total + p->num_sms - 1) / p->num_sms, std::min<int64_t>(4, g.gpr));
     tp.err = p->d_err;
     p->tcs_on = 1;
     p->x_on = 0;
@@ -229,6 +265,9 @@ rs_status rebuild(rs_plan *p, cudaStream_t s)
         build_b_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(sx, wx, p->gx.t_eff, tp.out_w, tp.C, tp.NP, tp.Kc, tp.g0, bm);
     else
         build_b_kernel<__half><<<grid, 128, 0, s>>>(sx, wx, p->gx.t_eff, tp.out_w, tp.C, tp.NP, tp.Kc, tp.g0, bm);
+    build_vband_kernel<<<unsigned(tp.gpr), 64, 0, s>>>(p->ty.start, static_cast<const float *>(p->ty.wwork),
+                                                       p->gy.t_eff, tp.out_h, tp.gpr, tp.Uv,
+                                                       const_cast<float4 *>(tp.vband), const_cast<int2 *>(tp.vinfo));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core weight matrix launch");
     return RS_OK;

@@ -80,16 +80,18 @@ struct Params {
     const unsigned char *bmat;  // per strip: B hi then B lo, [kN][Kc] in the canonical K-major layout
     const int32_t *g0;          // per strip: its first staged 8-sample group
     const int32_t *sy;          // [out_h] vertical window starts (the plan's table)
-    const float *wy;            // [out_h][Ty] vertical window weights (the plan's table)
+    const float4 *vband;        // [gpr][Uv] per row group: its 4 rows' weights at each union row
+    const int2 *vinfo;          // [gpr] per row group: first union row, union rows
     int32_t Kc;                 // staged samples per row, a multiple of kKC
     int32_t NP;                 // output pixels per strip (kN / C)
     int32_t n_strips;
     int32_t Ty;
-    int32_t Uv;                 // rows spanned by kVG consecutive windows at most (<= kMaxTy)
+    int32_t Uv;                 // union rows of a row group at most (<= kMaxTy)
+    int32_t gpr;                // row groups per strip: ceil(out_h / kVG)
     int32_t NS;                 // blocks in the filtered-row ring (2 or 3)
     int32_t NA, VW;
     int32_t pf;                 // chunks ahead of the copy in flight to prefetch into L2 (0: none)
-    int64_t per_cta;            // (strip, output row) positions per CTA
+    int64_t per_cta;            // (strip, row group) positions per CTA
     int *err;
 };
 
@@ -121,18 +123,21 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
     return __all_sync(0xffffffffu, ok);
 }
 
-// The positions [pos0, pos1) of a CTA as items (strip, first output row, end).
+// The positions [pos0, pos1) of a CTA, (strip, row group of kVG output rows)
+// pairs, as items (strip, first output row, end): a run of whole row groups.
 struct Item {
     int strip, i0, i1;
 };
-__device__ __forceinline__ bool next_item(int64_t &pos, int64_t pos1, int out_h, Item &it)
+__device__ __forceinline__ bool next_item(int64_t &pos, int64_t pos1, int gpr, int out_h, Item &it)
 {
     if (pos >= pos1) return false;
-    it.strip = int(pos / out_h);
-    it.i0 = int(pos - int64_t(it.strip) * out_h);
+    it.strip = int(pos / gpr);
+    const int q0 = int(pos - int64_t(it.strip) * gpr);
     const int64_t rest = pos1 - pos;
-    it.i1 = rest < int64_t(out_h - it.i0) ? it.i0 + int(rest) : out_h;
-    pos += it.i1 - it.i0;
+    const int q1 = rest < int64_t(gpr - q0) ? q0 + int(rest) : gpr;
+    it.i0 = q0 * kVG;
+    it.i1 = min(out_h, q1 * kVG);
+    pos += q1 - q0;
     return true;
 }
 
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t total = int64_t(p.n_strips) * p.out_h;
+    const int64_t total = int64_t(p.n_strips) * p.gpr;
     const int64_t pos0 = min(total, int64_t(blockIdx.x) * p.per_cta);
     const int64_t pos1 = min(total, pos0 + p.per_cta);
     const uint32_t chunk_bytes = uint32_t(kM) * kKC * 2;
@@ -208,9 +213,11 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
         if (lane == 0) {
             int64_t pos = pos0, q = 0;
             int cur = -1, nload = 0;
+            int s = 0;        // q % NA, kept by increments (no division per chunk)
+            uint32_t rnd = 0; // q / NA
             bool ok = true;
             Item it;
-            while (ok && next_item(pos, pos1, p.out_h, it)) {
+            while (ok && next_item(pos, pos1, p.gpr, p.out_h, it)) {
                 if (it.strip != cur) {
                     if (nload > 0 && !fused::wait_or_abort(bfree, uint32_t((nload - 1) & 1), abort_flag, p.err)) {
                         ok = false;
@@ -226,8 +233,7 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                 const int gz = __ldg(p.g0 + it.strip);
                 for (int b = 0; b < nblk && ok; ++b)
                     for (int c = 0; c < nchunk; ++c, ++q) {
-                        const int s = int(q % NA);
-                        if (q >= NA && !fused::wait_or_abort(&empty_a[s], uint32_t(((q / NA) - 1) & 1), abort_flag, p.err)) {
+                        if (rnd > 0 && !fused::wait_or_abort(&empty_a[s], (rnd - 1) & 1u, abort_flag, p.err)) {
                             ok = false;
                             break;
                         }
@@ -239,6 +245,10 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                             const int ahead = b * nchunk + c + p.pf;
                             const int pb = ahead / nchunk, pc = ahead - pb * nchunk;
                             if (pb < nblk) fused::tma_prefetch_2d(&tmap, 8 * gz + pc * kKC, r0 + pb * kM);
+                        }
+                        if (++s == NA) {
+                            s = 0;
+                            ++rnd;
                         }
                     }
             }
@@ -260,11 +270,13 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
             const uint32_t idesc = tc::idesc_f16(!std::is_same<T, __half>::value, false, false, kM, 2 * kN);
             const uint32_t a0 = fused::smem_addr(asm_), bw = fused::smem_addr(bsm);
             const uint32_t sbo_b = uint32_t(Kc) * 16u;
-            int64_t pos = pos0, q = 0, gb = 0;
+            int64_t pos = pos0, gb = 0;
             int cur = -1, nload = 0;
+            int s = 0;        // stage of the next chunk, kept by increments
+            uint32_t rnd = 0; // times the stage ring went round
             bool ok = true;
             Item it;
-            while (ok && next_item(pos, pos1, p.out_h, it)) {
+            while (ok && next_item(pos, pos1, p.gpr, p.out_h, it)) {
                 if (it.strip != cur) {
                     if (!fused::wait_or_abort(bfull, uint32_t(nload & 1), abort_flag, p.err)) {
                         ok = false;
@@ -284,9 +296,8 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                     tc::fence_after_sync();
                     // this warp's accumulator: columns [0, 48) hi, [48, 96) lo
                     const uint32_t dt = tmem + uint32_t((d * kChains + part) * 2 * kN);
-                    for (int c = 0; c < nchunk; ++c, ++q) {
-                        const int s = int(q % NA);
-                        if (!fused::wait_or_abort(&full_a[s], uint32_t((q / NA) & 1), abort_flag, p.err)) {
+                    for (int c = 0; c < nchunk; ++c) {
+                        if (!fused::wait_or_abort(&full_a[s], rnd & 1u, abort_flag, p.err)) {
                             ok = false;
                             break;
                         }
@@ -303,6 +314,10 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                             tc::mma_f16(dt, ad, tc::smem_desc(bw + koff, 128u, sbo_b), idesc, acc);
                         }
                         tc::mma_commit(&empty_a[s]); // the chunk's stage is free once these are done
+                        if (++s == NA) {
+                            s = 0;
+                            ++rnd;
+                        }
                     }
                     if (!ok) break;
                     tc::mma_commit(&acc_full[d]);
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                 // B stays until the run moves to another strip
                 int64_t look = pos;
                 Item nx;
-                if (ok && next_item(look, pos1, p.out_h, nx) && nx.strip != cur) tc::mma_commit(bfree);
+                if (ok && next_item(look, pos1, p.gpr, p.out_h, nx) && nx.strip != cur) tc::mma_commit(bfree);
             }
             // every MMA issued has completed before the tensor memory is released
             tc::mma_commit(&drain[part]);
@@ -320,20 +335,22 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
         // ================= accumulators -> filtered rows =================
         const int quad = warp & 3; // the tensor-memory lanes this warp may read
         int64_t pos = pos0, gb = 0;
+        int sl = 0;        // gb % NS, kept by increments
+        uint32_t rnd = 0;  // gb / NS
         bool ok = true;
         Item it;
-        while (ok && next_item(pos, pos1, p.out_h, it)) {
+        while (ok && next_item(pos, pos1, p.gpr, p.out_h, it)) {
             int r0, nblk;
             item_rows(it, r0, nblk);
             for (int b = 0; b < nblk; ++b, ++gb) {
-                const int d = int(gb & 1), sl = int(gb % NS);
+                const int d = int(gb & 1);
                 if (!warp_wait(&acc_full[d], uint32_t((gb >> 1) & 1), abort_flag, p.err)) {
                     ok = false;
                     break;
                 }
-                if (gb >= NS)
+                if (rnd > 0)
                     for (int v = 0; v < VW && ok; ++v)
-                        ok = warp_wait(&hfree[sl * kMaxVW + v], uint32_t(((gb / NS) - 1) & 1), abort_flag, p.err);
+                        ok = warp_wait(&hfree[sl * kMaxVW + v], (rnd - 1) & 1u, abort_flag, p.err);
                 if (!ok) break;
                 tc::fence_after_sync();
                 float *dst = hring + size_t(sl * kM + quad * 32 + lane) * kHP;
@@ -361,86 +378,82 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                     fused::mbar_arrive(&acc_empty[d]);
                     fused::mbar_arrive(&hfull[sl]);
                 }
+                if (++sl == NS) {
+                    sl = 0;
+                    ++rnd;
+                }
             }
         }
     } else if (warp < kFixedWarps + VW) {
         // ================= vertical pass =================
         const int v = warp - kFixedWarps;
-        int64_t pos = pos0, gbase = 0;
+        int64_t pos = pos0;
         bool ok = true;
         Item it;
         const int ring_rows = NS * kM;
-        while (ok && next_item(pos, pos1, p.out_h, it)) {
+        // ring slots of the next block to wait for (and its round) and of the
+        // next one to release, kept by increments: every block of every item is
+        // waited for and released once, in order
+        int w_sl = 0, r_sl = 0, gmod = 0;
+        uint32_t w_rnd = 0;
+        while (ok && next_item(pos, pos1, p.gpr, p.out_h, it)) {
             int r0, nblk;
             item_rows(it, r0, nblk);
             int waited = 0, released = 0;
-            auto wait_block = [&](int m) {
-                const int64_t g = gbase + m;
-                return warp_wait(&hfull[g % NS], uint32_t((g / NS) & 1), abort_flag, p.err);
+            auto wait_block = [&](int) {
+                const bool r = warp_wait(&hfull[w_sl], w_rnd & 1u, abort_flag, p.err);
+                if (++w_sl == NS) {
+                    w_sl = 0;
+                    ++w_rnd;
+                }
+                return r;
             };
-            auto release_block = [&](int m) {
+            auto release_block = [&](int) {
                 __syncwarp();
-                if (lane == 0) fused::mbar_arrive(&hfree[((gbase + m) % NS) * kMaxVW + v]);
+                if (lane == 0) fused::mbar_arrive(&hfree[r_sl * kMaxVW + v]);
+                if (++r_sl == NS) r_sl = 0;
             };
             const int x0 = it.strip * p.NP;
             const int ncols = min(kN, (p.out_w - x0) * C);
             T *orow = static_cast<T *>(p.out) + int64_t(x0) * C;
-            // The warp takes kVG = 4 consecutive output rows at a time ("a group"),
-            // group k of the item's being rows i0 + 4 (v + k VW) + r.  Their windows
-            // overlap, so the group runs over the union of its windows once, with a
-            // band of 4 weights per union row (zero outside a row's window): per
-            // union row one broadcast 16-byte weight load, one 8-byte load of the
-            // filtered row and 8 FMAs (4 rows x the lane's 2 samples: lanes 0..23
-            // own the sample pairs (2 lane, 2 lane + 1)).  The band of the group
-            // two ahead is filled while this one is summed: zeroed, then its
-            // weights copied in asynchronously (4-byte copies, one commit group per
-            // band); the window starts are loaded three groups ahead.
+            // The warp takes the item's row groups v, v + VW, ...: group g is the
+            // output rows i0 + 4 g + r, r < 4 (row group q = i0 / 4 + g of the
+            // plan's band table).  Their windows overlap, so a group runs over the
+            // union of its windows once, with the band of its 4 rows' weights at
+            // each union row (zero outside a row's own window): per union row one
+            // broadcast 16-byte weight load, one 8-byte load of the filtered row
+            // and 8 FMAs (4 rows x the lane's 2 samples: lanes 0..23 own the
+            // sample pairs (2 lane, 2 lane + 1)).  The band of the group two ahead
+            // is copied from the table while this one is summed (one 16-byte
+            // asynchronous copy per union row), and its (first union row, union
+            // rows) pair loaded a group earlier still.
             const int col = 2 * lane;
             const bool act = col < kN;
             const int Uv = p.Uv;
             float4 *bands = reinterpret_cast<float4 *>(wsm) + size_t(v) * 2 * Uv;
+            const int qb = it.i0 / kVG;
             const int ng = (it.i1 - it.i0 + kVG - 1) / kVG;
-            auto starts = [&](int g, int (&st)[kVG]) {
-#pragma unroll
-                for (int r = 0; r < kVG; ++r) {
-                    const int i = it.i0 + kVG * g + r;
-                    st[r] = (g < ng && i < it.i1) ? __ldg(p.sy + i) : -1;
-                }
-            };
-            auto fill = [&](int g, int slot, const int (&st)[kVG]) {
-                float4 *bd = bands + slot * Uv;
-                for (int u = lane; u < Uv; u += 32) bd[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                __syncwarp();
-                if (st[0] >= 0) {
-#pragma unroll
-                    for (int r = 0; r < kVG; ++r) {
-                        if (st[r] < 0) break;
-                        const int o = st[r] - st[0];
-                        const float *src = p.wy + int64_t(it.i0 + kVG * g + r) * Ty;
-                        for (int t = lane; t < Ty; t += 32) {
-                            const uint32_t dst = fused::smem_addr(reinterpret_cast<float *>(bd + o + t) + r);
-                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src + t)
-                                         : "memory");
-                        }
-                    }
+            auto fill = [&](int g, int slot) {
+                if (g < ng) {
+                    const float4 *src = p.vband + size_t(qb + g) * Uv;
+                    float4 *bd = bands + slot * Uv;
+                    for (int u = lane; u < Uv; u += 32)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(fused::smem_addr(bd + u)),
+                                     "l"(src + u)
+                                     : "memory");
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
             };
-            int sc[kVG], s1[kVG], s2[kVG];
-            starts(v, sc);
-            starts(v + VW, s1);
-            starts(v + 2 * VW, s2);
-            fill(v, 0, sc);
-            fill(v + VW, 1, s1);
+            auto info = [&](int g) { return g < ng ? __ldg(p.vinfo + qb + g) : make_int2(0, 0); };
+            int2 i_c = info(v), i_n = info(v + VW);
+            fill(v, 0);
+            fill(v + VW, 1);
             for (int k = 0, g = v; g < ng && ok; ++k, g += VW) {
                 // this group's band (the older of the two in flight) has landed
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
                 __syncwarp();
                 const float4 *bd = bands + (k & 1) * Uv;
-                int s_last = sc[0];
-#pragma unroll
-                for (int r = 1; r < kVG; ++r) s_last = sc[r] >= 0 ? sc[r] : s_last;
-                const int rs = sc[0] - r0, U = s_last + Ty - sc[0];
+                const int rs = i_c.x - r0, U = i_c.y;
                 const int lo = rs >> 7, hi = (rs + U - 1) >> 7;
                 // blocks below this window are done with (fill-ordered: wait, then release)
                 while (released < lo && ok) {
@@ -453,7 +466,7 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                 while (waited <= hi && ok) ok = wait_block(waited++);
                 if (!ok) break;
                 // the union's rows in the ring: up to the ring's end, then from its start
-                const int first = int((gbase * kM + rs) % ring_rows);
+                const int first = (gmod * kM + rs) % ring_rows; // gmod = the item's first block's slot
                 const int run1 = min(U, ring_rows - first);
                 float2 acc[kVG];
 #pragma unroll
@@ -476,22 +489,28 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                     rows(0, run1, hring + first * kHP + col);
                     if (run1 < U) rows(run1, U, hring + col);
                 }
+                const int nrow = min(kVG, it.i1 - (it.i0 + kVG * g));
 #pragma unroll
                 for (int r = 0; r < kVG; ++r) {
-                    if (sc[r] < 0) break;
-                    T *o = orow + int64_t(it.i0 + kVG * g + r) * p.out_stride;
-                    if (col < ncols) o[col] = fused::from_acc<T, float>(acc[r].x);
-                    if (col + 1 < ncols) o[col + 1] = fused::from_acc<T, float>(acc[r].y);
+                    if (r >= nrow) break;
+                    T *o = orow + int64_t(it.i0 + kVG * g + r) * p.out_stride + col;
+                    const T a = fused::from_acc<T, float>(acc[r].x), b = fused::from_acc<T, float>(acc[r].y);
+                    if (col + 1 < ncols && (reinterpret_cast<uintptr_t>(o) & 3u) == 0) {
+                        // both samples in one 4-byte store
+                        uint16_t ua, ub;
+                        memcpy(&ua, &a, 2);
+                        memcpy(&ub, &b, 2);
+                        *reinterpret_cast<uint32_t *>(o) = uint32_t(ua) | (uint32_t(ub) << 16);
+                    } else {
+                        if (col < ncols) o[0] = a;
+                        if (col + 1 < ncols) o[1] = b;
+                    }
                 }
                 // this band is free: the group two ahead goes into it
                 __syncwarp();
-                fill(g + 2 * VW, k & 1, s2);
-#pragma unroll
-                for (int r = 0; r < kVG; ++r) {
-                    sc[r] = s1[r];
-                    s1[r] = s2[r];
-                }
-                starts(g + 3 * VW, s2);
+                fill(g + 2 * VW, k & 1);
+                i_c = i_n;
+                i_n = info(g + 2 * VW);
             }
             // no copy may still be landing when the warp moves on
             asm volatile("cp.async.wait_all;" ::: "memory");
@@ -506,7 +525,7 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
                 }
                 if (ok) release_block(released++);
             }
-            gbase += nblk;
+            gmod = (gmod + nblk) % NS;
         }
     }
     tc::fence_before_sync();
