@@ -159,10 +159,11 @@ rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
     const rs_status gs = geometry(p, g);
     if (gs != RS_OK) return gs;
     const rs_plan_desc &d = p->desc;
-    const int VW = o.ex == 2 && o.vw > 0 ? std::min(kMaxVW, o.vw) : 8;
+    const bool vw_set = o.ex == 2 && o.vw > 0;
+    int VW = vw_set ? std::min(kMaxVW, o.vw) : 8;
     int NA = o.ex == 2 && o.ni_min >= 2 ? std::min(kMaxNA, o.ni_min) : 4;
     const void *fn = kernel_for(d.in_dtype, g.C);
-    const int nthreads = 32 * (kFixedWarps + VW);
+    int nthreads = 32 * (kFixedWarps + VW);
     // three blocks in the filtered-row ring where they fit (the read-back then
     // runs a block ahead of the vertical pass), else two; then the staged chunks
     int NS = kMaxNS;
@@ -171,6 +172,14 @@ rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
         return t <= 227 * 1024 && occupancy(fn, nthreads, t) >= 1;
     };
     if (!fits(NA, NS)) NS = 2;
+    if (!vw_set && !fits(NA, NS)) {
+        // wide strips (strong downscales) are bound by the latency of the
+        // staged input, not by the vertical pass: keep the staged chunks and
+        // take 4 vertical warps (x0.125: 4 chunks and 4 warps 45 us, 3 chunks
+        // and 8 warps 49 us)
+        VW = 4;
+        nthreads = 32 * (kFixedWarps + VW);
+    }
     while (NA > 2 && !fits(NA, NS)) --NA;
     if (!fits(NA, NS)) return RS_ERR_UNSUPPORTED;
     const size_t smem = layout(g.Kc, NA, g.Uv, VW, NS).total;

@@ -35,9 +35,11 @@
 //  * warps 3-6: read the accumulators back (each warp its quarter of the 128
 //    lanes), add a block's partial sums, into a ring of two blocks of
 //    filtered rows (FP32);
-//  * VW warps: the vertical pass, output row by output row, FP32 FMAs over the
-//    T_y filtered rows of its window, straight into the output.
-// A CTA takes a contiguous run of (strip, output row) positions, so it changes
+//  * VW warps: the vertical pass, in groups of 4 output rows over the union
+//    of their windows, FP32 FMAs with the group's band of weights (from a
+//    per-plan table, copied into shared memory two groups ahead), straight
+//    into the output.
+// A CTA takes a contiguous run of (strip, row group) positions, so it changes
 // strip at most a few times and its input rows run on without a halo except
 // at the ends of the run.  Every wait is bounded (2 s): a timeout sets the
 // plan's error word and every role stops; the producer lets its copies in
