@@ -179,7 +179,7 @@ def recorded_traffic(form=None):
 def stream_form(rs, plan):
     """(kind, h_warps, v_warps, staged_blocks, strip_width, row_ranges) of a
     streaming plan, else None."""
-    if plan.path not in ("stream", "tcstream", "fstream"):
+    if plan.path not in ("stream", "tcstream"):
         return None
     f = rs.rs_plan_get_stream_form(plan.handle)
     return [f.kind, f.h_warps, f.v_warps, f.staged_blocks, f.strip_width, f.row_ranges]
@@ -878,10 +878,8 @@ def main():
     t_tune = time.perf_counter() - t_tune
     # our kernels per step and plan: the weight tables, the band tables (one
     # launch for both bands of a band-streaming or tile plan; none for the
-    # pipelined kernel, which builds its bands on chip; two, horizontal and
-    # vertical, for the tensor-core and the FP32 streaming downscales) and the
-    # resample
-    launches_per_step = sum({2: 2, 3: 4, 4: 4}.get((stream_form(rs, p) or [0])[0], 3) for p in plans)
+    # pipelined kernel, which builds its bands on chip) and the resample
+    launches_per_step = sum(2 if (stream_form(rs, p) or [0])[0] == 2 else 3 for p in plans)
 
     side = torch.cuda.Stream()
 

@@ -124,10 +124,9 @@ typedef enum {
 #define RS_FORCE_STREAM 0x40u /* pick the row-streaming kernel (FP32/FP16/BF16, 1 or 3
                                  channels; bands of 4 outputs of at most 40 / 32
                                  inputs across / down); RS_ERR_UNSUPPORTED where
-                                 it cannot apply.  A downscale of 12 or more
-                                 taps across runs its tensor-core form (16-bit;
-                                 stream form 3, plan path 5) or its FP32 form
-                                 (stream form 4, plan path 6) where that applies */
+                                 it cannot apply.  A 16-bit downscale of 12 or
+                                 more taps across runs its tensor-core form
+                                 (stream form 3, plan path 5) where that applies */
 #define RS_PREFILTER 0x100u   /* interpolating cubic B-spline: with RS_K_BSPLINE3, the
                                  input is first replaced by its B-spline coefficients
                                  (per axis (c[k-1] + 4 c[k] + c[k+1]) / 6 = s[k], c
@@ -232,31 +231,23 @@ RS_API rs_status rs_plan_autotune(rs_plan *plan, const void *d_in, void *d_out, 
  * of 48 output samples against the strip's weight matrix (hi + lo 16-bit
  * parts, held in shared memory), 128 input rows per MMA block with TMA-staged
  * chunks and two tensor-memory accumulators, and the vertical pass in FP32 on
- * the filtered rows read back from tensor memory; 4: the FP32 streaming
- * downscale (plan path 6; FP32 plans of 1 or 3 channels that downscale both
- * axes, bands of at most 64 pixels per 4 outputs across and 128 rows per 4
- * output rows down): the same pipeline with the horizontal pass on SIMT warps
- * (a task per 32-row staged block and group of 4 output pixels, lanes along
- * rows) and the vertical pass in groups of 4 output rows.  Zeros choose a
- * field's default.  Forms 0-2 and 4 compute the same sums (each output's taps
- * in increasing order, FP32 accumulation; band zeros add exact zeros); form 3
- * sums each horizontal window in the tensor cores' order (FP32 accumulation),
- * so its results may differ from the others in the last bits. */
+ * the filtered rows read back from tensor memory.  Zeros choose a field's
+ * default.  Forms 0-2 compute the same sums (each output's taps in increasing
+ * order, FP32 accumulation; band zeros add exact zeros); form 3 sums each
+ * horizontal window in the tensor cores' order (FP32 accumulation), so its
+ * results may differ from the others in the last bits. */
 typedef struct {
-    int32_t kind;          /* 0, 1, 2, 3 or 4 as above                                */
-    int32_t h_warps;       /* warps on the horizontal pass (kind 1: 2..6; kind 2: 1..8;
-                              kind 4: 1..12, with v_warps at most 18, and at most
-                              4 staged_blocks (channels 3) or 12 staged_blocks
-                              (channels 1) warps)                                     */
+    int32_t kind;          /* 0, 1, 2 or 3 as above                                   */
+    int32_t h_warps;       /* warps on the horizontal pass (kind 1: 2..6; kind 2: 1..8) */
     int32_t staged_blocks; /* staged 32-row input blocks, 2..4 (kind 3: staged chunks of
-                              128 rows x 64 samples, 2..6; kind 4: 2..6)             */
-    int32_t strip_width;   /* output pixels per strip (a multiple of 4; kinds 3 and 4: 0
-                              to set, 48 / channels reported)                         */
+                              128 rows x 64 samples, 2..6)                            */
+    int32_t strip_width;   /* output pixels per strip (a multiple of 4; kind 3: 0 to set,
+                              48 / channels reported)                                 */
     int32_t prefetch;      /* kind 2: 1 = prefetch the block after the staging ring
                               into L2; kind 3: 1 = prefetch the chunk 2 rings ahead  */
     int32_t v_warps;       /* kind 2: warps on the vertical pass (a CTA has one producer
                               warp plus h_warps + v_warps <= 15; above 11 the CTA
-                              takes a whole SM); kinds 3 and 4: 1..10                 */
+                              takes a whole SM); kind 3: 1..8                         */
     int32_t row_ranges;    /* kind 2: output row ranges, one CTA per (strip, range);
                               1..255                                                  */
 } rs_stream_form;
@@ -270,7 +261,7 @@ RS_API rs_status rs_plan_set_stream_form(rs_plan *plan, const rs_stream_form *fo
 
 /* The form the plan's streaming kernel is configured in (RS_ERR_UNSUPPORTED
  * if the plan has no streaming configuration); whether rs_resample runs it is
- * rs_plan_info.path == 3 (kinds 0-2), 5 (kind 3) or 6 (kind 4). */
+ * rs_plan_info.path == 3 (kinds 0-2) or 5 (kind 3). */
 RS_API rs_status rs_plan_get_stream_form(const rs_plan *plan, rs_stream_form *form);
 
 /* Free a plan after waiting for its work to finish.  NULL is accepted. */
@@ -284,8 +275,7 @@ typedef struct {
     int32_t path;             /* 0 = fused tiles (SIMT), 1 = two-pass SIMT, 2 = fused
                                  tiles with the tcgen05 vertical pass, 3 = row-streaming,
                                  4 = vertical-first two-pass, 5 = tensor-core
-                                 streaming downscale (stream form kind 3), 6 = FP32
-                                 streaming downscale (stream form kind 4)           */
+                                 streaming downscale (stream form kind 3)           */
     int32_t tile_h, tile_w;   /* output tile of the chosen pass kernel            */
     int32_t group_h, group_w; /* outputs per thread group along each axis         */
     int32_t span_h, span_w;   /* band width (inputs per group)                    */

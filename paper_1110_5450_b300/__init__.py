@@ -40,7 +40,7 @@ BOUNDARIES = {"clamp": RS_B_CLAMP, "mirror": RS_B_MIRROR, "reflect101": RS_B_REF
               "truncate": RS_B_TRUNCATE}
 DEFAULT_PARAM = {"linear": 0.0, "cubic": -0.5, "lanczos": 3.0, "bspline3": 0.0, "mitchell": 1.0 / 3.0,
                  "gaussian": 0.5}
-PATHS = {0: "fused", 1: "two_pass", 2: "tcgen05", 3: "stream", 4: "vfirst", 5: "tcstream", 6: "fstream"}
+PATHS = {0: "fused", 1: "two_pass", 2: "tcgen05", 3: "stream", 4: "vfirst", 5: "tcstream"}
 
 
 class rs_plan_desc(ctypes.Structure):
@@ -262,8 +262,7 @@ def rs_plan_set_stream_form(plan: int, kind: int, h_warps: int = 0, staged_block
     """Runs the plan's row-streaming kernel in the given form (0 band kernel,
     phase-alternating; 1 band kernel, warp-specialised; 2 pipelined, with
     `prefetch`, `v_warps` and `row_ranges` options; 3 the tensor-core
-    downscale, with `staged_blocks` chunks and `v_warps`; 4 the FP32
-    streaming downscale, with `h_warps`, `staged_blocks` and `v_warps`)."""
+    downscale, with `staged_blocks` chunks and `v_warps`)."""
     f = rs_stream_form(int(kind), int(h_warps), int(staged_blocks), int(strip_width), int(prefetch),
                        int(v_warps), int(row_ranges))
     _check(_lib.rs_plan_set_stream_form(_vp(plan), ctypes.byref(f), _vp(stream)), "rs_plan_set_stream_form")

@@ -351,7 +351,7 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
             b->streamed[i] = 1;
             ++b->n_streamed;
             // one error word for the whole batch
-            p->sp.err = p->xp.err = p->tcp.err = p->fsp.err = static_cast<int *>(b->derr.p);
+            p->sp.err = p->xp.err = p->tcp.err = static_cast<int *>(b->derr.p);
             b->stream_order.push_back(i);
         }
     }
@@ -655,7 +655,7 @@ rs_status rs_batch_image_path(const rs_batch *b, int32_t index, int32_t *path)
     if (!b || !path || index < 0 || index >= int32_t(b->plans.size()))
         return fail(RS_ERR_INVALID_ARG, "batch: bad image index");
     const rs_plan *p = b->plans[size_t(index)];
-    *path = b->streamed[size_t(index)] ? (p->tcs_on ? 5 : p->fs_on ? 6 : 3) : 0;
+    *path = b->streamed[size_t(index)] ? (p->tcs_on ? 5 : 3) : 0;
     return RS_OK;
 }
 

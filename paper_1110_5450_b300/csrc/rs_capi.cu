@@ -1199,7 +1199,7 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
         double us_tile = 0;
         s = time_plan(p, d_in, d_out, stream, &us_tile);
         if (s != RS_OK) return s;
-        // {form (0 band kernels, 1 pipelined, 2 tensor-core downscale, 3 FP32 streaming downscale), warp-specialised,
+        // {form (0 band kernels, 1 pipelined, 2 tensor-core downscale), warp-specialised,
         //  horizontal warps, staged blocks (chunks), L2 prefetch, unused, vertical warps}
         const int cands_s[][7] = {{0, 0, 0, 3, 0, 0, 0}, {0, 0, 0, 2, 0, 0, 0}, {0, 1, 4, 3, 0, 0, 0},
                                   {0, 1, 4, 2, 0, 0, 0}, {0, 1, 3, 3, 0, 0, 0}, {0, 1, 5, 3, 0, 0, 0},
@@ -1208,14 +1208,12 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
                                   {1, 0, 4, 3, 0, 0, 4}, {1, 0, 7, 2, 0, 0, 8}, {1, 0, 8, 2, 0, 0, 7},
                                   {2, 0, 0, 4, 0, 0, 4}, {2, 0, 0, 4, 0, 0, 6}, {2, 0, 0, 4, 0, 0, 8},
                                   {2, 0, 0, 4, 0, 0, 10}, {2, 0, 0, 3, 0, 0, 6}, {2, 0, 0, 6, 0, 0, 6},
-                                  {2, 0, 0, 4, 1, 0, 8}, {2, 0, 0, 4, 1, 0, 10},
-                                  {3, 0, 10, 4, 0, 0, 6}, {3, 0, 12, 4, 0, 0, 6}, {3, 0, 8, 4, 0, 0, 6},
-                                  {3, 0, 10, 5, 0, 0, 6}, {3, 0, 10, 4, 0, 0, 8}, {3, 0, 12, 3, 0, 0, 6}};
-        const bool x_ok = xstream::eligible(p), t_ok = tcstream::eligible(p), f_ok = fstream::eligible(p);
+                                  {2, 0, 0, 4, 1, 0, 8}, {2, 0, 0, 4, 1, 0, 10}};
+        const bool x_ok = xstream::eligible(p), t_ok = tcstream::eligible(p);
         double best_s = 1e300;
         int best_code = 0;
         for (const auto &c : cands_s) {
-            if ((c[0] == 1 && !x_ok) || (c[0] == 2 && !t_ok) || (c[0] == 3 && !f_ok)) continue;
+            if ((c[0] == 1 && !x_ok) || (c[0] == 2 && !t_ok)) continue;
             stream::Opts o;
             o.ex = c[0];
             o.ws = c[1];
@@ -1321,14 +1319,7 @@ rs_status rs_plan_autotune(rs_plan *p, const void *d_in, void *d_out, void *stre
 rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *stream_v)
 {
     if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
-    if (f->kind == 4) {
-        // the FP32 streaming downscale: horizontal warps (1..8), staged blocks
-        // (2..6) and vertical warps (1..10), each 0 for the default
-        if (f->prefetch || f->row_ranges || f->strip_width || f->h_warps < 0 || f->h_warps > fstream::kMaxHW ||
-            f->staged_blocks < 0 || f->staged_blocks == 1 || f->staged_blocks > fstream::kMaxNA || f->v_warps < 0 ||
-            f->v_warps > tcstream::kMaxVW)
-            return fail(RS_ERR_INVALID_ARG, "malformed streaming form");
-    } else if (f->kind == 3) {
+    if (f->kind == 3) {
         // the tensor-core downscale: staged chunks (2..6) and vertical warps (1..8); no other choice
         if (f->h_warps || (f->prefetch != 0 && f->prefetch != 1) || f->row_ranges || f->strip_width ||
             f->staged_blocks < 0 ||
@@ -1346,11 +1337,11 @@ rs_status rs_plan_set_stream_form(rs_plan *p, const rs_stream_form *f, void *str
     if (p->path != 0 || p->prefilter)
         return fail(RS_ERR_UNSUPPORTED, "the plan has no fused path for the streaming kernel");
     stream::Opts o;
-    o.ex = f->kind == 4 ? 3 : f->kind == 3 ? 2 : f->kind == 2 ? 1 : 0;
+    o.ex = f->kind == 3 ? 2 : f->kind == 2 ? 1 : 0;
     o.ws = f->kind == 1 ? 1 : 0;
     o.hw = f->h_warps;
     if (f->kind == 1 && f->h_warps == 1) return fail(RS_ERR_INVALID_ARG, "kind 1 takes 2..6 horizontal warps");
-    o.ni_min = f->staged_blocks ? f->staged_blocks : (f->kind == 2 ? 2 : f->kind >= 3 ? 0 : 3);
+    o.ni_min = f->staged_blocks ? f->staged_blocks : (f->kind == 2 ? 2 : f->kind == 3 ? 0 : 3);
     o.sw = f->strip_width;
     o.pf = f->prefetch;
     o.vw = f->v_warps;
@@ -1374,16 +1365,6 @@ rs_status rs_plan_get_stream_form(const rs_plan *p, rs_stream_form *f)
     if (!p || !f) return fail(RS_ERR_INVALID_ARG, "NULL plan or form");
     if (!p->stream_ok) return fail(RS_ERR_UNSUPPORTED, "the plan has no streaming configuration");
     const stream::Opts o = stream::Opts::decode(p->stream_code);
-    if (p->fs_on) {
-        f->kind = 4;
-        f->h_warps = p->fsp.HW;
-        f->staged_blocks = p->fsp.NA;
-        f->strip_width = p->fsp.NP;
-        f->prefetch = 0;
-        f->v_warps = p->fsp.VW;
-        f->row_ranges = 0;
-        return RS_OK;
-    }
     if (p->tcs_on) {
         f->kind = 3;
         f->h_warps = 0;
@@ -1482,18 +1463,6 @@ rs_status rs_plan_get_info(const rs_plan *p, rs_plan_info *info)
         info->span_w = p->tcp.Kc / p->desc.channels; // staged input pixels per strip
         info->warps_pass1 = 0;
         info->stages = p->tcp.NA;
-        info->smem_bytes = int32_t(p->s_smem);
-        info->ctas_per_sm = p->s_ctas;
-    } else if (p->path == 0 && p->use_stream && p->fs_on) {
-        info->path = 6;
-        info->tile_h = tcstream::kM;   // filtered rows per ring block
-        info->tile_w = p->fsp.NP;      // output pixels per strip
-        info->group_h = 4;
-        info->group_w = 4;
-        info->span_h = p->fsp.Uv;
-        info->span_w = p->fsp.JH;
-        info->warps_pass1 = p->fsp.HW;
-        info->stages = p->fsp.NA;
         info->smem_bytes = int32_t(p->s_smem);
         info->ctas_per_sm = p->s_ctas;
     } else if (p->path == 0 && p->use_stream && p->x_on) {

@@ -13,7 +13,6 @@
 #include "rs_internal.h"
 #include "rs_stream.cuh"
 #include "rs_tcstream.cuh"
-#include "rs_fstream.cuh"
 #include "rs_xstream.cuh"
 
 namespace rs {
@@ -119,11 +118,6 @@ struct rs_plan {
     int tcs_on = 0;
     rs::tcstream::Params tcp{};
     rs::DeviceBuf tcbufs;
-    // the FP32 streaming downscale: when fs_on, s_fn / s_block / s_smem /
-    // s_grid describe it, fsp holds its parameters and fsbufs its tables
-    int fs_on = 0;
-    rs::fstream::Params fsp{};
-    rs::DeviceBuf fsbufs;
     // external placement of the streaming kernels' tables (a serving
     // arena): when ext_base is set, the streaming set-up carves its band or
     // descriptor tables out of [ext_base, ext_base + ext_bytes) instead of
@@ -200,9 +194,7 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 
 namespace stream {
 // Choices of a streaming configuration: ex = 1 the pipelined kernel
-// (rs_xstream.cuh), 2 the tensor-core downscale (rs_tcstream.cuh), 3 the FP32
-// streaming downscale (rs_fstream.cuh; hw, ni_min and vw give its horizontal
-// warps, staged blocks and vertical warps), 0 the band
+// (rs_xstream.cuh), 2 the tensor-core downscale (rs_tcstream.cuh), 0 the band
 // kernels of rs_stream.cuh, -1 the pipelined kernel where it applies with its
 // default choices, else the tensor-core downscale where it applies, else the
 // band kernels (ni_min and vw give the tensor-core kernel's staged chunks and
@@ -221,7 +213,7 @@ struct Opts {
     int code() const
     {
         return 1 + (ws > 0 ? 2 : 0) + 4 * hw + 64 * ni_min + 512 * (sw / 4) + (ex == 1 ? 32768 : 0) +
-               (pf ? 65536 : 0) + (ex == 2 ? 131072 : 0) + (vw << 18) + (nr << 22) + (ex == 3 ? (1 << 30) : 0);
+               (pf ? 65536 : 0) + (ex == 2 ? 131072 : 0) + (vw << 18) + (nr << 22);
     }
     static Opts decode(int c)
     {
@@ -230,7 +222,7 @@ struct Opts {
         o.hw = (c >> 2) & 15;
         o.ni_min = (c >> 6) & 7;
         o.sw = ((c >> 9) & 63) * 4;
-        o.ex = ((c >> 30) & 1) ? 3 : ((c >> 17) & 1) ? 2 : (c >> 15) & 1;
+        o.ex = ((c >> 17) & 1) ? 2 : (c >> 15) & 1;
         o.pf = (c >> 16) & 1;
         o.vw = (c >> 18) & 15;
         o.nr = (c >> 22) & 255;
@@ -272,30 +264,7 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 size_t space_bound(const AxisGeom &gx, const AxisGeom &gy, int C);
 // As stream::preload.
 void preload(int dtype);
-// Union rows of the row groups (kVG output rows from a multiple of kVG) at
-// most, for window starts sy and t_y taps.
-int vband_rows(const std::vector<int32_t> &sy, int t_y);
-// Builds the plan's vertical band table ([gpr][Uv] weights of each row
-// group's 4 rows at its union rows) and per group (first union row, union
-// rows) on `s`, from the plan's vertical window tables.
-cudaError_t launch_vband(const rs_plan *p, int gpr, int Uv, float4 *vband, int2 *vinfo, cudaStream_t s);
 } // namespace tcstream
-
-namespace fstream {
-// Whether the plan can run the FP32 streaming downscale (FP32, 1 or 3
-// channels, both axes downscaled, a 16-byte row pitch, bands of at most 64
-// pixels per group of 4 outputs, at most 128 rows per group of 4 output rows).
-bool eligible(const rs_plan *p);
-// Configures it on `s` (o.hw horizontal warps, o.ni_min staged blocks and
-// o.vw vertical warps when o.ex = 3; else the defaults); RS_ERR_UNSUPPORTED
-// when not eligible or when the tables would need external placement.
-rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o);
-// Rebuilds its horizontal and vertical band tables (after a recompute).
-rs_status rebuild(rs_plan *p, cudaStream_t s);
-rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
-// As stream::preload (FP32 only).
-void preload();
-} // namespace fstream
 
 namespace xstream {
 // As stream::preload, for the pipelined kernel.

@@ -779,7 +779,6 @@ rs_status rs_server_create(const rs_server_desc *desc, rs_server **out)
             xstream::preload(dt);
         }
         if (dt == RS_F16 || dt == RS_BF16) tcstream::preload(dt);
-        if (dt == RS_F32) fstream::preload();
     }
     S->th = std::thread(scheduler, S);
     *out = S;

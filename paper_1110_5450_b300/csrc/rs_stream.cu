@@ -274,8 +274,8 @@ rs_status bands_of(const rs_plan *p, Bands &b)
 
 int widths(rs_plan *p, const Opts &opts, int *out, int n)
 {
-    if (opts.ex == 2 || opts.ex == 3) {
-        if (!(opts.ex == 2 ? tcstream::eligible(p) : fstream::eligible(p)) || n < 1) return 0;
+    if (opts.ex == 2) {
+        if (!tcstream::eligible(p) || n < 1) return 0;
         out[0] = tcstream::kN / p->desc.channels; // one strip width
         return 1;
     }
@@ -292,7 +292,6 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
 {
     p->stream_ok = 0;
     if (opts.ex == 2) return tcstream::setup(p, s, opts);
-    if (opts.ex == 3) return fstream::setup(p, s, opts);
     // the exact-window form where it applies (or when asked for)
     if (opts.ex != 0) {
         const rs_status xs = xstream::setup(p, s, opts);
@@ -304,15 +303,10 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
         if (p->gx.t_eff >= 12) {
             const rs_status ts = tcstream::setup(p, s, opts);
             if (ts != RS_ERR_UNSUPPORTED) return ts;
-            // and for FP32 the SIMT form of that pipeline (x0.3: 78 against
-            // 94 us on the tuned band kernel)
-            const rs_status fs = fstream::setup(p, s, opts);
-            if (fs != RS_ERR_UNSUPPORTED) return fs;
         }
     }
     p->x_on = 0;
     p->tcs_on = 0;
-    p->fs_on = 0;
     Bands bd;
     const rs_status bst = bands_of(p, bd);
     if (bst != RS_OK) return bst;
@@ -409,7 +403,6 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
 rs_status rebuild(rs_plan *p, cudaStream_t s)
 {
     if (p->tcs_on) return tcstream::rebuild(p, s);
-    if (p->fs_on) return fstream::rebuild(p, s);
     if (p->x_on) return RS_OK; // the exact-window kernel reads the weight tables directly
     // both bands in one launch of the band kernel:
     //  * vertical: groups of 4 rows, every weight twice -> per tap (w0, w0, .., w3, w3);
@@ -466,7 +459,6 @@ rs_status encode_input_map(const rs_plan *p, const void *d_in, CUtensorMap *map)
 rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s)
 {
     if (p->tcs_on) return tcstream::launch(p, d_in, d_out, s);
-    if (p->fs_on) return fstream::launch(p, d_in, d_out, s);
     if (p->stmap_ptr != d_in) {
         const rs_status st = encode_input_map(p, d_in, &p->stmap);
         if (st != RS_OK) return st;

@@ -114,29 +114,16 @@ rs_status geometry(const rs_plan *p, Geometry &g)
     // rows spanned by a row group's windows (kVG output rows from a multiple of kVG)
     const std::vector<int32_t> &sy = p->host_start_y;
     g.gpr = int((sy.size() + kVG - 1) / kVG);
-    g.Uv = vband_rows(sy, g.Ty);
+    g.Uv = 0;
+    for (size_t i = 0; i < sy.size(); i += kVG) {
+        const size_t j = std::min(sy.size() - 1, i + kVG - 1);
+        g.Uv = std::max(g.Uv, int(sy[j] - sy[i]) + g.Ty);
+    }
     if (g.Uv > kMaxTy) return RS_ERR_UNSUPPORTED; // a band must span at most two blocks
     return RS_OK;
 }
 
 } // namespace
-
-int vband_rows(const std::vector<int32_t> &sy, int t_y)
-{
-    int Uv = 0;
-    for (size_t i = 0; i < sy.size(); i += kVG) {
-        const size_t j = std::min(sy.size() - 1, i + kVG - 1);
-        Uv = std::max(Uv, int(sy[j] - sy[i]) + t_y);
-    }
-    return Uv;
-}
-
-cudaError_t launch_vband(const rs_plan *p, int gpr, int Uv, float4 *vband, int2 *vinfo, cudaStream_t s)
-{
-    build_vband_kernel<<<unsigned(gpr), 64, 0, s>>>(p->ty.start, static_cast<const float *>(p->ty.wwork),
-                                                    p->gy.t_eff, int(p->gy.n_out), gpr, Uv, vband, vinfo);
-    return cudaGetLastError();
-}
 
 bool eligible(const rs_plan *p)
 {
@@ -168,7 +155,6 @@ void preload(int dtype)
 rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
 {
     p->tcs_on = 0;
-    p->fs_on = 0;
     Geometry g;
     const rs_status gs = geometry(p, g);
     if (gs != RS_OK) return gs;
@@ -288,8 +274,10 @@ rs_status rebuild(rs_plan *p, cudaStream_t s)
         build_b_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(sx, wx, p->gx.t_eff, tp.out_w, tp.C, tp.NP, tp.Kc, tp.g0, bm);
     else
         build_b_kernel<__half><<<grid, 128, 0, s>>>(sx, wx, p->gx.t_eff, tp.out_w, tp.C, tp.NP, tp.Kc, tp.g0, bm);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_vband(p, tp.gpr, tp.Uv, const_cast<float4 *>(tp.vband), const_cast<int2 *>(tp.vinfo), s);
+    build_vband_kernel<<<unsigned(tp.gpr), 64, 0, s>>>(p->ty.start, static_cast<const float *>(p->ty.wwork),
+                                                       p->gy.t_eff, tp.out_h, tp.gpr, tp.Uv,
+                                                       const_cast<float4 *>(tp.vband), const_cast<int2 *>(tp.vinfo));
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core weight matrix launch");
     return RS_OK;
 }

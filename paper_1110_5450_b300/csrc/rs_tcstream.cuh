@@ -143,170 +143,6 @@ __device__ __forceinline__ bool next_item(int64_t &pos, int64_t pos1, int gpr, i
     return true;
 }
 
-// The vertical pass of one warp (index v of the VW vertical warps) over the
-// CTA's positions [pos0, pos1): row groups of kVG output rows, each over the
-// union of its windows in the ring of NS blocks of kM filtered rows (pitch HP
-// floats), which the producing role fills in order and this role releases
-// block by block (hfull / hfree, one release barrier per vertical warp).  PP
-// is a parameter block with the fields used here.
-template <typename T, int C, int HP, typename PP>
-__device__ __forceinline__ void v_role(const PP &p, const float *hring, float *wsm, uint64_t *hfull,
-                                       uint64_t *hfree, volatile int *abort_flag, int v, int lane, int64_t pos0,
-                                       int64_t pos1)
-{
-    const int NS = p.NS, VW = p.VW, Ty = p.Ty;
-    // rows [r0, r_end) of an item's windows, and its blocks of kM rows
-    auto item_rows = [&](const Item &it, int &r0, int &nblk) {
-        r0 = __ldg(p.sy + it.i0);
-        const int r_end = __ldg(p.sy + it.i1 - 1) + Ty;
-        nblk = (r_end - r0 + kM - 1) / kM;
-    };
-    int64_t pos = pos0;
-    bool ok = true;
-    Item it;
-    const int ring_rows = NS * kM;
-    // ring slots of the next block to wait for (and its round) and of the
-    // next one to release, kept by increments: every block of every item is
-    // waited for and released once, in order
-    int w_sl = 0, r_sl = 0, gmod = 0;
-    uint32_t w_rnd = 0;
-    while (ok && next_item(pos, pos1, p.gpr, p.out_h, it)) {
-        int r0, nblk;
-        item_rows(it, r0, nblk);
-        int waited = 0, released = 0;
-        auto wait_block = [&](int) {
-            const bool r = warp_wait(&hfull[w_sl], w_rnd & 1u, abort_flag, p.err);
-            if (++w_sl == NS) {
-                w_sl = 0;
-                ++w_rnd;
-            }
-            return r;
-        };
-        auto release_block = [&](int) {
-            __syncwarp();
-            if (lane == 0) fused::mbar_arrive(&hfree[r_sl * kMaxVW + v]);
-            if (++r_sl == NS) r_sl = 0;
-        };
-        const int x0 = it.strip * p.NP;
-        const int ncols = min(kN, (p.out_w - x0) * C);
-        T *orow = static_cast<T *>(p.out) + int64_t(x0) * C;
-        // The warp takes the item's row groups v, v + VW, ...: group g is the
-        // output rows i0 + 4 g + r, r < 4 (row group q = i0 / 4 + g of the
-        // plan's band table).  Their windows overlap, so a group runs over the
-        // union of its windows once, with the band of its 4 rows' weights at
-        // each union row (zero outside a row's own window): per union row one
-        // broadcast 16-byte weight load, one 8-byte load of the filtered row
-        // and 8 FMAs (4 rows x the lane's 2 samples: lanes 0..23 own the
-        // sample pairs (2 lane, 2 lane + 1)).  The band of the group two ahead
-        // is copied from the table while this one is summed (one 16-byte
-        // asynchronous copy per union row), and its (first union row, union
-        // rows) pair loaded a group earlier still.
-        const int col = 2 * lane;
-        const bool act = col < kN;
-        const int Uv = p.Uv;
-        float4 *bands = reinterpret_cast<float4 *>(wsm) + size_t(v) * 2 * Uv;
-        const int qb = it.i0 / kVG;
-        const int ng = (it.i1 - it.i0 + kVG - 1) / kVG;
-        auto fill = [&](int g, int slot) {
-            if (g < ng) {
-                const float4 *src = p.vband + size_t(qb + g) * Uv;
-                float4 *bd = bands + slot * Uv;
-                for (int u = lane; u < Uv; u += 32)
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(fused::smem_addr(bd + u)),
-                                 "l"(src + u)
-                                 : "memory");
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        auto info = [&](int g) { return g < ng ? __ldg(p.vinfo + qb + g) : make_int2(0, 0); };
-        int2 i_c = info(v), i_n = info(v + VW);
-        fill(v, 0);
-        fill(v + VW, 1);
-        for (int k = 0, g = v; g < ng && ok; ++k, g += VW) {
-            // this group's band (the older of the two in flight) has landed
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-            __syncwarp();
-            const float4 *bd = bands + (k & 1) * Uv;
-            const int rs = i_c.x - r0, U = i_c.y;
-            const int lo = rs >> 7, hi = (rs + U - 1) >> 7;
-            // blocks below this window are done with (fill-ordered: wait, then release)
-            while (released < lo && ok) {
-                if (waited <= released) {
-                    ok = wait_block(released);
-                    waited = released + 1;
-                }
-                if (ok) release_block(released++);
-            }
-            while (waited <= hi && ok) ok = wait_block(waited++);
-            if (!ok) break;
-            // the union's rows in the ring: up to the ring's end, then from its start
-            const int first = (gmod * kM + rs) % ring_rows; // gmod = the item's first block's slot
-            const int run1 = min(U, ring_rows - first);
-            float2 acc[kVG];
-#pragma unroll
-            for (int r = 0; r < kVG; ++r) acc[r] = make_float2(0.f, 0.f);
-            if (act) {
-                auto rows = [&](int u0, int u1, const float *hr) {
-                    for (int u = u0; u < u1; ++u, hr += HP) {
-                        const float4 w = bd[u];
-                        const float2 h = *reinterpret_cast<const float2 *>(hr);
-                        acc[0].x = fmaf(w.x, h.x, acc[0].x);
-                        acc[0].y = fmaf(w.x, h.y, acc[0].y);
-                        acc[1].x = fmaf(w.y, h.x, acc[1].x);
-                        acc[1].y = fmaf(w.y, h.y, acc[1].y);
-                        acc[2].x = fmaf(w.z, h.x, acc[2].x);
-                        acc[2].y = fmaf(w.z, h.y, acc[2].y);
-                        acc[3].x = fmaf(w.w, h.x, acc[3].x);
-                        acc[3].y = fmaf(w.w, h.y, acc[3].y);
-                    }
-                };
-                rows(0, run1, hring + first * HP + col);
-                if (run1 < U) rows(run1, U, hring + col);
-            }
-            const int nrow = min(kVG, it.i1 - (it.i0 + kVG * g));
-#pragma unroll
-            for (int r = 0; r < kVG; ++r) {
-                if (r >= nrow) break;
-                T *o = orow + int64_t(it.i0 + kVG * g + r) * p.out_stride + col;
-                const T a = fused::from_acc<T, float>(acc[r].x), b = fused::from_acc<T, float>(acc[r].y);
-                if (col + 1 < ncols && (reinterpret_cast<uintptr_t>(o) & (2 * sizeof(T) - 1)) == 0) {
-                    // both samples in one store (4 bytes for 16-bit types, 8 for FP32)
-                    if constexpr (sizeof(T) == 2) {
-                        uint16_t ua, ub;
-                        memcpy(&ua, &a, 2);
-                        memcpy(&ub, &b, 2);
-                        *reinterpret_cast<uint32_t *>(o) = uint32_t(ua) | (uint32_t(ub) << 16);
-                    } else {
-                        *reinterpret_cast<float2 *>(o) = make_float2(a, b);
-                    }
-                } else {
-                    if (col < ncols) o[0] = a;
-                    if (col + 1 < ncols) o[1] = b;
-                }
-            }
-            // this band is free: the group two ahead goes into it
-            __syncwarp();
-            fill(g + 2 * VW, k & 1);
-            i_c = i_n;
-            i_n = info(g + 2 * VW);
-        }
-        // no copy may still be landing when the warp moves on
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncwarp();
-        // the rest of the item's blocks, each released as soon as it is seen
-        // full (holding one while waiting for a later one would deadlock:
-        // the read-back of block m + 2 waits for block m's release)
-        while (ok && released < nblk) {
-            if (waited <= released) {
-                ok = wait_block(released);
-                waited = released + 1;
-            }
-            if (ok) release_block(released++);
-        }
-        gmod = (gmod + nblk) % NS;
-    }
-}
-
 template <typename T, int C>
 __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
     tcstream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
@@ -551,7 +387,148 @@ __global__ void __launch_bounds__(32 * (kFixedWarps + kMaxVW), 1)
             }
         }
     } else if (warp < kFixedWarps + VW) {
-        v_role<T, C, kHP>(p, hring, wsm, hfull, hfree, abort_flag, warp - kFixedWarps, lane, pos0, pos1);
+        // ================= vertical pass =================
+        const int v = warp - kFixedWarps;
+        int64_t pos = pos0;
+        bool ok = true;
+        Item it;
+        const int ring_rows = NS * kM;
+        // ring slots of the next block to wait for (and its round) and of the
+        // next one to release, kept by increments: every block of every item is
+        // waited for and released once, in order
+        int w_sl = 0, r_sl = 0, gmod = 0;
+        uint32_t w_rnd = 0;
+        while (ok && next_item(pos, pos1, p.gpr, p.out_h, it)) {
+            int r0, nblk;
+            item_rows(it, r0, nblk);
+            int waited = 0, released = 0;
+            auto wait_block = [&](int) {
+                const bool r = warp_wait(&hfull[w_sl], w_rnd & 1u, abort_flag, p.err);
+                if (++w_sl == NS) {
+                    w_sl = 0;
+                    ++w_rnd;
+                }
+                return r;
+            };
+            auto release_block = [&](int) {
+                __syncwarp();
+                if (lane == 0) fused::mbar_arrive(&hfree[r_sl * kMaxVW + v]);
+                if (++r_sl == NS) r_sl = 0;
+            };
+            const int x0 = it.strip * p.NP;
+            const int ncols = min(kN, (p.out_w - x0) * C);
+            T *orow = static_cast<T *>(p.out) + int64_t(x0) * C;
+            // The warp takes the item's row groups v, v + VW, ...: group g is the
+            // output rows i0 + 4 g + r, r < 4 (row group q = i0 / 4 + g of the
+            // plan's band table).  Their windows overlap, so a group runs over the
+            // union of its windows once, with the band of its 4 rows' weights at
+            // each union row (zero outside a row's own window): per union row one
+            // broadcast 16-byte weight load, one 8-byte load of the filtered row
+            // and 8 FMAs (4 rows x the lane's 2 samples: lanes 0..23 own the
+            // sample pairs (2 lane, 2 lane + 1)).  The band of the group two ahead
+            // is copied from the table while this one is summed (one 16-byte
+            // asynchronous copy per union row), and its (first union row, union
+            // rows) pair loaded a group earlier still.
+            const int col = 2 * lane;
+            const bool act = col < kN;
+            const int Uv = p.Uv;
+            float4 *bands = reinterpret_cast<float4 *>(wsm) + size_t(v) * 2 * Uv;
+            const int qb = it.i0 / kVG;
+            const int ng = (it.i1 - it.i0 + kVG - 1) / kVG;
+            auto fill = [&](int g, int slot) {
+                if (g < ng) {
+                    const float4 *src = p.vband + size_t(qb + g) * Uv;
+                    float4 *bd = bands + slot * Uv;
+                    for (int u = lane; u < Uv; u += 32)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(fused::smem_addr(bd + u)),
+                                     "l"(src + u)
+                                     : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            auto info = [&](int g) { return g < ng ? __ldg(p.vinfo + qb + g) : make_int2(0, 0); };
+            int2 i_c = info(v), i_n = info(v + VW);
+            fill(v, 0);
+            fill(v + VW, 1);
+            for (int k = 0, g = v; g < ng && ok; ++k, g += VW) {
+                // this group's band (the older of the two in flight) has landed
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+                __syncwarp();
+                const float4 *bd = bands + (k & 1) * Uv;
+                const int rs = i_c.x - r0, U = i_c.y;
+                const int lo = rs >> 7, hi = (rs + U - 1) >> 7;
+                // blocks below this window are done with (fill-ordered: wait, then release)
+                while (released < lo && ok) {
+                    if (waited <= released) {
+                        ok = wait_block(released);
+                        waited = released + 1;
+                    }
+                    if (ok) release_block(released++);
+                }
+                while (waited <= hi && ok) ok = wait_block(waited++);
+                if (!ok) break;
+                // the union's rows in the ring: up to the ring's end, then from its start
+                const int first = (gmod * kM + rs) % ring_rows; // gmod = the item's first block's slot
+                const int run1 = min(U, ring_rows - first);
+                float2 acc[kVG];
+#pragma unroll
+                for (int r = 0; r < kVG; ++r) acc[r] = make_float2(0.f, 0.f);
+                if (act) {
+                    auto rows = [&](int u0, int u1, const float *hr) {
+                        for (int u = u0; u < u1; ++u, hr += kHP) {
+                            const float4 w = bd[u];
+                            const float2 h = *reinterpret_cast<const float2 *>(hr);
+                            acc[0].x = fmaf(w.x, h.x, acc[0].x);
+                            acc[0].y = fmaf(w.x, h.y, acc[0].y);
+                            acc[1].x = fmaf(w.y, h.x, acc[1].x);
+                            acc[1].y = fmaf(w.y, h.y, acc[1].y);
+                            acc[2].x = fmaf(w.z, h.x, acc[2].x);
+                            acc[2].y = fmaf(w.z, h.y, acc[2].y);
+                            acc[3].x = fmaf(w.w, h.x, acc[3].x);
+                            acc[3].y = fmaf(w.w, h.y, acc[3].y);
+                        }
+                    };
+                    rows(0, run1, hring + first * kHP + col);
+                    if (run1 < U) rows(run1, U, hring + col);
+                }
+                const int nrow = min(kVG, it.i1 - (it.i0 + kVG * g));
+#pragma unroll
+                for (int r = 0; r < kVG; ++r) {
+                    if (r >= nrow) break;
+                    T *o = orow + int64_t(it.i0 + kVG * g + r) * p.out_stride + col;
+                    const T a = fused::from_acc<T, float>(acc[r].x), b = fused::from_acc<T, float>(acc[r].y);
+                    if (col + 1 < ncols && (reinterpret_cast<uintptr_t>(o) & 3u) == 0) {
+                        // both samples in one 4-byte store
+                        uint16_t ua, ub;
+                        memcpy(&ua, &a, 2);
+                        memcpy(&ub, &b, 2);
+                        *reinterpret_cast<uint32_t *>(o) = uint32_t(ua) | (uint32_t(ub) << 16);
+                    } else {
+                        if (col < ncols) o[0] = a;
+                        if (col + 1 < ncols) o[1] = b;
+                    }
+                }
+                // this band is free: the group two ahead goes into it
+                __syncwarp();
+                fill(g + 2 * VW, k & 1);
+                i_c = i_n;
+                i_n = info(g + 2 * VW);
+            }
+            // no copy may still be landing when the warp moves on
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+            // the rest of the item's blocks, each released as soon as it is seen
+            // full (holding one while waiting for a later one would deadlock:
+            // the read-back of block m + 2 waits for block m's release)
+            while (ok && released < nblk) {
+                if (waited <= released) {
+                    ok = wait_block(released);
+                    waited = released + 1;
+                }
+                if (ok) release_block(released++);
+            }
+            gmod = (gmod + nblk) % NS;
+        }
     }
     tc::fence_before_sync();
     __syncthreads();

@@ -345,7 +345,6 @@ rs_status setup(rs_plan *p, cudaStream_t s, const stream::Opts &o)
     p->stmap_ptr = nullptr;
     p->x_on = 1;
     p->tcs_on = 0;
-    p->fs_on = 0;
     p->stream_ok = 1;
     p->scratch_bytes = int64_t(p->tables.n + p->bands.n + p->tmp.n + p->sbufs.n + p->xbufs.n);
     return RS_OK;

@@ -145,8 +145,8 @@ def test_form_is_reported_and_refused_cleanly(rs):
         rs.rs_plan_set_stream_form(p.handle, 2, 0, 0, 0, 0, s)
     assert e.value.status == rs.RS_ERR_UNSUPPORTED
     assert rs.rs_plan_get_info(p.handle).path == before
-    with pytest.raises(rs.RSError) as e:      # malformed: no kind 5
-        rs.rs_plan_set_stream_form(p.handle, 5, 0, 0, 0, 0, s)
+    with pytest.raises(rs.RSError) as e:      # malformed
+        rs.rs_plan_set_stream_form(p.handle, 4, 0, 0, 0, 0, s)
     assert e.value.status == rs.RS_ERR_INVALID_ARG
     with pytest.raises(rs.RSError) as e:
         rs.rs_plan_set_stream_form(p.handle, 1, 0, 0, 18, 0, s)  # width not a multiple of 4

@@ -58,8 +58,7 @@ def test_stream_parity(rs, shape, kernel, param, boundary, C):
         # only a band wider than the kernel takes (strong downscale) may refuse
         assert "unsupported" in str(e) and OH < H, e
         return
-    # a downscale with 12 or more taps across takes the FP32 streaming downscale (plan path 6)
-    assert info.path == 3 or (info.path == 6 and OH < H), info.path
+    assert info.path == 3
     err = np.abs(got - want).max()
     assert err <= TOL["f32"], (err, info.tile_w, info.span_h, info.span_w)
     tile, _ = run_gpu(t, OH, OW, kernel, boundary, param, rs.RS_NO_STREAM)
@@ -161,12 +160,10 @@ def test_stream_full_size_sampled_rows(rs):
 
 
 def test_stream_full_size_x03_sampled_rows(rs):
-    """4096x4096x3 x0.3 (antialiased, 20 taps) on the forced streaming path (the
-    FP32 streaming downscale, plan path 6; the band kernel at full size is in
-    the FP32 streaming downscale's own tests)."""
+    """4096x4096x3 x0.3 (antialiased, 20 taps) on the streaming kernel's wide strips."""
     t, exact = quantise(synth.sinusoids(4096, 4096, 3, seed=synth.SEED_C2), "f32")
     got, info = run_gpu(t, 0, 0, "lanczos", "mirror", 3.0, rs.RS_FORCE_STREAM, scale=0.3)
-    assert info.path in (3, 6) and (info.out_h, info.out_w) == (1229, 1229)
+    assert info.path == 3 and (info.out_h, info.out_w) == (1229, 1229)
     g = np.random.default_rng(5)
     rows = sorted(set([0, 1, 614, 1227, 1228]) | set(int(r) for r in g.integers(0, 1229, 8)))
     err = 0.0

@@ -132,7 +132,7 @@ def test_tc_chosen_automatically_for_wide_16bit(rs):
         assert p.path == "fused"
         p.close()
     p = rs.Plan(4096, 4096, 3, scale=0.3, kernel="lanczos", param=3.0, boundary="mirror", dtype=torch.float32)
-    assert p.path in ("fused", "stream", "fstream")   # FP32 never takes the 16-bit tensor-core path
+    assert p.path in ("fused", "stream")   # FP32 never takes the 16-bit tensor-core path
     p.close()
 
 
