@@ -32,11 +32,13 @@ using namespace rs;
 constexpr int64_t kStreamMinOut = int64_t(1) << 20;
 constexpr int kAux = 4; // side streams the streamed images are spread over
 
-// Streamed images on one multi-image pipelined kernel (xstream_multi_kernel):
-// one launch over all their CTAs.  dev holds [Params][tensor maps][CTA
-// offsets]; each run stages them in host[k] (pinned) and copies them up on the
-// group's side stream before the launch.
+// Streamed images on one multi-image kernel (the pipelined kernel's
+// xstream_multi_kernel, kind 0, or a band kernel's stream_multi_kernel /
+// stream_ws_multi_kernel, kind 1): one launch over all their CTAs.  dev holds
+// [Params][tensor maps][CTA offsets]; each run stages them in host[k]
+// (pinned) and copies them up on the group's side stream before the launch.
 struct MultiGroup {
+    int kind = 0;
     const void *fn = nullptr;
     int block = 0;
     size_t smem = 0;
@@ -53,7 +55,7 @@ struct MultiGroup {
 
 struct rs_batch {
     std::vector<rs_plan *> plans;
-    std::vector<MultiGroup> groups; // streamed upscales, one launch per kind
+    std::vector<MultiGroup> groups; // streamed images, one launch per kernel
     std::vector<char> streamed; // image i runs on the row-streaming kernel
     int n_streamed = 0;
     std::vector<int> stream_order; // streamed images, largest output first
@@ -386,11 +388,54 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
             g->off.push_back(g->total);
         }
         b->stream_order.swap(rest);
+        // the band kernels' images (the streamed downscales): each re-planned
+        // for its share of the SMs (by output pixels), so that its CTAs take
+        // longer row ranges than a launch of its own would give them, then one
+        // multi-image launch per band kernel
+        int64_t wsum = 0;
+        for (const int i : b->stream_order)
+            if (stream::multi_kernel(b->plans[i])) wsum += int64_t(b->plans[i]->gy.n_out) * b->plans[i]->gx.n_out;
+        rest.clear();
+        for (const int i : b->stream_order) {
+            rs_plan *p = b->plans[i];
+            if (!stream::multi_kernel(p) || b->stream_order.size() < 2) {
+                rest.push_back(i);
+                continue;
+            }
+            const int keep_sms = p->num_sms, keep_code = p->stream_code;
+            const double w = double(int64_t(p->gy.n_out) * p->gx.n_out) / double(std::max<int64_t>(1, wsum));
+            p->num_sms = std::max(1, int(double(keep_sms) * w + 0.5));
+            rs_status st = stream::setup(p, stream, stream::Opts::decode(keep_code));
+            p->num_sms = keep_sms;
+            if (st != RS_OK) st = stream::setup(p, stream, stream::Opts::decode(keep_code));
+            if (st != RS_OK) {
+                delete b;
+                return st;
+            }
+            p->sp.err = static_cast<int *>(b->derr.p);
+            const void *fn = stream::multi_kernel(p);
+            MultiGroup *g = nullptr;
+            for (MultiGroup &h : b->groups)
+                if (h.kind == 1 && h.fn == fn) g = &h;
+            if (!g) {
+                b->groups.emplace_back();
+                g = &b->groups.back();
+                g->kind = 1;
+                g->fn = fn;
+                g->block = p->s_block;
+                g->off.push_back(0);
+            }
+            g->imgs.push_back(i);
+            g->smem = std::max(g->smem, p->s_smem);
+            g->total += p->s_grid;
+            g->off.push_back(g->total);
+        }
+        b->stream_order.swap(rest);
         for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
             MultiGroup &g = b->groups[gi];
             const size_t m = g.imgs.size();
             g.aux = int(gi % kAux);
-            g.o_maps = (sizeof(xstream::Params) * m + 127) / 128 * 128;
+            g.o_maps = ((g.kind ? sizeof(stream::Params) : sizeof(xstream::Params)) * m + 127) / 128 * 128;
             g.o_off = g.o_maps + sizeof(CUtensorMap) * m;
             g.bytes = g.o_off + sizeof(int32_t) * (m + 1);
             if (occupancy(g.fn, g.block, g.smem) < 1) {
@@ -506,16 +551,23 @@ rs_status rs_batch_run(rs_batch *b, const void *const *d_in, void *const *d_out,
     if (b->n_streamed) {
         for (MultiGroup &g : b->groups) {
             const size_t m = g.imgs.size();
-            xstream::Params *hp = reinterpret_cast<xstream::Params *>(g.host[k]);
             CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(g.host[k] + g.o_maps);
             for (size_t j = 0; j < m; ++j) {
                 const int i = g.imgs[j];
                 if (g.st_in[k][j] == d_in[i] && g.st_out[k][j] == d_out[i]) continue;
-                xstream::Params xp = b->plans[i]->xp;
-                xp.in = d_in[i];
-                xp.out = d_out[i];
-                xp.err = static_cast<int *>(b->derr.p);
-                hp[j] = xp;
+                if (g.kind == 0) {
+                    xstream::Params xp = b->plans[i]->xp;
+                    xp.in = d_in[i];
+                    xp.out = d_out[i];
+                    xp.err = static_cast<int *>(b->derr.p);
+                    reinterpret_cast<xstream::Params *>(g.host[k])[j] = xp;
+                } else {
+                    stream::Params sp = b->plans[i]->sp;
+                    sp.in = d_in[i];
+                    sp.out = d_out[i];
+                    sp.err = static_cast<int *>(b->derr.p);
+                    reinterpret_cast<stream::Params *>(g.host[k])[j] = sp;
+                }
                 const rs_status st = stream::encode_input_map(b->plans[i], d_in[i], &hm[j]);
                 if (st != RS_OK) return st;
                 g.st_in[k][j] = d_in[i];
@@ -524,11 +576,13 @@ rs_status rs_batch_run(rs_batch *b, const void *const *d_in, void *const *d_out,
             cudaStream_t as = b->aux[g.aux];
             e = cudaMemcpyAsync(g.dev.p, g.host[k], g.bytes, cudaMemcpyHostToDevice, as);
             xstream::Multi mu;
+            stream::Multi ms;
             mu.ps = static_cast<const xstream::Params *>(g.dev.p);
-            mu.maps = reinterpret_cast<const CUtensorMap *>(static_cast<char *>(g.dev.p) + g.o_maps);
-            mu.cta_off = reinterpret_cast<const int32_t *>(static_cast<char *>(g.dev.p) + g.o_off);
-            mu.n = int32_t(m);
-            void *args[1] = {&mu};
+            ms.ps = static_cast<const stream::Params *>(g.dev.p);
+            mu.maps = ms.maps = reinterpret_cast<const CUtensorMap *>(static_cast<char *>(g.dev.p) + g.o_maps);
+            mu.cta_off = ms.cta_off = reinterpret_cast<const int32_t *>(static_cast<char *>(g.dev.p) + g.o_off);
+            mu.n = ms.n = int32_t(m);
+            void *args[1] = {g.kind ? static_cast<void *>(&ms) : static_cast<void *>(&mu)};
             if (e == cudaSuccess) e = cudaLaunchKernel(g.fn, dim3(g.total), dim3(g.block), args, g.smem, as);
             if (e != cudaSuccess) return cuda_fail(e, "batch: multi-image streaming launch");
         }

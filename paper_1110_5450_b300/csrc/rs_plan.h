@@ -242,6 +242,9 @@ rs_status launch(rs_plan *p, const void *d_in, void *d_out, cudaStream_t s);
 rs_status encode_input_map(const rs_plan *p, const void *d_in, CUtensorMap *map);
 // Row-range counts the configuration searches model (ascending).
 std::vector<int> range_counts(int n_strips, int64_t slots, int max_nr);
+// The multi-image variant (stream_multi_kernel / stream_ws_multi_kernel) of
+// the plan's configured band kernel, or nullptr (no band configuration).
+const void *multi_kernel(const rs_plan *p);
 // Loads every band-kernel instantiation of `dtype` (lazy module loading
 // would otherwise load each on its first launch, in the middle of a stream's
 // work) and tabulates its occupancy.

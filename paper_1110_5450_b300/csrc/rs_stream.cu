@@ -17,17 +17,23 @@ namespace {
 constexpr int kJV8[] = {8, 10, 12, 14, 16};
 constexpr int kJV4[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32};
 
-const void *kernel_for(int dtype, int C, int jv, int gv, bool ws)
+const void *kernel_for(int dtype, int C, int jv, int gv, bool ws, bool multi = false)
 {
     switch (dtype) {
-    case RS_F32: return kernel_f32(C, jv, gv, ws);
-    case RS_F16: return kernel_f16(C, jv, gv, ws);
-    case RS_BF16: return kernel_bf16(C, jv, gv, ws);
+    case RS_F32: return kernel_f32(C, jv, gv, ws, multi);
+    case RS_F16: return kernel_f16(C, jv, gv, ws, multi);
+    case RS_BF16: return kernel_bf16(C, jv, gv, ws, multi);
     }
     return nullptr;
 }
 
 } // namespace
+
+const void *multi_kernel(const rs_plan *p)
+{
+    if (!p->stream_ok || p->x_on || p->tcs_on) return nullptr;
+    return kernel_for(p->desc.in_dtype, p->desc.channels, p->sp.JV, p->sp.GV, p->sp.NW != 0, true);
+}
 
 void preload(int dtype)
 {
@@ -391,6 +397,7 @@ rs_status setup(rs_plan *p, cudaStream_t s, const Opts &opts)
     rs_status st = rebuild(p, s);
     if (st != RS_OK) return st;
     p->s_fn = fn;
+    p->s_block = kThreads;
     p->s_smem = smem;
     p->s_grid = n_strips * ((pairs + ppr - 1) / ppr);
     p->s_ctas = occ;

@@ -275,9 +275,12 @@ __device__ __forceinline__ void v_task(const float4 *src4, const float4 *wv, T *
     }
 }
 
+// The work of one CTA of the phase-alternating band kernel: CTA `bid` of the
+// image that `tmap_ptr` and `p` describe.
 template <typename T, int C, int JV, int GV>
-__global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+__device__ __forceinline__ void stream_cta(const CUtensorMap *tmap_ptr, const Params &p, int bid)
 {
+    const CUtensorMap &tmap = *tmap_ptr;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (fused::smem_addr(smem_raw) & 127u)) & 127u);
     const int ngx = p.SW / kG;
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     auto slot_vb = [&](int s) { return reinterpret_cast<const int32_t *>(slots + s * L.slot + L.in_blk + L.wv); };
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int strip = int(blockIdx.x) % p.n_strips, range = int(blockIdx.x) / p.n_strips;
+    const int strip = bid % p.n_strips, range = bid / p.n_strips;
     const int p0 = range * p.pairs_per_range;
     const int p1 = min(p.pairs, p0 + p.pairs_per_range);
     if (p0 >= p1) return;
@@ -426,6 +429,43 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     }
 }
 
+// Several images in one launch (a batch): CTA b belongs to image i with
+// cta_off[i] <= b < cta_off[i + 1] and takes that image's CTA b - cta_off[i];
+// ps and maps hold each image's parameters and 64-byte aligned tensor map.
+struct Multi {
+    const Params *ps;
+    const CUtensorMap *maps;
+    const int32_t *cta_off; // [n + 1]
+    int32_t n;
+};
+
+__device__ __forceinline__ int multi_image(const Multi &m, int b)
+{
+    int lo = 0, hi = m.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(m.cta_off + mid) <= b)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <typename T, int C, int JV, int GV>
+__global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ CUtensorMap tmap, const Params p)
+{
+    stream_cta<T, C, JV, GV>(&tmap, p, int(blockIdx.x));
+}
+
+template <typename T, int C, int JV, int GV>
+__global__ void __launch_bounds__(kThreads, 2) stream_multi_kernel(const __grid_constant__ Multi m)
+{
+    const int b = int(blockIdx.x), i = multi_image(m, b);
+    const Params p = m.ps[i];
+    stream_cta<T, C, JV, GV>(m.maps + i, p, b - __ldg(m.cta_off + i));
+}
+
 // ---------------------------------------------------------------------------
 // Warp-specialised variant: the first HW warps run the horizontal pass on
 // block k while the others run the vertical pass on block k - 1 (or earlier),
@@ -472,10 +512,11 @@ __device__ __forceinline__ bool group_and(int id, int threads, bool v)
     return r != 0;
 }
 
+// The work of one CTA of the warp-specialised band kernel.
 template <typename T, int C, int JV, int GV>
-__global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                  const Params p)
+__device__ __forceinline__ void stream_ws_cta(const CUtensorMap *tmap_ptr, const Params &p, int bid)
 {
+    const CUtensorMap &tmap = *tmap_ptr;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (fused::smem_addr(smem_raw) & 127u)) & 127u);
     const int ngx = p.SW / kG;
@@ -497,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int kHWarps = p.HW, kHThreads = 32 * p.HW, kVThreads = kThreads - kHThreads;
-    const int strip = int(blockIdx.x) % p.n_strips, range = int(blockIdx.x) / p.n_strips;
+    const int strip = bid % p.n_strips, range = bid / p.n_strips;
     const int p0 = range * p.pairs_per_range;
     const int p1 = min(p.pairs, p0 + p.pairs_per_range);
     if (p0 >= p1) return;
@@ -645,47 +686,65 @@ __global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_con
     }
 }
 
+template <typename T, int C, int JV, int GV>
+__global__ void __launch_bounds__(kThreads, 2) stream_ws_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                  const Params p)
+{
+    stream_ws_cta<T, C, JV, GV>(&tmap, p, int(blockIdx.x));
+}
+
+template <typename T, int C, int JV, int GV>
+__global__ void __launch_bounds__(kThreads, 2) stream_ws_multi_kernel(const __grid_constant__ Multi m)
+{
+    const int b = int(blockIdx.x), i = multi_image(m, b);
+    const Params p = m.ps[i];
+    stream_ws_cta<T, C, JV, GV>(m.maps + i, p, b - __ldg(m.cta_off + i));
+}
+
 // ---------------------------------------------------------------------------
 // Instantiated kernels: storage type x channels x vertical taps x rows per
 // vertical group (a plan's band is padded with zero weights to the next
 // instantiated width): groups of 8 rows up to 16 taps, groups of 4 up to 32.
 // One translation unit per storage type instantiates its table.
 
-template <typename T, int C, int JV, int GV> const void *kernel_of(bool ws)
+template <typename T, int C, int JV, int GV> const void *kernel_of(bool ws, bool multi)
 {
+    if (multi)
+        return ws ? reinterpret_cast<const void *>(&stream_ws_multi_kernel<T, C, JV, GV>)
+                  : reinterpret_cast<const void *>(&stream_multi_kernel<T, C, JV, GV>);
     return ws ? reinterpret_cast<const void *>(&stream_ws_kernel<T, C, JV, GV>)
               : reinterpret_cast<const void *>(&stream_kernel<T, C, JV, GV>);
 }
 
-template <typename T, int C, int GV> const void *kernel_jv(int jv, bool ws)
+template <typename T, int C, int GV> const void *kernel_jv(int jv, bool ws, bool multi)
 {
     switch (jv) {
-    case 4: return GV == 4 ? kernel_of<T, C, 4, 4>(ws) : nullptr;
-    case 6: return GV == 4 ? kernel_of<T, C, 6, 4>(ws) : nullptr;
-    case 8: return kernel_of<T, C, 8, GV>(ws);
-    case 10: return kernel_of<T, C, 10, GV>(ws);
-    case 12: return kernel_of<T, C, 12, GV>(ws);
-    case 14: return kernel_of<T, C, 14, GV>(ws);
-    case 16: return kernel_of<T, C, 16, GV>(ws);
-    case 20: return GV == 4 ? kernel_of<T, C, 20, 4>(ws) : nullptr;
-    case 24: return GV == 4 ? kernel_of<T, C, 24, 4>(ws) : nullptr;
-    case 28: return GV == 4 ? kernel_of<T, C, 28, 4>(ws) : nullptr;
-    case 32: return GV == 4 ? kernel_of<T, C, 32, 4>(ws) : nullptr;
+    case 4: return GV == 4 ? kernel_of<T, C, 4, 4>(ws, multi) : nullptr;
+    case 6: return GV == 4 ? kernel_of<T, C, 6, 4>(ws, multi) : nullptr;
+    case 8: return kernel_of<T, C, 8, GV>(ws, multi);
+    case 10: return kernel_of<T, C, 10, GV>(ws, multi);
+    case 12: return kernel_of<T, C, 12, GV>(ws, multi);
+    case 14: return kernel_of<T, C, 14, GV>(ws, multi);
+    case 16: return kernel_of<T, C, 16, GV>(ws, multi);
+    case 20: return GV == 4 ? kernel_of<T, C, 20, 4>(ws, multi) : nullptr;
+    case 24: return GV == 4 ? kernel_of<T, C, 24, 4>(ws, multi) : nullptr;
+    case 28: return GV == 4 ? kernel_of<T, C, 28, 4>(ws, multi) : nullptr;
+    case 32: return GV == 4 ? kernel_of<T, C, 32, 4>(ws, multi) : nullptr;
     }
     return nullptr;
 }
 
-template <typename T> const void *kernel_table(int C, int jv, int gv, bool ws)
+template <typename T> const void *kernel_table(int C, int jv, int gv, bool ws, bool multi)
 {
-    if (C == 1) return gv == 8 ? kernel_jv<T, 1, 8>(jv, ws) : kernel_jv<T, 1, 4>(jv, ws);
-    if (C == 3) return gv == 8 ? kernel_jv<T, 3, 8>(jv, ws) : kernel_jv<T, 3, 4>(jv, ws);
+    if (C == 1) return gv == 8 ? kernel_jv<T, 1, 8>(jv, ws, multi) : kernel_jv<T, 1, 4>(jv, ws, multi);
+    if (C == 3) return gv == 8 ? kernel_jv<T, 3, 8>(jv, ws, multi) : kernel_jv<T, 3, 4>(jv, ws, multi);
     return nullptr;
 }
 
 // defined in rs_stream_f32.cu, rs_stream_f16.cu, rs_stream_bf16.cu
-const void *kernel_f32(int C, int jv, int gv, bool ws);
-const void *kernel_f16(int C, int jv, int gv, bool ws);
-const void *kernel_bf16(int C, int jv, int gv, bool ws);
+const void *kernel_f32(int C, int jv, int gv, bool ws, bool multi = false);
+const void *kernel_f16(int C, int jv, int gv, bool ws, bool multi = false);
+const void *kernel_bf16(int C, int jv, int gv, bool ws, bool multi = false);
 
 } // namespace stream
 } // namespace rs

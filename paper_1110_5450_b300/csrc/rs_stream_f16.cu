@@ -5,7 +5,7 @@
 namespace rs {
 namespace stream {
 
-const void *kernel_f16(int C, int jv, int gv, bool ws) { return kernel_table<__half>(C, jv, gv, ws); }
+const void *kernel_f16(int C, int jv, int gv, bool ws, bool multi) { return kernel_table<__half>(C, jv, gv, ws, multi); }
 
 } // namespace stream
 } // namespace rs
