@@ -389,22 +389,36 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
             g->off.push_back(g->total);
         }
         b->stream_order.swap(rest);
-        // the band kernels' images (the streamed downscales): each re-planned
-        // for its share of the SMs (by output pixels), so that its CTAs take
-        // longer row ranges than a launch of its own would give them, then one
-        // multi-image launch per band kernel
-        int64_t wsum = 0;
+        // the band kernels' images (the streamed downscales): one multi-image
+        // launch per band kernel, each image first re-planned for its share of
+        // the SMs within its launch (by output pixels), so that its CTAs take
+        // longer row ranges than a launch of its own would give them; a kernel
+        // with one image keeps its own launch
+        std::vector<std::pair<const void *, int64_t>> wsum; // output pixels per band kernel
+        auto wsum_of = [&](const void *fn) -> int64_t & {
+            for (auto &w : wsum)
+                if (w.first == fn) return w.second;
+            wsum.emplace_back(fn, 0);
+            return wsum.back().second;
+        };
         for (const int i : b->stream_order)
-            if (stream::multi_kernel(b->plans[i])) wsum += int64_t(b->plans[i]->gy.n_out) * b->plans[i]->gx.n_out;
+            if (const void *fn = stream::multi_kernel(b->plans[i]))
+                wsum_of(fn) += int64_t(b->plans[i]->gy.n_out) * b->plans[i]->gx.n_out;
+        auto images_of = [&](const void *fn) {
+            int n = 0;
+            for (const int j : b->stream_order) n += stream::multi_kernel(b->plans[j]) == fn ? 1 : 0;
+            return n;
+        };
         rest.clear();
         for (const int i : b->stream_order) {
             rs_plan *p = b->plans[i];
-            if (!stream::multi_kernel(p) || b->stream_order.size() < 2) {
+            const void *fn0 = stream::multi_kernel(p);
+            if (!fn0 || images_of(fn0) < 2) {
                 rest.push_back(i);
                 continue;
             }
             const int keep_sms = p->num_sms, keep_code = p->stream_code;
-            const double w = double(int64_t(p->gy.n_out) * p->gx.n_out) / double(std::max<int64_t>(1, wsum));
+            const double w = double(int64_t(p->gy.n_out) * p->gx.n_out) / double(std::max<int64_t>(1, wsum_of(fn0)));
             p->num_sms = std::max(1, int(double(keep_sms) * w + 0.5));
             rs_status st = stream::setup(p, stream, stream::Opts::decode(keep_code));
             p->num_sms = keep_sms;
