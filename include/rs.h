@@ -344,10 +344,12 @@ RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in,
  * spread over the whole GPU.  The launch (parameter upload, kernel) is a CUDA
  * graph built at creation and replayed by rs_batch_run.  In a batch planned
  * for TMA, images of at least 2^20 output pixels that the row-streaming
- * kernel takes leave the tile list and run on that kernel instead, one launch
- * each, largest first, spread over four side streams that are forked from
- * and joined back into the caller's stream around the graph (so they overlap
- * one another and the persistent kernel; rs_batch_info.n_streamed).
+ * kernels take leave the tile list and run on them instead
+ * (rs_batch_info.n_streamed): the images of one streaming kernel share one
+ * multi-image launch (each image re-planned for its share of the SMs within
+ * that launch; a kernel with one image keeps a launch of its own), spread
+ * over four side streams that are forked from and joined back into the
+ * caller's stream around the graph.
  * ---------------------------------------------------------------------- */
 typedef struct rs_batch rs_batch;
 
