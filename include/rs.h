@@ -343,7 +343,7 @@ RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in,
  * list, dealt round-robin to the persistent CTAs, so every image's tiles
  * spread over the whole GPU.  The launch (parameter upload, kernel) is a CUDA
  * graph built at creation and replayed by rs_batch_run.  In a batch planned
- * for TMA, images of at least 2^20 output pixels that the row-streaming
+ * for TMA, images of at least 2^18 output pixels that the row-streaming
  * kernels take leave the tile list and run on them instead
  * (rs_batch_info.n_streamed): the images of one streaming kernel share one
  * multi-image launch (a band kernel's images are first re-planned for their

@@ -30,7 +30,9 @@
 
 using namespace rs;
 
-constexpr int64_t kStreamMinOut = int64_t(1) << 20;
+// (2^18: with the streamed images in multi-image launches, the C4 batch
+// measured 3.93 ms at 2^18, 3.98 at 2^19, 4.09 at 2^20, 4.01 at 2^17)
+constexpr int64_t kStreamMinOut = int64_t(1) << 18;
 constexpr int kAux = 4; // side streams the streamed images are spread over
 
 // Streamed images on one multi-image kernel (the pipelined kernel's
