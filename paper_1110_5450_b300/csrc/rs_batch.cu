@@ -24,6 +24,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "rs_plan.h"
@@ -365,15 +366,47 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
                int64_t(b->plans[y]->gy.n_out) * b->plans[y]->gx.n_out;
     });
     // the streamed upscales on the pipelined kernel: one multi-image launch per
-    // (kernel, block size), their CTAs in order of the images (largest first)
+    // (kernel, block size), their CTAs in order of the images (largest first);
+    // where a launch takes several images, each is first re-planned for its
+    // share of the SMs within it (by output pixels; its row ranges chosen
+    // anew, its other choices kept), as for the band kernels below
     {
         std::vector<int> rest;
+        std::vector<std::tuple<const void *, int, int64_t, int>> xsum; // (kernel, block): pixels, images
+        auto xsum_of = [&](const void *fn, int block) -> std::tuple<const void *, int, int64_t, int> & {
+            for (auto &w : xsum)
+                if (std::get<0>(w) == fn && std::get<1>(w) == block) return w;
+            xsum.emplace_back(fn, block, 0, 0);
+            return xsum.back();
+        };
+        for (const int i : b->stream_order)
+            if (const void *fn = xstream::multi_kernel(b->plans[i])) {
+                auto &w = xsum_of(fn, b->plans[i]->s_block);
+                std::get<2>(w) += int64_t(b->plans[i]->gy.n_out) * b->plans[i]->gx.n_out;
+                std::get<3>(w) += 1;
+            }
         for (const int i : b->stream_order) {
             rs_plan *p = b->plans[i];
             const void *fn = xstream::multi_kernel(p);
             if (!fn) {
                 rest.push_back(i);
                 continue;
+            }
+            const auto &w = xsum_of(fn, p->s_block);
+            if (std::get<3>(w) >= 2) {
+                const int keep_sms = p->num_sms, keep_code = p->stream_code;
+                stream::Opts o = stream::Opts::decode(keep_code);
+                o.nr = 0;
+                const double share = double(int64_t(p->gy.n_out) * p->gx.n_out) / double(std::max<int64_t>(1, std::get<2>(w)));
+                p->num_sms = std::max(1, int(double(keep_sms) * share + 0.5));
+                rs_status st = stream::setup(p, stream, o);
+                p->num_sms = keep_sms;
+                if (st != RS_OK || xstream::multi_kernel(p) != fn) st = stream::setup(p, stream, stream::Opts::decode(keep_code));
+                if (st != RS_OK) {
+                    delete b;
+                    return st;
+                }
+                p->xp.err = static_cast<int *>(b->derr.p);
             }
             MultiGroup *g = nullptr;
             for (MultiGroup &h : b->groups)
