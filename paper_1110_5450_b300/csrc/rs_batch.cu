@@ -5,9 +5,10 @@
 // beside the persistent kernel: on large upscales they are 2-4x faster than
 // the tile kernel.  The pipelined kernel's images go into one multi-image
 // launch per kernel kind (their CTAs in one grid, each image's parameters and
-// tensor map read from device arrays); so do the band kernels' images, each
-// re-planned first for its share of the SMs (by output pixels), so that its
-// CTAs take longer row ranges than a launch of its own would give them.
+// tensor map read from device arrays), and so do the band kernels' images.
+// Where a launch takes several images, each is re-planned first for its share
+// of the SMs within it (by output pixels), so that its CTAs take longer row
+// ranges than a launch of its own would give them.
 //
 // Each image gets an ordinary plan (exact taps, FP64 weight tables); the batch
 // then re-plans every image's fused configuration under one launch-wide
