@@ -347,7 +347,8 @@ RS_API rs_status rs_resample_noalloc(const rs_plan_desc *desc, const void *d_in,
  * kernels take leave the tile list and run on them instead
  * (rs_batch_info.n_streamed): the images of one streaming kernel share one
  * multi-image launch (where it takes several images, each is first
- * re-planned for its share of the SMs within that launch; a band kernel with
+ * re-planned for its share of the SMs within that launch, strip width and
+ * row ranges chosen anew for that share; a band kernel with
  * one image keeps a launch of its own), spread
  * over four side streams that are forked from and joined back into the
  * caller's stream around the graph.

@@ -7,8 +7,10 @@
 // launch per kernel kind (their CTAs in one grid, each image's parameters and
 // tensor map read from device arrays), and so do the band kernels' images.
 // Where a launch takes several images, each is re-planned first for its share
-// of the SMs within it (by output pixels), so that its CTAs take longer row
-// ranges than a launch of its own would give them.
+// of the SMs within it (by output pixels): its strip width and row ranges are
+// chosen anew for that share, so that its CTAs take wider strips and longer
+// row ranges than a launch of its own would give them (narrow 16-bit strips
+// stage small blocks and are bound by the latency of their copies).
 //
 // Each image gets an ordinary plan (exact taps, FP64 weight tables); the batch
 // then re-plans every image's fused configuration under one launch-wide
@@ -369,8 +371,9 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
     // the streamed upscales on the pipelined kernel: one multi-image launch per
     // (kernel, block size), their CTAs in order of the images (largest first);
     // where a launch takes several images, each is first re-planned for its
-    // share of the SMs within it (by output pixels; its row ranges chosen
-    // anew, its other choices kept), as for the band kernels below
+    // share of the SMs within it (by output pixels; its strip width and row
+    // ranges chosen anew, its other choices kept), as for the band kernels
+    // below
     {
         std::vector<int> rest;
         std::vector<std::tuple<const void *, int, int64_t, int>> xsum; // (kernel, block): pixels, images
@@ -398,6 +401,7 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
                 const int keep_sms = p->num_sms, keep_code = p->stream_code;
                 stream::Opts o = stream::Opts::decode(keep_code);
                 o.nr = 0;
+                o.sw = 0;
                 const double share = double(int64_t(p->gy.n_out) * p->gx.n_out) / double(std::max<int64_t>(1, std::get<2>(w)));
                 p->num_sms = std::max(1, int(double(keep_sms) * share + 0.5));
                 rs_status st = stream::setup(p, stream, o);
@@ -427,9 +431,9 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
         b->stream_order.swap(rest);
         // the band kernels' images (the streamed downscales): one multi-image
         // launch per band kernel, each image first re-planned for its share of
-        // the SMs within its launch (by output pixels), so that its CTAs take
-        // longer row ranges than a launch of its own would give them; a kernel
-        // with one image keeps its own launch
+        // the SMs within its launch (by output pixels; its strip width chosen
+        // anew for that share, its other choices kept); a kernel with one
+        // image keeps its own launch
         std::vector<std::pair<const void *, int64_t>> wsum; // output pixels per band kernel
         auto wsum_of = [&](const void *fn) -> int64_t & {
             for (auto &w : wsum)
@@ -456,9 +460,11 @@ rs_status rs_batch_create(const rs_plan_desc *descs, int32_t n, void *stream_v, 
             const int keep_sms = p->num_sms, keep_code = p->stream_code;
             const double w = double(int64_t(p->gy.n_out) * p->gx.n_out) / double(std::max<int64_t>(1, wsum_of(fn0)));
             p->num_sms = std::max(1, int(double(keep_sms) * w + 0.5));
-            rs_status st = stream::setup(p, stream, stream::Opts::decode(keep_code));
+            stream::Opts ob = stream::Opts::decode(keep_code);
+            ob.sw = 0;
+            rs_status st = stream::setup(p, stream, ob);
             p->num_sms = keep_sms;
-            if (st != RS_OK) st = stream::setup(p, stream, stream::Opts::decode(keep_code));
+            if (st != RS_OK || stream::multi_kernel(p) != fn0) st = stream::setup(p, stream, stream::Opts::decode(keep_code));
             if (st != RS_OK) {
                 delete b;
                 return st;
