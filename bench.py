@@ -910,6 +910,22 @@ def main():
             graph.replay()
     torch.cuda.synchronize()
 
+    # each scale's resample alone, K launches captured in a CUDA graph: the
+    # kernel timings below replay it between CUDA events, so that no host gap
+    # (the clock sampler's process competes for the host) opens between the
+    # launches and inflates their average
+    kgraphs = []
+    for i in (0, 1):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(args.steps):
+                plans[i](x, out=ys[i], stream=stream)
+        kgraphs.append(g)
+    with torch.cuda.stream(stream):
+        for g in kgraphs:
+            g.replay()
+    torch.cuda.synchronize()
+
     sampler = ClockSampler(dev.index or 0)
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
@@ -936,17 +952,17 @@ def main():
     # between CUDA events, right after the timed steps and on the same buffers
     ka = torch.cuda.Event(enable_timing=True)
     kb = torch.cuda.Event(enable_timing=True)
-    ka.record(stream)
-    for _ in range(args.steps):
-        plans[0](x, out=ys[0], stream=stream)
-    kb.record(stream)
+    with torch.cuda.stream(stream):
+        ka.record(stream)
+        kgraphs[0].replay()
+        kb.record(stream)
     # and the x0.3 resample, the same way (its own roofline figure)
     kc = torch.cuda.Event(enable_timing=True)
     kd = torch.cuda.Event(enable_timing=True)
-    kc.record(stream)
-    for _ in range(args.steps):
-        plans[1](x, out=ys[1], stream=stream)
-    kd.record(stream)
+    with torch.cuda.stream(stream):
+        kc.record(stream)
+        kgraphs[1].replay()
+        kd.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end)
