@@ -41,6 +41,9 @@ const void *multi_kernel(const rs_plan *p)
 {
     if (!p->x_on) return nullptr;
     const int big = p->s_block > 32 * kSmallWarps ? 1 : 0;
+    // blocks of at most kMidWarps warps: the variant with the higher register cap
+    if (!big && p->s_block <= 32 * kMidWarps)
+        return kernel_for(p->desc.in_dtype, p->desc.channels, int(p->gx.t_eff), 4);
     return kernel_for(p->desc.in_dtype, p->desc.channels, int(p->gx.t_eff), 2 + big);
 }
 

@@ -49,6 +49,7 @@ namespace xstream {
 
 constexpr int kMaxWarps = 16;   // producer + horizontal + vertical warps of a CTA, at most
 constexpr int kSmallWarps = 12; // at most this many: the kernel variant for 2 CTAs per SM
+constexpr int kMidWarps = 10;   // multi-image variant for 2 CTAs per SM of at most this many warps
 constexpr int kRB = 32;   // input rows per staged block (one per lane of a horizontal task)
 constexpr int kG = 4;     // outputs per group (columns across, rows down)
 constexpr int kMaxNI = 4; // staged input blocks at most
@@ -568,9 +569,13 @@ __global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ?
 }
 
 // The same kernel over the CTAs of several images (one launch for a batch's
-// streamed upscales of one kind).
+// streamed upscales of one kind).  BIG = 2: two CTAs per SM of at most
+// kMidWarps warps, whose higher register cap keeps the multi-image lookup
+// from spilling (the single-channel 4-tap variant spilled 16 bytes under the
+// 12-warp cap).
 template <typename T, int C, int TAPS, int BIG>
-__global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ? 1 : 2)
+__global__ void __launch_bounds__(BIG == 1 ? 32 * kMaxWarps : BIG == 2 ? 32 * kMidWarps : 32 * kSmallWarps,
+                                  BIG == 1 ? 1 : 2)
     xstream_multi_kernel(const __grid_constant__ Multi m)
 {
     const int b = int(blockIdx.x);
@@ -588,12 +593,14 @@ __global__ void __launch_bounds__(BIG ? 32 * kMaxWarps : 32 * kSmallWarps, BIG ?
 
 // Instantiated kernels: storage type x channels x taps per output x the
 // variant (big = 0 / 1: one image, up to kSmallWarps / kMaxWarps warps; 2 / 3:
-// the multi-image kernel with the same launch bounds).
+// the multi-image kernel with the same launch bounds; 4: the multi-image
+// kernel for up to kMidWarps warps).
 template <typename T, int C, int TAPS> const void *kernel_big(int big)
 {
     return big == 1   ? reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 1>)
            : big == 0 ? reinterpret_cast<const void *>(&xstream_kernel<T, C, TAPS, 0>)
            : big == 3 ? reinterpret_cast<const void *>(&xstream_multi_kernel<T, C, TAPS, 1>)
+           : big == 4 ? reinterpret_cast<const void *>(&xstream_multi_kernel<T, C, TAPS, 2>)
                       : reinterpret_cast<const void *>(&xstream_multi_kernel<T, C, TAPS, 0>);
 }
 template <typename T> const void *kernel_table(int C, int taps, int big)
