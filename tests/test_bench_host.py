@@ -30,3 +30,11 @@ def test_traffic_only_for_the_measured_sources(monkeypatch):
 
 def test_traffic_sources_exist():
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_committed_traffic_is_current():
+    # the committed DRAM record was taken on the kernel sources as they stand
+    # (a change to them needs a new capture, else the bench reports null)
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    assert rec["source_hash"] == bench.kernel_source_hash()
